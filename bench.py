@@ -1,0 +1,303 @@
+"""Throughput benchmark of the fused isotropic phase-field step on GB300.
+
+Workload (one "step"): one explicit time step of every instance of the 2D
+orientation sweep -- ten 1024 x 1024 free-dendrite runs at alpha0 = 0, 5,
+..., 45 degrees (h = 0.8, dt = 0.02, k = 0.15, eps4 = 0.02, lambda = 10,
+D = 0.6267 lambda, U0 = -0.55, seed r = 10 h), scheme S-bar_{2,1}, FP32
+fields, batched in one persistent launch per step replayed from a CUDA
+graph, with the FP64 observe reductions every 100 steps.  Synthetic data.
+
+Prints one JSON line (rank 0).  `value` is aggregate cell updates per
+second (GLUPS) over all ranks; `roofline` reports the dominant kernel's
+algorithmic HBM bandwidth against the measured copy bandwidth;
+`cpu_baseline` times the FP64 CPU oracle on a bounded sample; `e2e` is the
+same job through the public API with the state uploaded from and returned to
+pinned host buffers inside the timed region.
+
+--impl reference times the FP64 CPU oracle itself (the only baseline: the
+paper ships no code), one instance-step of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS & %HBM peak, batched FP32 vs plain FP64 at stated error; p50/p99 latency"
+THETAS = tuple(range(0, 50, 5))
+OBS_EVERY = 100
+B_PER_CELL = {"f32": 18, "f64": 34}  # read psi, U, grain; write psi', U'
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        try:
+            self.f.flush()
+            rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+            sm = [float(r[1]) for r in rows]
+            mx = max(float(r[2]) for r in rows)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+        except Exception as e:  # pragma: no cover
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)}
+
+
+def workloads(n, scheme):
+    from paper_2110_12448_gb300 import synth
+    return [synth.free_dendrite_2d(n, float(t), scheme, steps=20000) for t in THETAS]
+
+
+def cpu_baseline(n, scheme, max_seconds=20.0):
+    """FP64 oracle on the host cores, bounded sample: one instance, a few steps."""
+    import numpy as np
+    from oracle import oracle as O
+    ws = workloads(n, scheme)
+    w = ws[3]
+    p = O.params(nx=w.nx, ny=w.ny, scheme=O.SBAR21 if scheme == "SBAR21" else {"S21": 1, "S10": 0}[scheme], h=w.h,
+                 dt=w.dt, k=w.k, eps4=w.eps4, lam=w.lam, D=w.D)
+    psi, U, g = O.init_seeds(p, w.U0, w.seeds, w.seed_grain)
+    O.step(p, w.rots, g, psi, U, 1)  # warm
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < max_seconds and steps < 50:
+        psi, U = O.step(p, w.rots, g, psi, U, 1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": w.n_cells * steps / dt / 1e9, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} steps of one {w.nx}x{w.ny} instance (alpha0={THETAS[3]} deg) of the 10, FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import oracle as O
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    ws = workloads(args.n, args.scheme)
+    states = []
+    for w in ws:
+        p = O.params(nx=w.nx, ny=w.ny, scheme={"SBAR21": 2, "S21": 1, "S10": 0}[args.scheme], h=w.h, dt=w.dt, k=w.k,
+                     eps4=w.eps4, lam=w.lam, D=w.D)
+        psi, U, g = O.init_seeds(p, w.U0, w.seeds, w.seed_grain)
+        states.append([p, w, psi, U, g])
+
+    def one(i):
+        p, w, psi, U, g = states[i % len(states)]
+        psi, U = O.step(p, w.rots, g, psi, U, 1)
+        states[i % len(states)][2:4] = [psi, U]
+        return w.n_cells
+
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    cells = 0
+    for i in range(args.steps):
+        cells += one(args.warmup + i)
+    dt = time.perf_counter() - t0
+    v = cells / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"metric": METRIC, "value": v, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"orientation sweep 2D, 10 x {args.n}^2, {args.scheme}", "sample":
+                       "one instance-step per step, cycling alpha0", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} instance-steps of {args.n}^2"},
+            "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2110_12448_gb300 import native as N
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    stream = torch.cuda.Stream()
+    ws = workloads(args.n, args.scheme)
+    sims = []
+    with torch.cuda.stream(stream):
+        for w in ws:
+            sims.append(N.Sim.from_workload(w, args.precision, stream=stream))
+    max_work = sum(N.Group.work_items(s) for s in sims)
+    group = N.Group(len(sims), max_work, stream=stream)
+    for s in sims:
+        group.add(s)
+    cells = sum(s.n_cells for s in sims)
+
+    def steps(k, ev=None):
+        """k steps with observe every OBS_EVERY; returns kernel-only event pairs."""
+        done = 0
+        pairs = []
+        while done < k:
+            chunk = min(OBS_EVERY - (sims[0].steps_done % OBS_EVERY), k - done)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            group.step(chunk, use_graph=True)
+            b.record(stream)
+            pairs.append((a, b, chunk))
+            done += chunk
+            if sims[0].steps_done % OBS_EVERY == 0:
+                for s in sims:
+                    s.observe(0)
+        return pairs
+
+    steps(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    with clocks:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pairs = steps(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    kern_ms = sum(a.elapsed_time(b) for a, b, _ in pairs)
+    n_launch = sum(c for _, _, c in pairs)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = cells * args.steps * world / (ms / 1e3) / 1e9
+
+    # roofline of the fused step kernel: algorithmic bytes per launch / mean launch time
+    peak, peak_kind = peaks()
+    bpc = B_PER_CELL[args.precision]
+    achieved = cells * bpc / (kern_ms / n_launch / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": peak_kind, "bytes_per_cell": bpc,
+            "kernel": f"k_step2d<{'float' if args.precision == 'f32' else 'double'},{args.scheme},128>"}
+
+    # end to end through the public API: state in from pinned host buffers,
+    # K steps, state and observation back, all inside the timed region
+    host = [(torch.empty(s.shape, dtype=torch.float32 if args.precision == "f32" else torch.float64).pin_memory(),
+             torch.empty(s.shape, dtype=torch.float32 if args.precision == "f32" else torch.float64).pin_memory())
+            for s in sims]
+    for s, (hp, hu) in zip(sims, host):
+        a, b = s.get_fields()
+        hp.numpy()[...] = a
+        hu.numpy()[...] = b
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s, (hp, hu) in zip(sims, host):
+        s.set_fields(hp.numpy(), hu.numpy())
+    steps(args.steps)
+    h2d = d2h = 0
+    for s, (hp, hu) in zip(sims, host):
+        a, b = s.get_fields()
+        hp.numpy()[...] = a
+        hu.numpy()[...] = b
+        h2d += hp.numel() * hp.element_size() * 2
+        d2h += hp.numel() * hp.element_size() * 2
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": cells * args.steps * world / e2e_s / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": f"orientation sweep 2D, 10 x {args.n}^2 instances (alpha0 = 0..45 deg), "
+                                       f"{args.scheme}, batched persistent launch + CUDA graph, observe every "
+                                       f"{OBS_EVERY} steps",
+                           "cells_per_gpu": cells, "l2": f"state {cells * 16 / 1e6:.0f} MB per step > 129 MB L2"},
+                "roofline": roof, "e2e": e2e, "clocks": clocks.summary(),
+                "gpu_launches": n_launch + 2 * len(sims) * (args.steps // OBS_EVERY)}
+        if world == 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(args.n, args.scheme)
+        print(json.dumps(line), flush=True)
+    group.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--scheme", default="SBAR21", choices=["SBAR21", "S21", "S10"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,192 @@
+/*
+ * pf.h -- C-ABI of the GB300 (sm_103a) library for the explicit time step of
+ * the quantitative binary-alloy phase-field model with the O(h^2)-isotropic
+ * finite differences of Ji, Molavi Tabrizi & Karma, arXiv:2110.12448.
+ *
+ * The model (Sec. 2.1, Eqs. PF_a and PF_b, isothermal: F1 = 1, F2 = U):
+ *   a_s^2 dpsi/dt = div J - sqrt2 phi a_s^2 |grad psi|^2
+ *                   + sqrt2 [phi - lambda (1 - phi^2) U],
+ *   J = a_s^2 grad psi + |grad psi|^2 a_s d a_s / d(grad psi),
+ *   (1 + k - (1-k) phi) dU/dt = D div[(1 - phi) grad U] + (anti-trapping)
+ *                   + [1 + (1-k) U] d phi/dt,
+ *   phi = tanh(psi / sqrt2)                                         (Eq. 1)
+ * with the cubic anisotropy a_s of Eq. anis_function evaluated in each
+ * grain's rotated crystal frame, explicit Euler in time (Sec. 3.3.1) and
+ * no-flux (cell-centred mirror) walls.
+ *
+ * Schemes (Sec. 3.3.1 and Sec. 6.2.1):
+ *   PF_S10      L_{1,0}, G_{1,0}, <10> divergence, standard anti-trapping
+ *   PF_S21      L_{2,1}, G_{2,1}, D~_{2,1}, standard anti-trapping A_{2,1}
+ *               with the 21-point |grad psi| of App. B
+ *   PF_SBAR21   L_{2,1}, G_{2,1}, D~_{2,1} for D and the approximated
+ *               anti-trapping of Eq. Anti_approx
+ *   PF_S100     3D <100> scheme with standard anti-trapping
+ *   PF_SBAR120  L_{1,2,0}, G_{1,2,0}, D~_{1,2,0} for D and Eq. Anti_approx
+ * The O(eps4) anisotropy terms use the <10>/<100> face shell (Sec. 2.2).
+ *
+ * Conventions for every entry point:
+ *   - return 0 (PF_OK) or a negative PF_ERR_* code; no exception crosses
+ *     the ABI; pf_status_string() names a code.
+ *   - fields are row-major with x fastest: index (k*ny + j)*nx + i; cell
+ *     (i,j,k) sits at (i h, j h, k h) in units of the interface width W.
+ *   - the library never allocates device memory.  The caller passes one
+ *     device buffer of pf_required_bytes() bytes (256-byte aligned) that
+ *     must outlive the handle, and a cudaStream_t (as void*) on which all
+ *     work of the handle is queued; NULL means the legacy default stream.
+ *   - host arrays are read or written during the call only (copied).
+ *   - a handle is used from one host thread at a time.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pf_sim pf_sim;
+typedef struct pf_group pf_group;
+
+typedef enum { PF_S10 = 0, PF_S21 = 1, PF_SBAR21 = 2, PF_S100 = 3, PF_SBAR120 = 4 } pf_scheme;
+typedef enum { PF_F32 = 0, PF_F64 = 1 } pf_precision;
+
+enum {
+    PF_OK = 0,
+    PF_ERR_INVALID = -1,   /* bad argument, size or parameter */
+    PF_ERR_BUDGET = -2,    /* caller buffer smaller than required */
+    PF_ERR_CUDA = -3,      /* a CUDA call failed (details: pf_last_cuda_error) */
+    PF_ERR_NONFINITE = -4, /* observe found NaN/Inf in psi or U */
+    PF_ERR_TIMEOUT = -5,   /* a bounded device wait gave up */
+    PF_ERR_STATE = -6      /* call not valid in the handle's state */
+};
+
+/* Problem statement (Sec. 2.1): grid, lattice spacing h (units of W), time
+ * step dt (units of tau0), partition coefficient k, anisotropy strength
+ * eps4, coupling lambda, diffusivity D (= a1 a2 W/d0), initial
+ * supersaturation U0, scheme, arithmetic precision of the fields, capacity
+ * of the grain table (>= 1) and of the seed list used by pf_init_seeds
+ * (0 = 64).  dt must not exceed the explicit-Euler bound
+ * 2 h^2 / (Lambda max(D, 1)), Lambda = 16/3 for the isotropic Laplacians,
+ * 8 for L_{1,0}, 12 for L_{1,0,0}.  Every axis needs at least 4 cells. */
+typedef struct {
+    int32_t dim, nx, ny, nz;
+    double h, dt, k, eps4, lambda, D, U0;
+    int32_t scheme;     /* pf_scheme */
+    int32_t precision;  /* pf_precision */
+    int32_t max_grains;
+    int32_t max_seeds;
+} pf_params;
+
+/* A spherical (circular in 2D) seed: centre (x, y, z) and radius r in units
+ * of W, and the grain it belongs to. */
+typedef struct {
+    double x, y, z, r;
+    int32_t grain;
+    int32_t reserved;
+} pf_seed;
+
+/* Observation (tip tracking of Sec. 3.3.2 and 6.2.2, solute integral of
+ * Eq. Supersaturation).  All reductions run in FP64 on the device. */
+typedef struct {
+    int64_t step;             /* steps taken by the handle */
+    double t;                 /* step * dt */
+    double tip[3];            /* tip position (NaN if no tip) */
+    double v_tip;             /* |tip - previous tip| / elapsed time; 0 on first call */
+    double angle_xy_deg;      /* growth angle in the xy plane, counter-clockwise from +y */
+    double angle_out_deg;     /* elevation of the tip above the xy plane (3D) */
+    double solute;            /* sum (1+k-(1-k)phi)(1+(1-k)U)/2 h^d */
+    double solid_fraction;    /* mean of (1+phi)/2 */
+    double tip_score;         /* projection of the tip on the growth axis */
+    int64_t tip_index;        /* linear index of the tip cell, -1 if none */
+    int32_t found;            /* 1 if a tip was found */
+    int32_t nonfinite;        /* number of cells with NaN/Inf psi or U */
+} pf_obs;
+
+/* Device bytes the caller must supply to pf_create for these parameters
+ * (0 if the parameters are invalid). */
+size_t pf_required_bytes(const pf_params* p);
+
+/* Create a simulation on caller-owned device memory dev_mem (bytes >=
+ * pf_required_bytes(p), 256-byte aligned) and stream.  Validates p (sizes,
+ * scheme vs dim, dt against the stability bound) and sets the grain table to
+ * one grain with the identity rotation, every cell to grain 0, psi = -1e3
+ * (liquid) and U = U0.  *out receives the handle. */
+int pf_create(const pf_params* p, void* dev_mem, size_t bytes, void* stream, pf_sim** out);
+
+/* Set n_grains (<= max_grains) crystal orientations.  rot9: n_grains row-major
+ * 3x3 matrices mapping crystal to lab coordinates (2D uses the upper-left
+ * 2x2); Sec. 2.1 imposes the orientation through such rotations.  centres3:
+ * n_grains reference points (x, y, z) used by pf_observe for the tip
+ * projection and growth angle, or NULL for the domain centre. */
+int pf_set_grains(pf_sim* s, int n_grains, const double* rot9, const double* centres3);
+
+/* psi = max over seeds of (r_s - |x - c_s|), the signed distance to the
+ * union of seeds; grain = grain of the seed attaining the maximum (ties: the
+ * lowest seed index); U = U0.  Computed in FP64 on the device. */
+int pf_init_seeds(pf_sim* s, int n_seeds, const pf_seed* seeds);
+
+/* Copy an explicit per-cell grain map (nx*ny*nz int16, values < n_grains). */
+int pf_set_grain_index(pf_sim* s, const int16_t* host_grain);
+int pf_get_grain_index(pf_sim* s, int16_t* host_grain);
+
+/* Advance n >= 0 explicit Euler steps, queued asynchronously on the stream
+ * (one fused kernel launch per step). */
+int pf_step(pf_sim* s, int64_t n);
+
+/* Synchronise the stream and observe grain g (0 <= g < n_grains) or, with
+ * g = -1, every cell with grain 0's centre and axes.  Tip: among cells of
+ * the grain with psi >= 0 whose neighbour along the lattice axis closest to
+ * the growth axis has psi < 0, the linearly interpolated psi = 0 crossing
+ * with the largest projection on the growth axis (the crystal axis with the
+ * largest +y component); ties go to the lowest cell index.  Returns
+ * PF_ERR_NONFINITE (with *out filled) when NaN/Inf cells exist. */
+int pf_observe(pf_sim* s, int grain, pf_obs* out);
+
+/* Checkpoint / restore of the current fields (nx*ny*nz elements of the
+ * handle's precision each) and of the step counter. */
+int pf_get_fields(pf_sim* s, void* psi_host, void* U_host);
+int pf_set_fields(pf_sim* s, const void* psi_host, const void* U_host);
+int pf_get_step(pf_sim* s, int64_t* step);
+int pf_set_step(pf_sim* s, int64_t step);
+
+/* Device addresses of the current psi, U (precision of the handle) and the
+ * int16 grain map; valid until the next pf_step / pf_group_step. */
+int pf_device_fields(pf_sim* s, void** psi, void** U, void** grain);
+
+/* Tile shape of the fused kernel (cells per block along x, and the number
+ * of rows (2D) or planes (3D) a block sweeps); 0 keeps the current value.
+ * Used by the autotuner.  block_x must be one of the compiled widths. */
+int pf_set_tile(pf_sim* s, int block_x, int block_y, int sweep);
+int pf_get_tile(pf_sim* s, int* block_x, int* block_y, int* sweep);
+
+int pf_destroy(pf_sim* s);
+const char* pf_status_string(int code);
+/* Text of the last CUDA error seen by any call (thread-local). */
+const char* pf_last_cuda_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Batching: many simulations stepped together by one persistent launch per  */
+/* (dimension, scheme, precision) class, optionally replayed from a CUDA     */
+/* graph.  The group owns no fields; members keep their own memory.          */
+/* ------------------------------------------------------------------------ */
+
+/* Device bytes for a group of up to max_instances members whose tiles total
+ * at most max_work work items (pf_group_work_items counts a member's). */
+size_t pf_group_required_bytes(int max_instances, int max_work);
+int pf_group_work_items(const pf_sim* s);
+int pf_group_create(int max_instances, int max_work, void* dev_mem, size_t bytes, void* stream, pf_group** out);
+/* Members must not be stepped on their own while in the group. */
+int pf_group_add(pf_group* g, pf_sim* s);
+int pf_group_remove(pf_group* g, pf_sim* s);
+/* Advance every member by n steps.  With use_graph != 0, even-length runs
+ * of launches are captured once per membership change and replayed. */
+int pf_group_step(pf_group* g, int64_t n, int use_graph);
+int pf_group_size(const pf_group* g);
+int pf_group_destroy(pf_group* g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

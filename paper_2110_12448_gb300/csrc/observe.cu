@@ -1,0 +1,174 @@
+// observe.cu -- FP64 reductions (solute integral of Eq. Supersaturation,
+// solid fraction, non-finite scan, tip tracking of Sec. 3.3.2 / 6.2.2) and
+// the seed initialisation, for sm_103a.
+//
+// Reductions are deterministic: a fixed grid of OBS_BLOCKS blocks walks the
+// cells grid-stride, each block reduces in a fixed tree order, and one block
+// combines the partials in index order.  The tip candidate is chosen by the
+// total order (larger projection, then smaller cell index), so it does not
+// depend on the reduction order.  Candidate positions and projections are
+// formed with explicitly rounded FP64 operations (no contraction) so that the
+// choice is reproducible on any FP64 implementation of the same formula.
+#include <cfloat>
+
+#include "pf_internal.cuh"
+
+namespace pf {
+namespace {
+
+constexpr double SQ2 = 1.41421356237309504880;
+
+__device__ __forceinline__ bool better(double s1, long long i1, double s2, long long i2) {
+    // is (s1, i1) preferred over (s2, i2)?
+    if (i2 < 0) return i1 >= 0;
+    if (i1 < 0) return false;
+    if (s1 > s2) return true;
+    if (s1 < s2) return false;
+    return i1 < i2;
+}
+
+__device__ __forceinline__ void combine(ObsPartial& a, const ObsPartial& b) {
+    a.solute += b.solute;
+    a.solid += b.solid;
+    a.nonfinite += b.nonfinite;
+    if (better(b.score, b.tip_index, a.score, a.tip_index)) {
+        a.score = b.score;
+        a.tip_index = b.tip_index;
+        a.tip[0] = b.tip[0];
+        a.tip[1] = b.tip[1];
+        a.tip[2] = b.tip[2];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(OBS_THREADS) k_observe(ObsArgs a, ObsPartial* __restrict__ partials) {
+    const T* __restrict__ psi = static_cast<const T*>(a.psi);
+    const T* __restrict__ U = static_cast<const T*>(a.U);
+    const long long nx = a.nx, ny = a.ny, nz = a.dim == 3 ? a.nz : 1;
+    const long long N = nx * ny * nz;
+    ObsPartial acc;
+    acc.solute = 0.0;
+    acc.solid = 0.0;
+    acc.nonfinite = 0;
+    acc.score = -DBL_MAX;
+    acc.tip_index = -1;
+    acc.tip[0] = acc.tip[1] = acc.tip[2] = 0.0;
+    acc.pad = 0.0;
+    const double k = a.k, omk = 1.0 - a.k;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const double ps = (double)psi[c], u = (double)U[c];
+        if (!isfinite(ps) || !isfinite(u)) {
+            acc.nonfinite += 1;
+            continue;
+        }
+        const double ph = tanh(ps / SQ2);
+        acc.solute += (1.0 + k - omk * ph) * (1.0 + omk * u) / 2.0;
+        acc.solid += (1.0 + ph) / 2.0;
+        if (a.grain_filter >= 0 && a.grain[c] != a.grain_filter) continue;
+        if (!(ps >= 0.0)) continue;
+        const long long i = c % nx, j = (c / nx) % ny, kk = c / (nx * ny);
+        long long ii = i, jj = j, kq = kk;
+        if (a.ea == 0) ii += a.es;
+        else if (a.ea == 1) jj += a.es;
+        else kq += a.es;
+        if (ii < 0 || jj < 0 || kq < 0 || ii >= nx || jj >= ny || kq >= nz) continue;
+        const double pn = (double)psi[(kq * ny + jj) * nx + ii];
+        if (!(pn < 0.0)) continue;
+        const double frac = __ddiv_rn(ps, __dsub_rn(ps, pn));
+        double p[3] = {__dmul_rn((double)i, a.h), __dmul_rn((double)j, a.h),
+                       a.dim == 3 ? __dmul_rn((double)kk, a.h) : 0.0};
+        p[a.ea] = __dadd_rn(p[a.ea], __dmul_rn((double)a.es * frac, a.h));
+        double sc = 0.0;
+        for (int q = 0; q < a.dim; ++q) sc = __dadd_rn(sc, __dmul_rn(__dsub_rn(p[q], a.cg[q]), a.d[q]));
+        if (better(sc, c, acc.score, acc.tip_index)) {
+            acc.score = sc;
+            acc.tip_index = c;
+            acc.tip[0] = p[0];
+            acc.tip[1] = p[1];
+            acc.tip[2] = p[2];
+        }
+    }
+    __shared__ ObsPartial sh[OBS_THREADS];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = OBS_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) combine(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(32) k_observe_finish(const ObsPartial* __restrict__ partials, int n,
+                                                       ObsPartial* __restrict__ out) {
+    if (threadIdx.x != 0) return;
+    ObsPartial acc = partials[0];
+    for (int b = 1; b < n; ++b) combine(acc, partials[b]);
+    *out = acc;
+}
+
+template <typename T>
+__global__ void k_init_seeds(int dim, int nx, int ny, int nz, double h, double U0, const SeedDev* __restrict__ seeds,
+                             int n_seeds, T* __restrict__ psi, T* __restrict__ U, int16_t* __restrict__ grain) {
+    const long long N = (long long)nx * ny * (dim == 3 ? nz : 1);
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const long long i = c % nx, j = (c / nx) % ny, k = c / ((long long)nx * ny);
+        const double x = __dmul_rn((double)i, h), y = __dmul_rn((double)j, h);
+        const double z = dim == 3 ? __dmul_rn((double)k, h) : 0.0;
+        double best = -DBL_MAX;
+        int bs = 0;
+        bool any = false;
+        for (int s = 0; s < n_seeds; ++s) {
+            const double dx = __dsub_rn(x, seeds[s].x), dy = __dsub_rn(y, seeds[s].y);
+            const double dz = dim == 3 ? __dsub_rn(z, seeds[s].z) : 0.0;
+            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            const double v = __dsub_rn(seeds[s].r, __dsqrt_rn(d2));
+            if (!any || v > best) {
+                best = v;
+                bs = s;
+                any = true;
+            }
+        }
+        psi[c] = (T)best;
+        U[c] = (T)U0;
+        grain[c] = (int16_t)seeds[bs].grain;
+    }
+}
+
+template <typename T> __global__ void k_fill(T* __restrict__ p, T v, long long n) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        p[c] = v;
+}
+
+}  // namespace
+
+cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* result, cudaStream_t st) {
+    if (a.prec == 0)
+        k_observe<float><<<OBS_BLOCKS, OBS_THREADS, 0, st>>>(a, partials);
+    else
+        k_observe<double><<<OBS_BLOCKS, OBS_THREADS, 0, st>>>(a, partials);
+    k_observe_finish<<<1, 32, 0, st>>>(partials, OBS_BLOCKS, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_seeds(int prec, int dim, int nx, int ny, int nz, double h, double U0, const SeedDev* seeds,
+                              int n_seeds, void* psi, void* U, int16_t* grain, cudaStream_t st) {
+    const int grid = 4 * 152, block = 256;
+    if (prec == 0)
+        k_init_seeds<float><<<grid, block, 0, st>>>(dim, nx, ny, nz, h, U0, seeds, n_seeds, static_cast<float*>(psi),
+                                                    static_cast<float*>(U), grain);
+    else
+        k_init_seeds<double><<<grid, block, 0, st>>>(dim, nx, ny, nz, h, U0, seeds, n_seeds,
+                                                     static_cast<double*>(psi), static_cast<double*>(U), grain);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(int prec, void* p, double v, long long n, cudaStream_t st) {
+    const int grid = 4 * 152, block = 256;
+    if (prec == 0)
+        k_fill<float><<<grid, block, 0, st>>>(static_cast<float*>(p), (float)v, n);
+    else
+        k_fill<double><<<grid, block, 0, st>>>(static_cast<double*>(p), v, n);
+    return cudaGetLastError();
+}
+
+}  // namespace pf

@@ -1,0 +1,726 @@
+// pf_api.cu -- the C-ABI of include/pf.h: parameter validation, layout of
+// the caller's device buffer, work lists, launches, observation and the
+// batching groups (one persistent launch per class, CUDA-graph replay).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pf.h"
+#include "pf_internal.cuh"
+
+using namespace pf;
+
+namespace {
+
+thread_local std::string g_last_cuda;
+
+int cuda_fail(cudaError_t e, const char* what) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    g_last_cuda = buf;
+    return PF_ERR_CUDA;
+}
+#define CK(call)                                       \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool valid_params(const pf_params* p) {
+    if (!p) return false;
+    if (p->dim != 2 && p->dim != 3) return false;
+    if (p->nx < 4 || p->ny < 4 || (p->dim == 3 && p->nz < 4)) return false;
+    if (p->nx > (1 << 20) || p->ny > (1 << 20) || (p->dim == 3 && p->nz > (1 << 14))) return false;
+    if (p->dim == 2 && !(p->scheme == PF_S10 || p->scheme == PF_S21 || p->scheme == PF_SBAR21)) return false;
+    if (p->dim == 3 && !(p->scheme == PF_S100 || p->scheme == PF_SBAR120)) return false;
+    if (p->precision != PF_F32 && p->precision != PF_F64) return false;
+    if (!(p->h > 0) || !(p->dt > 0) || !std::isfinite(p->h) || !std::isfinite(p->dt)) return false;
+    if (!(p->k > 0 && p->k < 1)) return false;
+    if (!(p->eps4 >= 0 && p->eps4 < 0.25)) return false;
+    if (!(p->D > 0) || !(p->lambda >= 0) || !std::isfinite(p->U0)) return false;
+    if (p->max_grains < 1 || p->max_grains > 32767 || p->max_seeds < 0 || p->max_seeds > (1 << 20)) return false;
+    // explicit Euler bound: dt <= 2 h^2 / (Lambda max(D, 1))
+    const bool iso = p->scheme == PF_S21 || p->scheme == PF_SBAR21 || p->scheme == PF_SBAR120;
+    const double lam = iso ? 16.0 / 3.0 : (p->dim == 2 ? 8.0 : 12.0);
+    const double bound = 2.0 * p->h * p->h / (lam * std::max(p->D, 1.0));
+    if (p->dt > bound) return false;
+    return true;
+}
+
+struct Layout {
+    size_t psi0, psi1, U0, U1, grain, rot, seeds, partials, result, work, rec, total;
+    size_t N;
+    int esz, max_seeds, max_work;
+};
+
+long long cells(const pf_params* p) { return (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1); }
+
+int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// capacity of the work list: the smallest tile any compiled shape produces
+int max_work_items(const pf_params* p) {
+    if (p->dim == 2) return cdiv(p->nx, 60) * cdiv(p->ny, 8);
+    return cdiv(p->nx, 12) * cdiv(p->ny, 4) * cdiv(p->nz, 4);
+}
+
+Layout layout(const pf_params* p) {
+    Layout L{};
+    L.N = (size_t)cells(p);
+    L.esz = p->precision == PF_F64 ? 8 : 4;
+    L.max_seeds = p->max_seeds > 0 ? p->max_seeds : 64;
+    L.max_work = max_work_items(p);
+    size_t o = 0;
+    auto take = [&](size_t n) {
+        size_t r = o;
+        o = align256(o + n);
+        return r;
+    };
+    L.psi0 = take(L.N * L.esz);
+    L.psi1 = take(L.N * L.esz);
+    L.U0 = take(L.N * L.esz);
+    L.U1 = take(L.N * L.esz);
+    L.grain = take(L.N * sizeof(int16_t));
+    L.rot = take((size_t)p->max_grains * 9 * L.esz);
+    L.seeds = take((size_t)L.max_seeds * sizeof(SeedDev));
+    L.partials = take((size_t)OBS_BLOCKS * sizeof(ObsPartial));
+    L.result = take(sizeof(ObsPartial));
+    L.work = take((size_t)L.max_work * sizeof(WorkItem));
+    L.rec = take(sizeof(InstRec));
+    L.total = o;
+    return L;
+}
+
+int g_num_sms = 0;
+int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 152;
+    }
+    return g_num_sms;
+}
+
+}  // namespace
+
+struct pf_sim {
+    pf_params p;
+    Layout L;
+    char* base;
+    cudaStream_t st;
+    void* psi[2];
+    void* U[2];
+    int16_t* grain;
+    void* rot;
+    SeedDev* seeds;
+    ObsPartial* partials;
+    ObsPartial* result;
+    WorkItem* work;
+    InstRec* rec;
+    int n_grains;
+    std::vector<double> rot_h, centres_h;
+    int64_t step;
+    int bx, by, sweep, n_work, grid;
+    bool work_dirty;
+    std::vector<WorkItem> work_h;
+    std::vector<int> have_prev;       // per grain + 1 (index 0 = global)
+    std::vector<double> prev;         // t, x, y, z per slot
+    pf_group* group;
+};
+
+namespace {
+
+void default_tile(pf_sim* s) {
+    if (s->p.dim == 2) {
+        s->bx = 128;
+        s->by = 1;
+        s->sweep = 64;
+    } else {
+        s->bx = 36;
+        s->by = 12;
+        s->sweep = 32;
+    }
+}
+
+void build_work(const pf_sim* s, int inst, std::vector<WorkItem>& out) {
+    const pf_params& p = s->p;
+    if (p.dim == 2) {
+        const int TX = s->bx - 4;
+        for (int y0 = 0; y0 < p.ny; y0 += s->sweep)
+            for (int x0 = 0; x0 < p.nx; x0 += TX) out.push_back(WorkItem{inst, x0, y0, 0, s->sweep, 0, 0, 0});
+    } else {
+        const int TX = s->bx - 4, TY = s->by - 4;
+        for (int z0 = 0; z0 < p.nz; z0 += s->sweep)
+            for (int y0 = 0; y0 < p.ny; y0 += TY)
+                for (int x0 = 0; x0 < p.nx; x0 += TX) out.push_back(WorkItem{inst, x0, y0, z0, s->sweep, 0, 0, 0});
+    }
+}
+
+int occupancy(const pf_sim* s) {
+    const int prec = s->p.precision == PF_F64 ? 1 : 0;
+    return s->p.dim == 2 ? occupancy_step2d(prec, s->p.scheme, s->bx) : occupancy_step3d(prec, s->p.scheme, s->bx, s->by);
+}
+
+InstRec make_rec(const pf_sim* s, int parity_offset) {
+    InstRec r{};
+    r.psi[0] = s->psi[0];
+    r.psi[1] = s->psi[1];
+    r.U[0] = s->U[0];
+    r.U[1] = s->U[1];
+    r.grain = s->grain;
+    r.rot = s->rot;
+    r.nx = s->p.nx;
+    r.ny = s->p.ny;
+    r.nz = s->p.dim == 3 ? s->p.nz : 1;
+    r.parity_offset = parity_offset;
+    r.h = s->p.h;
+    r.dt = s->p.dt;
+    r.k = s->p.k;
+    r.eps4 = s->p.eps4;
+    r.lambda = s->p.lambda;
+    r.D = s->p.D;
+    return r;
+}
+
+int upload_work(pf_sim* s) {
+    s->work_h.clear();
+    build_work(s, 0, s->work_h);
+    if ((int)s->work_h.size() > s->L.max_work) return PF_ERR_INVALID;
+    s->n_work = (int)s->work_h.size();
+    CK(cudaMemcpyAsync(s->work, s->work_h.data(), s->work_h.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s->st));
+    InstRec r = make_rec(s, 0);
+    CK(cudaMemcpyAsync(s->rec, &r, sizeof(r), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    const int occ = occupancy(s);
+    if (occ <= 0) return PF_ERR_INVALID;
+    s->grid = std::min(s->n_work, occ * num_sms());
+    s->work_dirty = false;
+    return PF_OK;
+}
+
+int upload_rot(pf_sim* s) {
+    const int n = s->n_grains;
+    if (s->p.precision == PF_F64) {
+        CK(cudaMemcpyAsync(s->rot, s->rot_h.data(), (size_t)n * 9 * sizeof(double), cudaMemcpyHostToDevice, s->st));
+        CK(cudaStreamSynchronize(s->st));
+    } else {
+        std::vector<float> f(s->rot_h.begin(), s->rot_h.end());
+        CK(cudaMemcpyAsync(s->rot, f.data(), (size_t)n * 9 * sizeof(float), cudaMemcpyHostToDevice, s->st));
+        CK(cudaStreamSynchronize(s->st));
+    }
+    return PF_OK;
+}
+
+bool launch_sim_step(const pf_sim* s, int launch_parity) {
+    const int prec = s->p.precision == PF_F64 ? 1 : 0;
+    if (s->p.dim == 2) return launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, launch_parity);
+    return launch_step3d(prec, s->p.scheme, s->bx, s->by, s->grid, s->st, s->work, s->n_work, s->rec, launch_parity);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pf_required_bytes(const pf_params* p) {
+    if (!valid_params(p)) return 0;
+    return layout(p).total;
+}
+
+int pf_create(const pf_params* p, void* dev_mem, size_t bytes, void* stream, pf_sim** out) {
+    if (!out) return PF_ERR_INVALID;
+    *out = nullptr;
+    if (!valid_params(p) || !dev_mem) return PF_ERR_INVALID;
+    if (((uintptr_t)dev_mem & 255) != 0) return PF_ERR_INVALID;
+    Layout L = layout(p);
+    if (bytes < L.total) return PF_ERR_BUDGET;
+    pf_sim* s = new (std::nothrow) pf_sim();
+    if (!s) return PF_ERR_INVALID;
+    s->p = *p;
+    if (s->p.dim == 2) s->p.nz = 1;
+    s->L = L;
+    s->base = static_cast<char*>(dev_mem);
+    s->st = static_cast<cudaStream_t>(stream);
+    s->psi[0] = s->base + L.psi0;
+    s->psi[1] = s->base + L.psi1;
+    s->U[0] = s->base + L.U0;
+    s->U[1] = s->base + L.U1;
+    s->grain = reinterpret_cast<int16_t*>(s->base + L.grain);
+    s->rot = s->base + L.rot;
+    s->seeds = reinterpret_cast<SeedDev*>(s->base + L.seeds);
+    s->partials = reinterpret_cast<ObsPartial*>(s->base + L.partials);
+    s->result = reinterpret_cast<ObsPartial*>(s->base + L.result);
+    s->work = reinterpret_cast<WorkItem*>(s->base + L.work);
+    s->rec = reinterpret_cast<InstRec*>(s->base + L.rec);
+    s->n_grains = 1;
+    s->rot_h.assign(9, 0.0);
+    s->rot_h[0] = s->rot_h[4] = s->rot_h[8] = 1.0;
+    s->centres_h.assign(3, 0.0);
+    s->centres_h[0] = (p->nx - 1) * 0.5 * p->h;
+    s->centres_h[1] = (p->ny - 1) * 0.5 * p->h;
+    s->centres_h[2] = p->dim == 3 ? (p->nz - 1) * 0.5 * p->h : 0.0;
+    s->step = 0;
+    s->group = nullptr;
+    s->have_prev.assign(2, 0);
+    s->prev.assign(8, 0.0);
+    default_tile(s);
+    int rc;
+    if ((rc = upload_rot(s)) != PF_OK) { delete s; return rc; }
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(s->grain, 0, L.N * sizeof(int16_t), s->st)) != cudaSuccess) { delete s; return cuda_fail(e, "memset grain"); }
+    const int prec = p->precision == PF_F64 ? 1 : 0;
+    if ((e = launch_fill(prec, s->psi[0], -1e3, (long long)L.N, s->st)) != cudaSuccess) { delete s; return cuda_fail(e, "fill psi"); }
+    if ((e = launch_fill(prec, s->U[0], p->U0, (long long)L.N, s->st)) != cudaSuccess) { delete s; return cuda_fail(e, "fill U"); }
+    if ((rc = upload_work(s)) != PF_OK) { delete s; return rc; }
+    *out = s;
+    return PF_OK;
+}
+
+int pf_set_grains(pf_sim* s, int n_grains, const double* rot9, const double* centres3) {
+    if (!s || !rot9 || n_grains < 1 || n_grains > s->p.max_grains) return PF_ERR_INVALID;
+    for (int i = 0; i < 9 * n_grains; ++i)
+        if (!std::isfinite(rot9[i])) return PF_ERR_INVALID;
+    s->n_grains = n_grains;
+    s->rot_h.assign(rot9, rot9 + 9 * n_grains);
+    s->centres_h.assign(3 * n_grains, 0.0);
+    for (int g = 0; g < n_grains; ++g) {
+        if (centres3) {
+            for (int a = 0; a < 3; ++a) s->centres_h[3 * g + a] = centres3[3 * g + a];
+        } else {
+            s->centres_h[3 * g + 0] = (s->p.nx - 1) * 0.5 * s->p.h;
+            s->centres_h[3 * g + 1] = (s->p.ny - 1) * 0.5 * s->p.h;
+            s->centres_h[3 * g + 2] = s->p.dim == 3 ? (s->p.nz - 1) * 0.5 * s->p.h : 0.0;
+        }
+    }
+    s->have_prev.assign(n_grains + 1, 0);
+    s->prev.assign(4 * (n_grains + 1), 0.0);
+    return upload_rot(s);
+}
+
+int pf_init_seeds(pf_sim* s, int n_seeds, const pf_seed* seeds) {
+    if (!s || !seeds || n_seeds < 1 || n_seeds > s->L.max_seeds) return PF_ERR_INVALID;
+    std::vector<SeedDev> h(n_seeds);
+    for (int i = 0; i < n_seeds; ++i) {
+        if (seeds[i].grain < 0 || seeds[i].grain >= s->n_grains) return PF_ERR_INVALID;
+        if (!std::isfinite(seeds[i].x) || !std::isfinite(seeds[i].y) || !std::isfinite(seeds[i].z) ||
+            !std::isfinite(seeds[i].r))
+            return PF_ERR_INVALID;
+        h[i] = SeedDev{seeds[i].x, seeds[i].y, s->p.dim == 3 ? seeds[i].z : 0.0, seeds[i].r, seeds[i].grain, 0};
+    }
+    CK(cudaMemcpyAsync(s->seeds, h.data(), n_seeds * sizeof(SeedDev), cudaMemcpyHostToDevice, s->st));
+    const int cur = (int)(s->step & 1);
+    CK(launch_init_seeds(s->p.precision == PF_F64 ? 1 : 0, s->p.dim, s->p.nx, s->p.ny, s->p.nz, s->p.h, s->p.U0, s->seeds,
+                         n_seeds, s->psi[cur], s->U[cur], s->grain, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return PF_OK;
+}
+
+int pf_set_grain_index(pf_sim* s, const int16_t* g) {
+    if (!s || !g) return PF_ERR_INVALID;
+    for (size_t c = 0; c < s->L.N; ++c)
+        if (g[c] < 0 || g[c] >= s->n_grains) return PF_ERR_INVALID;
+    CK(cudaMemcpyAsync(s->grain, g, s->L.N * sizeof(int16_t), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return PF_OK;
+}
+
+int pf_get_grain_index(pf_sim* s, int16_t* g) {
+    if (!s || !g) return PF_ERR_INVALID;
+    CK(cudaMemcpyAsync(g, s->grain, s->L.N * sizeof(int16_t), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return PF_OK;
+}
+
+int pf_step(pf_sim* s, int64_t n) {
+    if (!s || n < 0) return PF_ERR_INVALID;
+    if (s->group) return PF_ERR_STATE;
+    if (s->work_dirty) {
+        int rc = upload_work(s);
+        if (rc != PF_OK) return rc;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (!launch_sim_step(s, (int)((s->step + i) & 1))) return PF_ERR_INVALID;
+    }
+    if (n > 0) CK(cudaGetLastError());
+    s->step += n;
+    return PF_OK;
+}
+
+int pf_observe(pf_sim* s, int grain, pf_obs* out) {
+    if (!s || !out || grain < -1 || grain >= s->n_grains) return PF_ERR_INVALID;
+    const int dim = s->p.dim;
+    const int gg = grain < 0 ? 0 : grain;
+    const double* R = &s->rot_h[9 * gg];
+    // growth axis: crystal axis (+- column of R) with the largest y component
+    double d[3] = {0, 0, 0}, best = -INFINITY;
+    for (int a = 0; a < dim; ++a)
+        for (int sg = 1; sg >= -1; sg -= 2) {
+            const double yc = sg * R[3 + a];
+            if (yc > best) {
+                best = yc;
+                for (int q = 0; q < 3; ++q) d[q] = q < dim ? sg * R[q * 3 + a] : 0.0;
+            }
+        }
+    int ea = 0;
+    for (int a = 1; a < dim; ++a)
+        if (std::fabs(d[a]) > std::fabs(d[ea])) ea = a;
+    const int es = d[ea] >= 0 ? 1 : -1;
+    ObsArgs a{};
+    const int cur = (int)(s->step & 1);
+    a.psi = s->psi[cur];
+    a.U = s->U[cur];
+    a.grain = s->grain;
+    a.prec = s->p.precision == PF_F64 ? 1 : 0;
+    a.dim = dim;
+    a.nx = s->p.nx;
+    a.ny = s->p.ny;
+    a.nz = dim == 3 ? s->p.nz : 1;
+    a.grain_filter = grain;
+    a.h = s->p.h;
+    a.k = s->p.k;
+    for (int q = 0; q < 3; ++q) {
+        a.cg[q] = s->centres_h[3 * gg + q];
+        a.d[q] = d[q];
+    }
+    a.ea = ea;
+    a.es = es;
+    CK(launch_observe(a, s->partials, s->result, s->st));
+    ObsPartial r;
+    CK(cudaMemcpyAsync(&r, s->result, sizeof(r), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    std::memset(out, 0, sizeof(*out));
+    out->step = s->step;
+    out->t = (double)s->step * s->p.dt;
+    const double hd = dim == 3 ? s->p.h * s->p.h * s->p.h : s->p.h * s->p.h;
+    out->solute = r.solute * hd;
+    out->solid_fraction = r.solid / (double)s->L.N;
+    out->nonfinite = (int32_t)r.nonfinite;
+    out->found = r.tip_index >= 0 ? 1 : 0;
+    out->tip_index = r.tip_index;
+    out->tip_score = r.tip_index >= 0 ? r.score : -INFINITY;
+    const int slot = grain + 1;
+    if (r.tip_index >= 0) {
+        for (int q = 0; q < 3; ++q) out->tip[q] = r.tip[q];
+        const double rx = r.tip[0] - a.cg[0], ry = r.tip[1] - a.cg[1], rz = dim == 3 ? r.tip[2] - a.cg[2] : 0.0;
+        out->angle_xy_deg = std::atan2(-rx, ry) * (180.0 / 3.14159265358979323846);
+        out->angle_out_deg = std::atan2(rz, std::sqrt(rx * rx + ry * ry)) * (180.0 / 3.14159265358979323846);
+        if (s->have_prev[slot] && out->t > s->prev[4 * slot]) {
+            double dd = 0.0;
+            for (int q = 0; q < 3; ++q) dd += (r.tip[q] - s->prev[4 * slot + 1 + q]) * (r.tip[q] - s->prev[4 * slot + 1 + q]);
+            out->v_tip = std::sqrt(dd) / (out->t - s->prev[4 * slot]);
+        }
+        s->have_prev[slot] = 1;
+        s->prev[4 * slot] = out->t;
+        for (int q = 0; q < 3; ++q) s->prev[4 * slot + 1 + q] = r.tip[q];
+    } else {
+        out->tip[0] = out->tip[1] = out->tip[2] = NAN;
+        out->angle_xy_deg = out->angle_out_deg = NAN;
+    }
+    return r.nonfinite > 0 ? PF_ERR_NONFINITE : PF_OK;
+}
+
+int pf_get_fields(pf_sim* s, void* psi_host, void* U_host) {
+    if (!s || (!psi_host && !U_host)) return PF_ERR_INVALID;
+    const int cur = (int)(s->step & 1);
+    const size_t b = s->L.N * s->L.esz;
+    if (psi_host) CK(cudaMemcpyAsync(psi_host, s->psi[cur], b, cudaMemcpyDeviceToHost, s->st));
+    if (U_host) CK(cudaMemcpyAsync(U_host, s->U[cur], b, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return PF_OK;
+}
+
+int pf_set_fields(pf_sim* s, const void* psi_host, const void* U_host) {
+    if (!s || (!psi_host && !U_host)) return PF_ERR_INVALID;
+    const int cur = (int)(s->step & 1);
+    const size_t b = s->L.N * s->L.esz;
+    if (psi_host) CK(cudaMemcpyAsync(s->psi[cur], psi_host, b, cudaMemcpyHostToDevice, s->st));
+    if (U_host) CK(cudaMemcpyAsync(s->U[cur], U_host, b, cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return PF_OK;
+}
+
+int pf_get_step(pf_sim* s, int64_t* step) {
+    if (!s || !step) return PF_ERR_INVALID;
+    *step = s->step;
+    return PF_OK;
+}
+
+int pf_set_step(pf_sim* s, int64_t step) {
+    if (!s || step < 0) return PF_ERR_INVALID;
+    if (s->group) return PF_ERR_STATE;
+    if ((step & 1) != (s->step & 1)) {
+        // keep the current fields where the new counter expects them
+        const int from = (int)(s->step & 1), to = from ^ 1;
+        const size_t b = s->L.N * s->L.esz;
+        CK(cudaMemcpyAsync(s->psi[to], s->psi[from], b, cudaMemcpyDeviceToDevice, s->st));
+        CK(cudaMemcpyAsync(s->U[to], s->U[from], b, cudaMemcpyDeviceToDevice, s->st));
+        CK(cudaStreamSynchronize(s->st));
+    }
+    s->step = step;
+    std::fill(s->have_prev.begin(), s->have_prev.end(), 0);
+    return PF_OK;
+}
+
+int pf_device_fields(pf_sim* s, void** psi, void** U, void** grain) {
+    if (!s) return PF_ERR_INVALID;
+    const int cur = (int)(s->step & 1);
+    if (psi) *psi = s->psi[cur];
+    if (U) *U = s->U[cur];
+    if (grain) *grain = s->grain;
+    return PF_OK;
+}
+
+int pf_set_tile(pf_sim* s, int block_x, int block_y, int sweep) {
+    if (!s) return PF_ERR_INVALID;
+    if (s->group) return PF_ERR_STATE;
+    const int obx = s->bx, oby = s->by, osw = s->sweep;
+    if (block_x) s->bx = block_x;
+    if (block_y) s->by = block_y;
+    if (sweep) s->sweep = sweep;
+    bool ok = s->sweep >= 8 && s->sweep <= 1 << 20 && occupancy(s) > 0;
+    if (ok) {
+        std::vector<WorkItem> tmp;
+        build_work(s, 0, tmp);
+        ok = (int)tmp.size() <= s->L.max_work;
+    }
+    if (!ok) {
+        s->bx = obx;
+        s->by = oby;
+        s->sweep = osw;
+        return PF_ERR_INVALID;
+    }
+    return upload_work(s);
+}
+
+int pf_get_tile(pf_sim* s, int* block_x, int* block_y, int* sweep) {
+    if (!s) return PF_ERR_INVALID;
+    if (block_x) *block_x = s->bx;
+    if (block_y) *block_y = s->by;
+    if (sweep) *sweep = s->sweep;
+    return PF_OK;
+}
+
+int pf_destroy(pf_sim* s) {
+    if (!s) return PF_ERR_INVALID;
+    if (s->group) return PF_ERR_STATE;
+    cudaStreamSynchronize(s->st);
+    delete s;
+    return PF_OK;
+}
+
+const char* pf_status_string(int code) {
+    switch (code) {
+        case PF_OK: return "ok";
+        case PF_ERR_INVALID: return "invalid argument";
+        case PF_ERR_BUDGET: return "device buffer too small";
+        case PF_ERR_CUDA: return "CUDA error";
+        case PF_ERR_NONFINITE: return "non-finite values in the fields";
+        case PF_ERR_TIMEOUT: return "device wait timed out";
+        case PF_ERR_STATE: return "call not valid in this state";
+        default: return "unknown status";
+    }
+}
+
+const char* pf_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// groups
+// ---------------------------------------------------------------------------
+struct pf_group {
+    int max_inst, max_work;
+    cudaStream_t st;
+    char* base;
+    InstRec* recs;
+    WorkItem* work;
+    std::vector<pf_sim*> members;
+    int64_t launches;
+    bool dirty;
+    struct Cls {
+        int dim, scheme, prec, bx, by, w0, n, grid;
+    };
+    std::vector<Cls> classes;
+    cudaGraphExec_t graph;
+    int graph_len;
+    int graph_parity;
+};
+
+namespace {
+
+int group_rebuild(pf_group* g) {
+    std::vector<InstRec> recs;
+    std::vector<WorkItem> work;
+    g->classes.clear();
+    // sort members into classes
+    std::vector<int> order(g->members.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    auto key = [&](int i) {
+        const pf_sim* s = g->members[i];
+        return ((long long)s->p.dim << 40) | ((long long)s->p.scheme << 32) | ((long long)s->p.precision << 24) |
+               ((long long)s->bx << 12) | (long long)s->by;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
+    for (size_t m = 0; m < g->members.size(); ++m) {
+        const pf_sim* s = g->members[m];
+        recs.push_back(make_rec(s, (int)((s->step ^ g->launches) & 1)));
+    }
+    long long prev = -1;
+    for (int i : order) {
+        const pf_sim* s = g->members[i];
+        const long long k = key(i);
+        if (k != prev) {
+            pf_group::Cls c{s->p.dim, s->p.scheme, s->p.precision == PF_F64 ? 1 : 0, s->bx, s->by, (int)work.size(), 0, 0};
+            g->classes.push_back(c);
+            prev = k;
+        }
+        build_work(s, i, work);
+        g->classes.back().n = (int)work.size() - g->classes.back().w0;
+    }
+    if ((int)work.size() > g->max_work) return PF_ERR_BUDGET;
+    for (auto& c : g->classes) {
+        int occ = c.dim == 2 ? occupancy_step2d(c.prec, c.scheme, c.bx) : occupancy_step3d(c.prec, c.scheme, c.bx, c.by);
+        if (occ <= 0) return PF_ERR_INVALID;
+        c.grid = std::min(c.n, occ * num_sms());
+    }
+    if (!recs.empty()) CK(cudaMemcpyAsync(g->recs, recs.data(), recs.size() * sizeof(InstRec), cudaMemcpyHostToDevice, g->st));
+    if (!work.empty()) CK(cudaMemcpyAsync(g->work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    if (g->graph) {
+        cudaGraphExecDestroy(g->graph);
+        g->graph = nullptr;
+    }
+    g->dirty = false;
+    return PF_OK;
+}
+
+bool group_launch_once(pf_group* g, int launch_parity) {
+    for (const auto& c : g->classes) {
+        if (c.n == 0) continue;
+        bool ok = c.dim == 2 ? launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs, launch_parity)
+                             : launch_step3d(c.prec, c.scheme, c.bx, c.by, c.grid, g->st, g->work + c.w0, c.n, g->recs,
+                                             launch_parity);
+        if (!ok) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pf_group_required_bytes(int max_instances, int max_work) {
+    if (max_instances < 1 || max_work < 1) return 0;
+    return align256((size_t)max_instances * sizeof(InstRec)) + align256((size_t)max_work * sizeof(WorkItem));
+}
+
+int pf_group_work_items(const pf_sim* s) {
+    if (!s) return PF_ERR_INVALID;
+    std::vector<WorkItem> tmp;
+    build_work(s, 0, tmp);
+    return (int)tmp.size();
+}
+
+int pf_group_create(int max_instances, int max_work, void* dev_mem, size_t bytes, void* stream, pf_group** out) {
+    if (!out) return PF_ERR_INVALID;
+    *out = nullptr;
+    if (max_instances < 1 || max_work < 1 || !dev_mem || ((uintptr_t)dev_mem & 255)) return PF_ERR_INVALID;
+    if (bytes < pf_group_required_bytes(max_instances, max_work)) return PF_ERR_BUDGET;
+    pf_group* g = new (std::nothrow) pf_group();
+    if (!g) return PF_ERR_INVALID;
+    g->max_inst = max_instances;
+    g->max_work = max_work;
+    g->st = static_cast<cudaStream_t>(stream);
+    g->base = static_cast<char*>(dev_mem);
+    g->recs = reinterpret_cast<InstRec*>(g->base);
+    g->work = reinterpret_cast<WorkItem*>(g->base + align256((size_t)max_instances * sizeof(InstRec)));
+    g->launches = 0;
+    g->dirty = true;
+    g->graph = nullptr;
+    g->graph_len = 0;
+    g->graph_parity = 0;
+    *out = g;
+    return PF_OK;
+}
+
+int pf_group_add(pf_group* g, pf_sim* s) {
+    if (!g || !s) return PF_ERR_INVALID;
+    if (s->group) return PF_ERR_STATE;
+    if ((int)g->members.size() >= g->max_inst) return PF_ERR_BUDGET;
+    if (s->work_dirty) {
+        int rc = upload_work(s);
+        if (rc != PF_OK) return rc;
+    }
+    CK(cudaStreamSynchronize(s->st));
+    g->members.push_back(s);
+    s->group = g;
+    g->dirty = true;
+    return PF_OK;
+}
+
+int pf_group_remove(pf_group* g, pf_sim* s) {
+    if (!g || !s || s->group != g) return PF_ERR_INVALID;
+    CK(cudaStreamSynchronize(g->st));
+    g->members.erase(std::find(g->members.begin(), g->members.end(), s));
+    s->group = nullptr;
+    g->dirty = true;
+    return PF_OK;
+}
+
+int pf_group_step(pf_group* g, int64_t n, int use_graph) {
+    if (!g || n < 0) return PF_ERR_INVALID;
+    if (g->members.empty() || n == 0) return PF_OK;
+    if (g->dirty) {
+        int rc = group_rebuild(g);
+        if (rc != PF_OK) return rc;
+    }
+    int64_t done = 0;
+    const int GL = 16;  // launches per graph replay (even)
+    if (use_graph && n >= GL) {
+        if ((g->launches & 1) != 0) {
+            if (!group_launch_once(g, 1)) return PF_ERR_INVALID;
+            ++done;
+        }
+        if (!g->graph) {
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal));
+            bool ok = true;
+            for (int i = 0; i < GL && ok; ++i) ok = group_launch_once(g, i & 1);
+            cudaError_t e = cudaStreamEndCapture(g->st, &graph);
+            if (!ok) return PF_ERR_INVALID;
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&g->graph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            g->graph_len = GL;
+        }
+        while (n - done >= GL) {
+            CK(cudaGraphLaunch(g->graph, g->st));
+            done += GL;
+        }
+    }
+    for (; done < n; ++done)
+        if (!group_launch_once(g, (int)((g->launches + done) & 1))) return PF_ERR_INVALID;
+    CK(cudaGetLastError());
+    g->launches += n;
+    for (pf_sim* s : g->members) s->step += n;
+    return PF_OK;
+}
+
+int pf_group_size(const pf_group* g) { return g ? (int)g->members.size() : PF_ERR_INVALID; }
+
+int pf_group_destroy(pf_group* g) {
+    if (!g) return PF_ERR_INVALID;
+    cudaStreamSynchronize(g->st);
+    for (pf_sim* s : g->members) s->group = nullptr;
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    delete g;
+    return PF_OK;
+}
+
+}  // extern "C"

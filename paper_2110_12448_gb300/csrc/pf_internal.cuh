@@ -1,0 +1,85 @@
+// pf_internal.cuh -- device-side records shared by the kernels and the C-ABI
+// layer of the sm_103a phase-field library.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pf {
+
+// Scheme identifiers (values of pf_scheme in include/pf.h).
+enum : int { S10 = 0, S21 = 1, SBAR21 = 2, S100 = 3, SBAR120 = 4 };
+
+// One simulation as the fused kernels see it.  psi/U hold the two time
+// levels; the current level of an instance in a launch is
+// parity_offset ^ launch_parity.
+struct InstRec {
+    void* psi[2];
+    void* U[2];
+    const int16_t* grain;  // per-cell grain index
+    const void* rot;       // n_grains x 9, crystal -> lab, in the field precision
+    int32_t nx, ny, nz, parity_offset;
+    double h, dt, k, eps4, lambda, D;
+};
+
+// A unit of work: one block sweeps `ext` rows (2D) or planes (3D) starting
+// at (x0, y0, z0) of instance `inst`.
+struct WorkItem {
+    int32_t inst, x0, y0, z0, ext, pad0, pad1, pad2;
+};
+
+// Guard on |grad psi|^2 h^2 below which the interface normal is undefined:
+// a_s = 1, anisotropic flux 0, anti-trapping flux 0.
+template <typename T> struct Guard;
+template <> struct Guard<float> { static constexpr float v = 1e-12f; };
+template <> struct Guard<double> { static constexpr double v = 1e-20; };
+
+// Cell-centred mirror of an index into [0, n): -1 -> 0, -2 -> 1, n -> n-1,
+// n+1 -> n-2.  Values further out (never consumed) are clamped in range.
+__device__ __forceinline__ int mirror_idx(int i, int n) {
+    i = i < 0 ? -1 - i : i;
+    i = i >= n ? 2 * n - 1 - i : i;
+    i = i < 0 ? 0 : i;
+    return i;
+}
+
+// Launchers (defined in step2d.cu / step3d.cu).  prec: 0 float, 1 double.
+// Return false if (prec, scheme, block) has no compiled kernel.
+bool launch_step2d(int prec, int scheme, int bx, int grid, cudaStream_t st, const WorkItem* work, int n_work,
+                   const InstRec* recs, int launch_parity);
+bool launch_step3d(int prec, int scheme, int bx, int by, int grid, cudaStream_t st, const WorkItem* work,
+                   int n_work, const InstRec* recs, int launch_parity);
+// Blocks of the fused kernel that fit on one SM (0 if not compiled).
+int occupancy_step2d(int prec, int scheme, int bx);
+int occupancy_step3d(int prec, int scheme, int bx, int by);
+
+// Observation / initialisation kernels (observe.cu).
+struct ObsPartial {
+    double solute, solid, score;
+    long long tip_index;
+    long long nonfinite;
+    double tip[3];
+    double pad;
+};
+struct ObsArgs {
+    const void* psi;
+    const void* U;
+    const int16_t* grain;
+    int prec, dim, nx, ny, nz, grain_filter;
+    double h, k;
+    double cg[3], d[3];
+    int ea, es;
+};
+constexpr int OBS_BLOCKS = 304;  // 2 x 152 SMs
+constexpr int OBS_THREADS = 256;
+cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* result, cudaStream_t st);
+
+struct SeedDev {
+    double x, y, z, r;
+    int32_t grain, pad;
+};
+cudaError_t launch_init_seeds(int prec, int dim, int nx, int ny, int nz, double h, double U0, const SeedDev* seeds,
+                              int n_seeds, void* psi, void* U, int16_t* grain, cudaStream_t st);
+cudaError_t launch_fill(int prec, void* p, double v, long long n, cudaStream_t st);
+
+}  // namespace pf

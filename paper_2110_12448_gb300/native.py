@@ -1,0 +1,304 @@
+"""ctypes binding of ``libpf.so`` (the C-ABI declared in ``include/pf.h``).
+
+Argument marshalling only: every step of the path runs in the library's
+CUDA kernels.  PyTorch supplies the device buffers (``torch.empty`` of
+``pf_required_bytes``) and the stream.  There is no CPU fallback: if the
+library is missing, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+SCHEMES = {"S10": 0, "S21": 1, "SBAR21": 2, "S100": 3, "SBAR120": 4}
+PRECISIONS = {"f32": 0, "f64": 1}
+PF_OK, PF_ERR_INVALID, PF_ERR_BUDGET, PF_ERR_CUDA, PF_ERR_NONFINITE, PF_ERR_TIMEOUT, PF_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+
+
+class PfError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what}: {code} ({status_string(code)})"
+        if code == PF_ERR_CUDA:
+            msg += f" [{lib().pf_last_cuda_error().decode()}]"
+        super().__init__(msg)
+
+
+class Params(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("h", C.c_double), ("dt", C.c_double), ("k", C.c_double), ("eps4", C.c_double),
+                ("lam", C.c_double), ("D", C.c_double), ("U0", C.c_double),
+                ("scheme", C.c_int32), ("precision", C.c_int32), ("max_grains", C.c_int32),
+                ("max_seeds", C.c_int32)]
+
+
+class Seed(C.Structure):
+    _fields_ = [("x", C.c_double), ("y", C.c_double), ("z", C.c_double), ("r", C.c_double),
+                ("grain", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Obs(C.Structure):
+    _fields_ = [("step", C.c_int64), ("t", C.c_double), ("tip", C.c_double * 3), ("v_tip", C.c_double),
+                ("angle_xy_deg", C.c_double), ("angle_out_deg", C.c_double), ("solute", C.c_double),
+                ("solid_fraction", C.c_double), ("tip_score", C.c_double), ("tip_index", C.c_int64),
+                ("found", C.c_int32), ("nonfinite", C.c_int32)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libpf.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libpf.so missing at {path}: the CUDA library is required (no CPU fallback)")
+            L = C.CDLL(path)
+            vp, i64 = C.c_void_p, C.c_int64
+            P = C.POINTER
+            sig = {
+                "pf_required_bytes": (C.c_size_t, [P(Params)]),
+                "pf_create": (C.c_int, [P(Params), vp, C.c_size_t, vp, P(vp)]),
+                "pf_set_grains": (C.c_int, [vp, C.c_int, P(C.c_double), P(C.c_double)]),
+                "pf_init_seeds": (C.c_int, [vp, C.c_int, P(Seed)]),
+                "pf_set_grain_index": (C.c_int, [vp, P(C.c_int16)]),
+                "pf_get_grain_index": (C.c_int, [vp, P(C.c_int16)]),
+                "pf_step": (C.c_int, [vp, i64]),
+                "pf_observe": (C.c_int, [vp, C.c_int, P(Obs)]),
+                "pf_get_fields": (C.c_int, [vp, vp, vp]),
+                "pf_set_fields": (C.c_int, [vp, vp, vp]),
+                "pf_get_step": (C.c_int, [vp, P(i64)]),
+                "pf_set_step": (C.c_int, [vp, i64]),
+                "pf_device_fields": (C.c_int, [vp, P(vp), P(vp), P(vp)]),
+                "pf_set_tile": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
+                "pf_get_tile": (C.c_int, [vp, P(C.c_int), P(C.c_int), P(C.c_int)]),
+                "pf_destroy": (C.c_int, [vp]),
+                "pf_status_string": (C.c_char_p, [C.c_int]),
+                "pf_last_cuda_error": (C.c_char_p, []),
+                "pf_group_required_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+                "pf_group_work_items": (C.c_int, [vp]),
+                "pf_group_create": (C.c_int, [C.c_int, C.c_int, vp, C.c_size_t, vp, P(vp)]),
+                "pf_group_add": (C.c_int, [vp, vp]),
+                "pf_group_remove": (C.c_int, [vp, vp]),
+                "pf_group_step": (C.c_int, [vp, i64, C.c_int]),
+                "pf_group_size": (C.c_int, [vp]),
+                "pf_group_destroy": (C.c_int, [vp]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().pf_status_string(int(code)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != PF_OK:
+        raise PfError(rc, what)
+
+
+def make_params(dim, nx, ny, nz=1, h=0.8, dt=0.02, k=0.15, eps4=0.02, lam=10.0, D=None, U0=-0.55,
+                scheme="SBAR21", precision="f32", max_grains=1, max_seeds=0) -> Params:
+    if D is None:
+        D = 0.6267 * lam
+    return Params(int(dim), int(nx), int(ny), int(nz if dim == 3 else 1), float(h), float(dt), float(k), float(eps4),
+                  float(lam), float(D), float(U0), SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
+                  PRECISIONS[precision] if isinstance(precision, str) else int(precision), int(max_grains),
+                  int(max_seeds))
+
+
+def required_bytes(p: Params) -> int:
+    return int(lib().pf_required_bytes(C.byref(p)))
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return int(getattr(stream, "cuda_stream", stream) or 0)
+
+
+class Sim:
+    """One simulation on caller-owned (torch) device memory."""
+
+    def __init__(self, p: Params, stream=None, device="cuda"):
+        import torch
+        self.p = p
+        self.np_dtype = np.float64 if p.precision == 1 else np.float32
+        n = required_bytes(p)
+        if n == 0:
+            raise PfError(PF_ERR_INVALID, "pf_required_bytes")
+        self.nbytes = n
+        self.mem = torch.empty(n, dtype=torch.uint8, device=device)
+        self.stream = stream
+        self._st = _stream_handle(stream)
+        h = C.c_void_p()
+        _check(lib().pf_create(C.byref(p), C.c_void_p(self.mem.data_ptr()), n, C.c_void_p(self._st), C.byref(h)),
+               "pf_create")
+        self.h = h
+        self.shape = (p.nz, p.ny, p.nx) if p.dim == 3 else (p.ny, p.nx)
+
+    @classmethod
+    def from_workload(cls, w, precision="f32", scheme=None, stream=None, init=True):
+        p = make_params(w.dim, w.nx, w.ny, w.nz, w.h, w.dt, w.k, w.eps4, w.lam, w.D, w.U0, scheme or w.scheme,
+                        precision, max_grains=max(1, w.n_grains), max_seeds=max(1, len(w.seeds)))
+        s = cls(p, stream=stream)
+        s.set_grains(w.rots, w.centres)
+        if init:
+            s.init_seeds(w.seeds, w.seed_grain)
+        return s
+
+    # -- configuration -------------------------------------------------
+    def set_grains(self, rots, centres=None):
+        r = np.ascontiguousarray(rots, dtype=np.float64).reshape(-1, 9)
+        c = None if centres is None else np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+        _check(lib().pf_set_grains(self.h, r.shape[0], r.ctypes.data_as(C.POINTER(C.c_double)),
+                                   None if c is None else c.ctypes.data_as(C.POINTER(C.c_double))), "pf_set_grains")
+
+    def init_seeds(self, seeds, seed_grain):
+        s = np.asarray(seeds, dtype=np.float64).reshape(-1, 4)
+        g = np.asarray(seed_grain).reshape(-1)
+        arr = (Seed * len(s))()
+        for i in range(len(s)):
+            arr[i] = Seed(s[i, 0], s[i, 1], s[i, 2], s[i, 3], int(g[i]), 0)
+        _check(lib().pf_init_seeds(self.h, len(s), arr), "pf_init_seeds")
+
+    def set_grain_index(self, g):
+        g = np.ascontiguousarray(g, dtype=np.int16).reshape(self.shape)
+        _check(lib().pf_set_grain_index(self.h, g.ctypes.data_as(C.POINTER(C.c_int16))), "pf_set_grain_index")
+
+    def get_grain_index(self):
+        g = np.zeros(self.shape, np.int16)
+        _check(lib().pf_get_grain_index(self.h, g.ctypes.data_as(C.POINTER(C.c_int16))), "pf_get_grain_index")
+        return g
+
+    def set_tile(self, bx=0, by=0, sweep=0):
+        _check(lib().pf_set_tile(self.h, int(bx), int(by), int(sweep)), "pf_set_tile")
+
+    def get_tile(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().pf_get_tile(self.h, C.byref(a), C.byref(b), C.byref(c)), "pf_get_tile")
+        return a.value, b.value, c.value
+
+    # -- stepping and observation --------------------------------------
+    def step(self, n: int = 1):
+        _check(lib().pf_step(self.h, int(n)), "pf_step")
+
+    def observe(self, grain: int = -1, allow_nonfinite=False) -> dict:
+        o = Obs()
+        rc = lib().pf_observe(self.h, int(grain), C.byref(o))
+        if rc != PF_OK and not (allow_nonfinite and rc == PF_ERR_NONFINITE):
+            raise PfError(rc, "pf_observe")
+        d = {f: getattr(o, f) for f, _ in Obs._fields_}
+        d["tip"] = tuple(o.tip)
+        d["status"] = rc
+        return d
+
+    def get_fields(self):
+        psi = np.zeros(self.shape, self.np_dtype)
+        U = np.zeros(self.shape, self.np_dtype)
+        _check(lib().pf_get_fields(self.h, C.c_void_p(psi.ctypes.data), C.c_void_p(U.ctypes.data)), "pf_get_fields")
+        return psi, U
+
+    def set_fields(self, psi, U):
+        psi = np.ascontiguousarray(psi, dtype=self.np_dtype).reshape(self.shape)
+        U = np.ascontiguousarray(U, dtype=self.np_dtype).reshape(self.shape)
+        _check(lib().pf_set_fields(self.h, C.c_void_p(psi.ctypes.data), C.c_void_p(U.ctypes.data)), "pf_set_fields")
+
+    @property
+    def steps_done(self) -> int:
+        v = C.c_int64()
+        _check(lib().pf_get_step(self.h, C.byref(v)), "pf_get_step")
+        return v.value
+
+    def set_step(self, n: int):
+        _check(lib().pf_set_step(self.h, int(n)), "pf_set_step")
+
+    def device_fields(self):
+        a, b, c = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        _check(lib().pf_device_fields(self.h, C.byref(a), C.byref(b), C.byref(c)), "pf_device_fields")
+        return a.value, b.value, c.value
+
+    @property
+    def n_cells(self) -> int:
+        return int(np.prod(self.shape))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(lib().pf_destroy(self.h), "pf_destroy")
+            self.h = None
+            self.mem = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().pf_destroy(self.h)
+        except Exception:
+            pass
+
+
+class Group:
+    """Instances stepped together by one persistent launch per class."""
+
+    def __init__(self, max_instances: int, max_work: int, stream=None, device="cuda"):
+        import torch
+        n = int(lib().pf_group_required_bytes(int(max_instances), int(max_work)))
+        if n == 0:
+            raise PfError(PF_ERR_INVALID, "pf_group_required_bytes")
+        self.mem = torch.empty(n, dtype=torch.uint8, device=device)
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib().pf_group_create(int(max_instances), int(max_work), C.c_void_p(self.mem.data_ptr()), n,
+                                     C.c_void_p(_stream_handle(stream)), C.byref(h)), "pf_group_create")
+        self.h = h
+        self.members = []
+
+    @staticmethod
+    def work_items(sim: Sim) -> int:
+        n = lib().pf_group_work_items(sim.h)
+        if n < 0:
+            raise PfError(n, "pf_group_work_items")
+        return n
+
+    def add(self, sim: Sim):
+        _check(lib().pf_group_add(self.h, sim.h), "pf_group_add")
+        self.members.append(sim)
+
+    def remove(self, sim: Sim):
+        _check(lib().pf_group_remove(self.h, sim.h), "pf_group_remove")
+        self.members.remove(sim)
+
+    def step(self, n: int = 1, use_graph: bool = True):
+        _check(lib().pf_group_step(self.h, int(n), 1 if use_graph else 0), "pf_group_step")
+
+    def __len__(self):
+        return int(lib().pf_group_size(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(lib().pf_group_destroy(self.h), "pf_group_destroy")
+            self.h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().pf_group_destroy(self.h)
+        except Exception:
+            pass

@@ -1,0 +1,68 @@
+"""Host-side checks of the C-ABI library that need no GPU: the library builds
+and loads, exports every function include/pf.h declares, and validates the
+problem statement (sizes, scheme vs dimension, explicit-Euler bound on dt)
+in pf_required_bytes, which touches no device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2110_12448_gb300 import native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(pf_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = C.CDLL(native.lib_path() if os.path.exists(native.lib_path()) else native.lib()._name)
+    names = declared_functions()
+    assert len(names) >= 25
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    assert native.status_string(0) == "ok"
+    assert "buffer" in native.status_string(native.PF_ERR_BUDGET)
+    assert native.status_string(12345) == "unknown status"
+
+
+def _p(**kw):
+    d = dict(dim=2, nx=64, ny=48, nz=1, scheme="SBAR21", precision="f32")
+    d.update(kw)
+    return native.make_params(**d)
+
+
+def test_required_bytes_layout():
+    b32 = native.required_bytes(_p())
+    b64 = native.required_bytes(_p(precision="f64"))
+    n = 64 * 48
+    assert b32 >= 4 * n * 4 + n * 2 and b64 >= 4 * n * 8 + n * 2
+    assert b64 > b32
+    assert native.required_bytes(_p(dim=3, nx=16, ny=16, nz=16, scheme="SBAR120", dt=0.015)) > 4 * 4 * 16 ** 3
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=3), dict(ny=0), dict(dim=4), dict(scheme="SBAR120"), dict(dim=3, nz=8, scheme="SBAR21"),
+    dict(precision=7), dict(h=0.0), dict(dt=-1.0), dict(k=1.0), dict(k=0.0), dict(eps4=-0.1), dict(max_grains=0),
+    dict(D=-1.0), dict(U0=float("nan")),
+    # explicit Euler bound: 2 h^2 / (16/3 D) for the isotropic Laplacian
+    dict(dt=2 * 0.64 / (16 / 3 * 6.267) * 1.01),
+    dict(scheme="S10", dt=2 * 0.64 / (8 * 6.267) * 1.01),
+])
+def test_invalid_parameters_rejected(bad):
+    assert native.required_bytes(_p(**bad)) == 0
+
+
+def test_stability_bound_boundary():
+    ok = 2 * 0.64 / (16 / 3 * 6.267) * 0.99
+    assert native.required_bytes(_p(dt=ok)) > 0
+    # S10 has the larger Laplacian symbol (8) and so the tighter bound
+    assert native.required_bytes(_p(scheme="S10", dt=ok)) == 0
