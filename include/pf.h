@@ -166,6 +166,33 @@ const char* pf_status_string(int code);
 /* Text of the last CUDA error seen by any call (thread-local). */
 const char* pf_last_cuda_error(void);
 
+/* Observation without any device allocation by the caller.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc -- for example code that runs inside a host
+ * application or plugin framework which owns every device allocation, or a
+ * real-time loop that must not trigger the device-wide synchronisation an
+ * allocation can cause -- but that already hold the fields in device memory.
+ * It computes the same FP64 reductions as pf_observe on caller-given device
+ * fields: psi_dev, U_dev (nx*ny*nz elements of p->precision) and, when
+ * grain >= 0, the int16 grain map grain_dev; rot9 is the observed grain's
+ * crystal-to-lab matrix (grain 0's for grain = -1) and centre3 its reference
+ * point.  Only p->dim, nx, ny, nz, h, k and precision are read.  The call
+ * synchronises `stream` (NULL = legacy default stream) and fills *out like
+ * pf_observe, except step, t and v_tip, which are 0 (no history is kept).
+ *
+ * Scratch: instead of memory from the caller, the block partials live in a
+ * fixed 22 KB array in the library's device globals, which every GPU that
+ * loads the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on a device (two streams, two host threads) race
+ * and must be serialised by the caller.  Grids above PF_NOALLOC_MAX_CELLS
+ * cells are rejected with PF_ERR_INVALID.  Never allocates device memory. */
+#define PF_NOALLOC_MAX_CELLS (1LL << 34)
+int pf_observe_fields_noalloc(const pf_params* p, const void* psi_dev, const void* U_dev, const int16_t* grain_dev,
+                              const double* rot9, const double* centre3, int grain, void* stream, pf_obs* out);
+
 /* ------------------------------------------------------------------------ */
 /* Batching: many simulations stepped together by one persistent launch per  */
 /* (dimension, scheme, precision) class, optionally replayed from a CUDA     */

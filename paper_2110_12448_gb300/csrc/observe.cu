@@ -10,6 +10,7 @@
 // formed with explicitly rounded FP64 operations (no contraction) so that the
 // choice is reproducible on any FP64 implementation of the same formula.
 #include <cfloat>
+#include <mutex>
 
 #include "pf_internal.cuh"
 
@@ -140,6 +141,35 @@ template <typename T> __global__ void k_fill(T* __restrict__ p, T v, long long n
 }
 
 }  // namespace
+
+// Fixed scratch for pf_observe_fields_noalloc: OBS_BLOCKS block partials and
+// one result record (22 KB).  It lives in the module's global memory on every
+// device that loads the library, for the life of the process.  Every call of
+// that entry point overwrites all of it, so nothing needs clearing; calls whose
+// kernels overlap on a device race on it.
+static __device__ __align__(256) ObsPartial g_noalloc_scratch[OBS_BLOCKS + 1];
+
+// Device address of the scratch on the current device.  The first call on a
+// device looks it up with cudaGetSymbolAddress (a host-side name of a
+// __device__ array is not a device address) and caches it per device.
+cudaError_t noalloc_scratch(ObsPartial** partials, ObsPartial** result) {
+    static std::mutex mu;
+    static void* addr[256] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *partials = static_cast<ObsPartial*>(addr[dev]);
+    *result = *partials + OBS_BLOCKS;
+    return cudaSuccess;
+}
 
 cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* result, cudaStream_t st) {
     if (a.prec == 0)

@@ -528,6 +528,75 @@ const char* pf_status_string(int code) {
 
 const char* pf_last_cuda_error(void) { return g_last_cuda.c_str(); }
 
+int pf_observe_fields_noalloc(const pf_params* p, const void* psi_dev, const void* U_dev, const int16_t* grain_dev,
+                              const double* rot9, const double* centre3, int grain, void* stream, pf_obs* out) {
+    if (!p || !psi_dev || !U_dev || !rot9 || !centre3 || !out || grain < -1) return PF_ERR_INVALID;
+    if (grain >= 0 && !grain_dev) return PF_ERR_INVALID;
+    if (p->dim != 2 && p->dim != 3) return PF_ERR_INVALID;
+    if (p->precision != PF_F32 && p->precision != PF_F64) return PF_ERR_INVALID;
+    if (p->nx < 1 || p->ny < 1 || (p->dim == 3 && p->nz < 1) || !(p->h > 0) || !(p->k > 0 && p->k < 1))
+        return PF_ERR_INVALID;
+    const long long N = (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
+    if (N > PF_NOALLOC_MAX_CELLS) return PF_ERR_INVALID;
+    const int dim = p->dim;
+    double d[3] = {0, 0, 0}, best = -INFINITY;
+    for (int a = 0; a < dim; ++a)
+        for (int sg = 1; sg >= -1; sg -= 2) {
+            const double yc = sg * rot9[3 + a];
+            if (yc > best) {
+                best = yc;
+                for (int q = 0; q < 3; ++q) d[q] = q < dim ? sg * rot9[q * 3 + a] : 0.0;
+            }
+        }
+    int ea = 0;
+    for (int a = 1; a < dim; ++a)
+        if (std::fabs(d[a]) > std::fabs(d[ea])) ea = a;
+    ObsArgs a{};
+    a.psi = psi_dev;
+    a.U = U_dev;
+    a.grain = grain_dev;
+    a.prec = p->precision == PF_F64 ? 1 : 0;
+    a.dim = dim;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.nz = dim == 3 ? p->nz : 1;
+    a.grain_filter = grain;
+    a.h = p->h;
+    a.k = p->k;
+    for (int q = 0; q < 3; ++q) {
+        a.cg[q] = centre3[q];
+        a.d[q] = d[q];
+    }
+    a.ea = ea;
+    a.es = d[ea] >= 0 ? 1 : -1;
+    ObsPartial* partials = nullptr;
+    ObsPartial* result = nullptr;
+    CK(noalloc_scratch(&partials, &result));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(launch_observe(a, partials, result, st));
+    ObsPartial r;
+    CK(cudaMemcpyAsync(&r, result, sizeof(r), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::memset(out, 0, sizeof(*out));
+    const double hd = dim == 3 ? p->h * p->h * p->h : p->h * p->h;
+    out->solute = r.solute * hd;
+    out->solid_fraction = r.solid / (double)N;
+    out->nonfinite = (int32_t)r.nonfinite;
+    out->found = r.tip_index >= 0 ? 1 : 0;
+    out->tip_index = r.tip_index;
+    out->tip_score = r.tip_index >= 0 ? r.score : -INFINITY;
+    if (r.tip_index >= 0) {
+        for (int q = 0; q < 3; ++q) out->tip[q] = r.tip[q];
+        const double rx = r.tip[0] - centre3[0], ry = r.tip[1] - centre3[1], rz = dim == 3 ? r.tip[2] - centre3[2] : 0.0;
+        out->angle_xy_deg = std::atan2(-rx, ry) * (180.0 / 3.14159265358979323846);
+        out->angle_out_deg = std::atan2(rz, std::sqrt(rx * rx + ry * ry)) * (180.0 / 3.14159265358979323846);
+    } else {
+        out->tip[0] = out->tip[1] = out->tip[2] = NAN;
+        out->angle_xy_deg = out->angle_out_deg = NAN;
+    }
+    return r.nonfinite > 0 ? PF_ERR_NONFINITE : PF_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

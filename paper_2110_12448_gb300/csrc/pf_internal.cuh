@@ -73,6 +73,8 @@ struct ObsArgs {
 constexpr int OBS_BLOCKS = 304;  // 2 x 152 SMs
 constexpr int OBS_THREADS = 256;
 cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* result, cudaStream_t st);
+// Device address of the library's fixed observe scratch on the current device.
+cudaError_t noalloc_scratch(ObsPartial** partials, ObsPartial** result);
 
 struct SeedDev {
     double x, y, z, r;

@@ -95,6 +95,8 @@ def lib():
                 "pf_group_step": (C.c_int, [vp, i64, C.c_int]),
                 "pf_group_size": (C.c_int, [vp]),
                 "pf_group_destroy": (C.c_int, [vp]),
+                "pf_observe_fields_noalloc": (C.c_int, [P(Params), vp, vp, vp, P(C.c_double), P(C.c_double), C.c_int,
+                                                        vp, P(Obs)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -251,6 +253,26 @@ class Sim:
                 lib().pf_destroy(self.h)
         except Exception:
             pass
+
+
+def observe_fields_noalloc(p: Params, psi_dev: int, U_dev: int, grain_dev: Optional[int], rot9, centre3,
+                           grain: int = -1, stream=None, allow_nonfinite=False) -> dict:
+    """pf_observe_fields_noalloc: the observe reductions on caller-held device
+    fields, using the library's fixed device scratch instead of caller memory."""
+    r = np.ascontiguousarray(rot9, dtype=np.float64).reshape(9)
+    c = np.ascontiguousarray(centre3, dtype=np.float64).reshape(3)
+    o = Obs()
+    rc = lib().pf_observe_fields_noalloc(C.byref(p), C.c_void_p(psi_dev), C.c_void_p(U_dev),
+                                         C.c_void_p(grain_dev) if grain_dev else None,
+                                         r.ctypes.data_as(C.POINTER(C.c_double)),
+                                         c.ctypes.data_as(C.POINTER(C.c_double)), int(grain),
+                                         C.c_void_p(_stream_handle(stream)), C.byref(o))
+    if rc != PF_OK and not (allow_nonfinite and rc == PF_ERR_NONFINITE):
+        raise PfError(rc, "pf_observe_fields_noalloc")
+    d = {f: getattr(o, f) for f, _ in Obs._fields_}
+    d["tip"] = tuple(o.tip)
+    d["status"] = rc
+    return d
 
 
 class Group:
