@@ -138,9 +138,9 @@ namespace {
 
 void default_tile(pf_sim* s) {
     if (s->p.dim == 2) {
-        s->bx = 128;
+        s->bx = 64;  // one warp per 60-column strip
         s->by = 1;
-        s->sweep = 64;
+        s->sweep = 32;
     } else {
         s->bx = 36;
         s->by = 12;

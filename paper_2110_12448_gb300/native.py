@@ -54,7 +54,8 @@ class Obs(C.Structure):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """Path of libpf.so; the PF_LIBRARY environment variable overrides it."""
+    return os.environ.get("PF_LIBRARY", _build.LIB)
 
 
 def lib():
@@ -62,7 +63,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = os.environ.get("PF_LIBRARY") or _build.build()
             if not os.path.exists(path):
                 raise RuntimeError(f"libpf.so missing at {path}: the CUDA library is required (no CPU fallback)")
             L = C.CDLL(path)
