@@ -1,6 +1,421 @@
-// step3d.cu -- placeholder until the 3D kernel lands.
+// step3d.cu -- fused explicit time step of the quantitative alloy phase-field
+// model in 3D for sm_103a (arXiv:2110.12448, Sec. 5-6, Eqs. PF_a and PF_b).
+//
+// 2.5D blocking: a block owns a TX x TY column of cells and sweeps it along z
+// with shared-memory plane rings (psi with a 2-cell halo in x and y, phi, U and
+// delta phi on the 1-cell ring).  Iteration z:
+//   load psi plane z+2 (and phi on the ring region), U plane z+1
+//   phase 1 at plane z+1 on the (TX+2) x (TY+2) ring region: d psi/dt, psi',
+//     phi', delta phi; ring cells outside the domain take their mirror cell's
+//     values (the thread computes the mirror cell)
+//   phase 2 at plane z on the TX x TY outputs: U'
+// Each cell of psi and U is read from HBM once per step by the column that
+// owns it (halo reads hit L2) and psi', U' are written once.
+//
+// Schemes: S-bar_{1,2,0}: L_{1,2,0} = 1/3 L_{1,0,0} + 2/3 L_{0,1,0} (Eqs.
+// 3D_L100, 3D_L110), G_{1,2,0} (Eqs. Grad_100, Grad_110), D~_{1,2,0} (Eqs.
+// divergence_100, divergence_110 with the alpha averages of Sec. 5.2) for D
+// and the approximated anti-trapping (Eq. Anti_approx).  S_{1,0,0}: the <100>
+// shell with a two-point face mean for D and the standard anti-trapping
+// normalised by the face gradient.  Anisotropy: div(J - grad psi) over the
+// six <100> faces in the cell's crystal frame (cubic a_s of Eq.
+// anis_function), a_s^2 from the centred gradient.
 #include "pf_internal.cuh"
+
 namespace pf {
-bool launch_step3d(int, int, int, int, int, cudaStream_t, const WorkItem*, int, const InstRec*, int) { return false; }
-int occupancy_step3d(int, int, int, int) { return 0; }
+namespace {
+
+template <typename T> struct M3;
+template <> struct M3<float> {
+    static __device__ __forceinline__ float tanh_(float x) {
+        return 1.0f - __fdividef(2.0f, 1.0f + __expf(2.0f * x));
+    }
+    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+};
+template <> struct M3<double> {
+    static __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+};
+
+// Component `ax` of (J - g) for a lab-frame face gradient g, crystal frame R
+// (row-major crystal -> lab).  a_s = 1 - 3 eps + 4 eps sum n'^4, J = d(a_s^2
+// |g|^2 / 2)/dg; see the 2D kernel for the algebra.
+template <typename T>
+__device__ __forceinline__ T aniso_q3(const T g[3], const T R[9], T eps, T hh, int ax) {
+    T c[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) c[p] = R[p] * g[0] + R[3 + p] * g[1] + R[6 + p] * g[2];
+    const T r2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    if (r2 * hh < Guard<T>::v) return T(0);
+    const T inv = M3<T>::rcp(r2);
+    T s[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) s[p] = c[p] * c[p] * inv;
+    const T q = s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
+    const T a = T(1) - T(3) * eps + T(4) * eps * q;
+    const T c1 = T(16) * eps * a;
+    const T c0 = a * a - T(1) - c1 * q;
+    T out = T(0);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) out += R[3 * ax + p] * (c[p] * (c0 + c1 * s[p]));
+    return out;
+}
+template <typename T> __device__ __forceinline__ T aniso_a3(const T g[3], const T R[9], T eps, T hh) {
+    T c[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) c[p] = R[p] * g[0] + R[3 + p] * g[1] + R[6 + p] * g[2];
+    const T r2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    if (r2 * hh < Guard<T>::v) return T(1);
+    const T inv = M3<T>::rcp(r2);
+    T q = T(0);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const T s = c[p] * c[p] * inv;
+        q += s * s;
+    }
+    return T(1) - T(3) * eps + T(4) * eps * q;
+}
+
+template <typename T, int S, int TX, int TY> struct Tile3 {
+    static constexpr int AX = TX + 2, AY = TY + 2;  // ring-1 region = threads
+    static constexpr int PX = TX + 4, PY = TY + 4;  // psi region (halo 2)
+    static constexpr int NT = AX * AY;
+    static constexpr size_t smem = sizeof(T) * (8 * PX * PY + 8 * NT + 4 * NT + 4 * NT);
+};
+
+template <typename T, int S, int TX, int TY>
+__global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* __restrict__ work, int n_work,
+                                                              const InstRec* __restrict__ recs, int launch_parity) {
+    using TL = Tile3<T, S, TX, TY>;
+    constexpr int AX = TL::AX, AY = TL::AY, PX = TL::PX, PY = TL::PY, NT = TL::NT;
+    constexpr bool ISO = (S == SBAR120);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* s_psi = reinterpret_cast<T*>(smem_raw);  // [8][PY][PX]
+    T* s_phi = s_psi + 8 * PX * PY;             // [8][AY][AX]
+    T* s_U = s_phi + 8 * NT;                    // [4][AY][AX]
+    T* s_dphi = s_U + 4 * NT;                   // [4][AY][AX]
+    const int tid = threadIdx.x;
+    const int tx = tid % AX, ty = tid / AX;
+    const T SQ2 = T(1.41421356237309504880);
+    const T ISQ2 = T(0.70710678118654752440);
+
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const WorkItem wi = work[w];
+        const InstRec& rec = recs[wi.inst];
+        const int nx = rec.nx, ny = rec.ny, nz = rec.nz;
+        const long long sxy = (long long)nx * ny;
+        const int par = rec.parity_offset ^ launch_parity;
+        const T* __restrict__ psi = static_cast<const T*>(rec.psi[par]);
+        const T* __restrict__ Uf = static_cast<const T*>(rec.U[par]);
+        T* __restrict__ psi_o = static_cast<T*>(rec.psi[par ^ 1]);
+        T* __restrict__ U_o = static_cast<T*>(rec.U[par ^ 1]);
+        const int16_t* __restrict__ grain = rec.grain;
+        const T* __restrict__ rot = static_cast<const T*>(rec.rot);
+        const T ih = T(1.0 / rec.h), hh = T(rec.h * rec.h), dt = T(rec.dt);
+        const T i4h = T(0.25 / rec.h);
+        const T kk = T(rec.k), omk = T(1.0 - rec.k), eps = T(rec.eps4), lam = T(rec.lambda), Dc = T(rec.D);
+        const T ih2 = T(1.0 / (rec.h * rec.h));
+        const T isq2dt = T(1.0 / (1.41421356237309504880 * rec.dt));
+        const int x0 = wi.x0, y0 = wi.y0, z0 = wi.z0;
+        const int z1 = min(z0 + wi.ext, nz);
+
+        // this thread's ring-region cell and the cell it computes in phase 1
+        const int vx = x0 - 1 + tx, vy = y0 - 1 + ty;
+        const int mx = mirror_idx(vx, nx), my = mirror_idx(vy, ny);
+        const bool do_p1 = vx >= -1 && vx <= nx && vy >= -1 && vy <= ny;
+        const bool do_p2 = tx >= 1 && tx <= AX - 2 && ty >= 1 && ty <= AY - 2 && vx < nx && vy < ny;
+        const int jx = mx - x0 + 2, jy = my - y0 + 2;  // psi-region index of the phase-1 cell
+
+        auto PS = [&](int z, int y, int x) -> T& { return s_psi[((z & 7) * PY + y) * PX + x]; };
+        auto RG = [&](T* base, int slots, int z, int y, int x) -> T& {
+            return base[((z & (slots - 1)) * AY + y) * AX + x];
+        };
+
+        auto load_psi_plane = [&](int vz) {
+            const int rz = mirror_idx(vz, nz);
+            for (int i = tid; i < PX * PY; i += NT) {
+                const int px = i % PX, py = i / PX;
+                const int gx = mirror_idx(x0 - 2 + px, nx), gy = mirror_idx(y0 - 2 + py, ny);
+                const T v = __ldg(psi + rz * sxy + (long long)gy * nx + gx);
+                PS(vz, py, px) = v;
+                if (px >= 1 && px <= PX - 2 && py >= 1 && py <= PY - 2)
+                    RG(s_phi, 8, vz, py - 1, px - 1) = M3<T>::tanh_(v * ISQ2);
+            }
+        };
+        auto load_U_plane = [&](int vz) {
+            const int rz = mirror_idx(vz, nz);
+            RG(s_U, 4, vz, ty, tx) = __ldg(Uf + rz * sxy + (long long)my * nx + mx);
+        };
+
+        // phase 1 at real plane p for the cell (mx, my, p); returns phi', writes delta phi
+        auto phase1 = [&](int p, T& psin) -> T {
+            const int g = grain[p * sxy + (long long)my * nx + mx];
+            T R[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) R[q] = __ldg(rot + 9 * g + q);
+            auto P = [&](int dx, int dy, int dz) -> T { return PS(p + dz, jy + dy, jx + dx); };
+            const T pc = P(0, 0, 0);
+            T s100 = T(0), s110 = T(0);
+            s100 = P(1, 0, 0) + P(-1, 0, 0) + P(0, 1, 0) + P(0, -1, 0) + P(0, 0, 1) + P(0, 0, -1);
+            T L, G;
+            {
+                const T ex = P(1, 0, 0) - P(-1, 0, 0), ey = P(0, 1, 0) - P(0, -1, 0), ez = P(0, 0, 1) - P(0, 0, -1);
+                const T g100 = (ex * ex + ey * ey + ez * ez) * T(0.25) * ih2;
+                if (ISO) {
+#pragma unroll
+                    for (int a = -1; a <= 1; a += 2)
+#pragma unroll
+                        for (int b = -1; b <= 1; b += 2) s110 += P(a, b, 0) + P(a, 0, b) + P(0, a, b);
+                    L = (T(1.0 / 3.0) * (s100 - T(6) * pc) + T(2.0 / 3.0) * T(0.25) * (s110 - T(12) * pc)) * ih2;
+                    const T d1 = P(1, 1, 0) - P(-1, -1, 0), d2 = P(1, -1, 0) - P(-1, 1, 0);
+                    const T d3 = P(1, 0, 1) - P(-1, 0, -1), d4 = P(-1, 0, 1) - P(1, 0, -1);
+                    const T d5 = P(0, 1, 1) - P(0, -1, -1), d6 = P(0, -1, 1) - P(0, 1, -1);
+                    const T g010 = (d1 * d1 + d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5 + d6 * d6) * T(1.0 / 16.0) * ih2;
+                    G = T(1.0 / 3.0) * g100 + T(2.0 / 3.0) * g010;
+                } else {
+                    L = (s100 - T(6) * pc) * ih2;
+                    G = g100;
+                }
+            }
+            // six <100> faces
+            T N = T(0);
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    const int e[3] = {ax == 0 ? sg : 0, ax == 1 ? sg : 0, ax == 2 ? sg : 0};
+                    T gf[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (q == ax) {
+                            gf[q] = (P(e[0], e[1], e[2]) - pc) * ih * T(sg);
+                        } else {
+                            const int t[3] = {q == 0, q == 1, q == 2};
+                            gf[q] = (P(e[0] + t[0], e[1] + t[1], e[2] + t[2]) + P(t[0], t[1], t[2]) -
+                                     P(e[0] - t[0], e[1] - t[1], e[2] - t[2]) - P(-t[0], -t[1], -t[2])) *
+                                    i4h;
+                        }
+                    }
+                    N += T(sg) * aniso_q3<T>(gf, R, eps, hh, ax);
+                }
+            }
+            N *= ih;
+            T gc[3] = {(P(1, 0, 0) - P(-1, 0, 0)) * T(0.5) * ih, (P(0, 1, 0) - P(0, -1, 0)) * T(0.5) * ih,
+                       (P(0, 0, 1) - P(0, 0, -1)) * T(0.5) * ih};
+            const T ac = aniso_a3<T>(gc, R, eps, hh);
+            const T ph = RG(s_phi, 8, p, jy - 1, jx - 1);
+            const T u = RG(s_U, 4, p, jy - 1, jx - 1);
+            const T rate = (L + N + SQ2 * (ph - lam * (T(1) - ph * ph) * u)) * M3<T>::rcp(ac * ac) - SQ2 * ph * G;
+            psin = pc + dt * rate;
+            const T phn = M3<T>::tanh_(psin * ISQ2);
+            RG(s_dphi, 4, p, ty, tx) = phn - ph;
+            return phn;
+        };
+
+        // ---- prologue ----
+        for (int vz = z0 - 2; vz <= z0 + 1; ++vz) load_psi_plane(vz);
+        load_U_plane(z0 - 1);
+        load_U_plane(z0);
+        __syncthreads();
+        T phin_cur = T(0);
+        if (do_p1) {
+            T psn;
+            phin_cur = phase1(z0, psn);
+            if (do_p2 && z0 < z1) psi_o[z0 * sxy + (long long)vy * nx + vx] = psn;
+            if (z0 - 1 >= 0) {
+                T d;
+                (void)phase1(z0 - 1, d);
+            } else {
+                RG(s_dphi, 4, z0 - 1, ty, tx) = RG(s_dphi, 4, z0, ty, tx);
+            }
+        }
+        __syncthreads();
+
+        for (int r = z0; r < z1; ++r) {
+            load_psi_plane(r + 2);
+            load_U_plane(r + 1);
+            __syncthreads();
+            T phin_next = T(0);
+            if (do_p1) {
+                if (r + 1 < nz) {
+                    T psn;
+                    phin_next = phase1(r + 1, psn);
+                    if (do_p2 && r + 1 < z1) psi_o[(r + 1) * sxy + (long long)vy * nx + vx] = psn;
+                } else {
+                    RG(s_dphi, 4, r + 1, ty, tx) = RG(s_dphi, 4, r, ty, tx);
+                }
+            }
+            __syncthreads();
+            if (do_p2) {
+                // 3x3x3 neighbourhoods around (tx, ty, r) in the ring region
+                auto PH = [&](int dx, int dy, int dz) -> T { return RG(s_phi, 8, r + dz, ty + dy, tx + dx); };
+                auto UU = [&](int dx, int dy, int dz) -> T { return RG(s_U, 4, r + dz, ty + dy, tx + dx); };
+                auto DP = [&](int dx, int dy, int dz) -> T { return RG(s_dphi, 4, r + dz, ty + dy, tx + dx); };
+                auto PSI = [&](int dx, int dy, int dz) -> T { return PS(r + dz, ty + 1 + dy, tx + 1 + dx); };
+                auto aD = [&](int dx, int dy, int dz) -> T { return T(1) - PH(dx, dy, dz); };
+                auto aA = [&](int dx, int dy, int dz) -> T {
+                    return (T(1) + omk * UU(dx, dy, dz)) * DP(dx, dy, dz) * isq2dt;
+                };
+                T Dt = T(0), At = T(0);
+                const T u0 = UU(0, 0, 0), p0 = PSI(0, 0, 0);
+                if (ISO) {
+                    // D~_{1,2,0} * 6 h^2 = 2 sum_<100> abar db + sum_<110> abar db
+                    T sD = T(0), sA = T(0);
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+                        for (int sg = -1; sg <= 1; sg += 2) {
+                            const int e[3] = {ax == 0 ? sg : 0, ax == 1 ? sg : 0, ax == 2 ? sg : 0};
+                            T nD = aD(0, 0, 0) + aD(e[0], e[1], e[2]);
+                            T nA = aA(0, 0, 0) + aA(e[0], e[1], e[2]);
+                            T mD = T(0), mA = T(0);
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                if (q == ax) continue;
+#pragma unroll
+                                for (int s2 = -1; s2 <= 1; s2 += 2) {
+                                    const int t[3] = {q == 0 ? s2 : 0, q == 1 ? s2 : 0, q == 2 ? s2 : 0};
+                                    mD += aD(t[0], t[1], t[2]) + aD(e[0] + t[0], e[1] + t[1], e[2] + t[2]);
+                                    mA += aA(t[0], t[1], t[2]) + aA(e[0] + t[0], e[1] + t[1], e[2] + t[2]);
+                                }
+                            }
+                            const T abD = T(0.25) * nD + T(1.0 / 16.0) * mD;
+                            const T abA = T(0.25) * nA + T(1.0 / 16.0) * mA;
+                            sD += T(2) * abD * (UU(e[0], e[1], e[2]) - u0);
+                            sA += T(2) * abA * (PSI(e[0], e[1], e[2]) - p0);
+                        }
+#pragma unroll
+                    for (int ax3 = 0; ax3 < 3; ++ax3)
+#pragma unroll
+                        for (int s1 = -1; s1 <= 1; s1 += 2)
+#pragma unroll
+                            for (int s2 = -1; s2 <= 1; s2 += 2) {
+                                int e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
+                                const int a1 = ax3 == 0 ? 1 : 0, a2 = ax3 == 2 ? 1 : 2;
+                                e1[a1] = s1;
+                                e2[a2] = s2;
+                                const int d[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
+                                T nD = aD(0, 0, 0) + aD(e1[0], e1[1], e1[2]) + aD(e2[0], e2[1], e2[2]) + aD(d[0], d[1], d[2]);
+                                T nA = aA(0, 0, 0) + aA(e1[0], e1[1], e1[2]) + aA(e2[0], e2[1], e2[2]) + aA(d[0], d[1], d[2]);
+                                T mD = T(0), mA = T(0);
+#pragma unroll
+                                for (int s3 = -1; s3 <= 1; s3 += 2) {
+                                    int t[3] = {0, 0, 0};
+                                    t[ax3] = s3;
+                                    mD += aD(t[0], t[1], t[2]) + aD(e1[0] + t[0], e1[1] + t[1], e1[2] + t[2]) +
+                                          aD(e2[0] + t[0], e2[1] + t[1], e2[2] + t[2]) + aD(d[0] + t[0], d[1] + t[1], d[2] + t[2]);
+                                    mA += aA(t[0], t[1], t[2]) + aA(e1[0] + t[0], e1[1] + t[1], e1[2] + t[2]) +
+                                          aA(e2[0] + t[0], e2[1] + t[1], e2[2] + t[2]) + aA(d[0] + t[0], d[1] + t[1], d[2] + t[2]);
+                                }
+                                const T abD = T(3.0 / 16.0) * nD + T(1.0 / 32.0) * mD;
+                                const T abA = T(3.0 / 16.0) * nA + T(1.0 / 32.0) * mA;
+                                sD += abD * (UU(d[0], d[1], d[2]) - u0);
+                                sA += abA * (PSI(d[0], d[1], d[2]) - p0);
+                            }
+                    Dt = sD * T(1.0 / 6.0) * ih2;
+                    At = sA * T(1.0 / 6.0) * ih2;
+                } else {
+                    // S_{1,0,0}: <100> faces, two-point face mean; anti-trapping
+                    // normalised by the face gradient
+                    T sD = T(0), sA = T(0);
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+                        for (int sg = -1; sg <= 1; sg += 2) {
+                            const int e[3] = {ax == 0 ? sg : 0, ax == 1 ? sg : 0, ax == 2 ? sg : 0};
+                            sD += T(0.5) * (aD(0, 0, 0) + aD(e[0], e[1], e[2])) * (UU(e[0], e[1], e[2]) - u0);
+                            T gf[3];
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                if (q == ax) {
+                                    gf[q] = (PSI(e[0], e[1], e[2]) - p0) * ih * T(sg);
+                                } else {
+                                    const int t[3] = {q == 0, q == 1, q == 2};
+                                    gf[q] = (PSI(e[0] + t[0], e[1] + t[1], e[2] + t[2]) + PSI(t[0], t[1], t[2]) -
+                                             PSI(e[0] - t[0], e[1] - t[1], e[2] - t[2]) - PSI(-t[0], -t[1], -t[2])) *
+                                            i4h;
+                                }
+                            }
+                            const T m2 = gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2];
+                            if (!(m2 * hh < Guard<T>::v))
+                                sA += T(0.5) * (aA(0, 0, 0) + aA(e[0], e[1], e[2])) * (PSI(e[0], e[1], e[2]) - p0) *
+                                      M3<T>::rcp(M3<T>::sqrt_(m2));
+                        }
+                    Dt = sD * ih2;
+                    At = sA * ih2;
+                }
+                const T dph = DP(0, 0, 0);
+                const T un = u0 + (dt * (Dc * Dt + At) + (T(1) + omk * u0) * dph) * M3<T>::rcp(T(1) + kk - omk * phin_cur);
+                U_o[r * sxy + (long long)vy * nx + vx] = un;
+            }
+            phin_cur = phin_next;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int S, int TX, int TY>
+bool launch_t(int grid, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp) {
+    using TL = Tile3<T, S, TX, TY>;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_step3d<T, S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem) !=
+            cudaSuccess)
+            return false;
+        attr = true;
+    }
+    k_step3d<T, S, TX, TY><<<grid, TL::NT, TL::smem, st>>>(work, n_work, recs, lp);
+    return true;
+}
+template <typename T, int S, int TX, int TY> int occ_t() {
+    using TL = Tile3<T, S, TX, TY>;
+    if (cudaFuncSetAttribute(k_step3d<T, S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem) !=
+        cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step3d<T, S, TX, TY>, TL::NT, TL::smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+// Compiled tiles (block_x, block_y) = (TX + 4, TY + 4): (34, 18) and (34, 10).
+template <typename T, int S>
+bool launch_s(int bx, int by, int grid, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp) {
+    if (bx == 34 && by == 18) return launch_t<T, S, 30, 14>(grid, st, work, n_work, recs, lp);
+    if (bx == 34 && by == 10) return launch_t<T, S, 30, 6>(grid, st, work, n_work, recs, lp);
+    return false;
+}
+template <typename T, int S> int occ_s(int bx, int by) {
+    if (bx == 34 && by == 18) return occ_t<T, S, 30, 14>();
+    if (bx == 34 && by == 10) return occ_t<T, S, 30, 6>();
+    return 0;
+}
+
+}  // namespace
+
+bool launch_step3d(int prec, int scheme, int bx, int by, int grid, cudaStream_t st, const WorkItem* work, int n_work,
+                   const InstRec* recs, int lp) {
+    if (prec == 0) {
+        if (scheme == S100) return launch_s<float, S100>(bx, by, grid, st, work, n_work, recs, lp);
+        if (scheme == SBAR120) return launch_s<float, SBAR120>(bx, by, grid, st, work, n_work, recs, lp);
+    } else {
+        if (scheme == S100) return launch_s<double, S100>(bx, by, grid, st, work, n_work, recs, lp);
+        if (scheme == SBAR120) return launch_s<double, SBAR120>(bx, by, grid, st, work, n_work, recs, lp);
+    }
+    return false;
+}
+
+int occupancy_step3d(int prec, int scheme, int bx, int by) {
+    if (prec == 0) {
+        if (scheme == S100) return occ_s<float, S100>(bx, by);
+        if (scheme == SBAR120) return occ_s<float, SBAR120>(bx, by);
+    } else {
+        if (scheme == S100) return occ_s<double, S100>(bx, by);
+        if (scheme == SBAR120) return occ_s<double, SBAR120>(bx, by);
+    }
+    return 0;
+}
+
 }  // namespace pf
