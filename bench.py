@@ -45,6 +45,20 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate(ms_local: float, cells_per_rank: int, steps: int, world: int, device=None) -> tuple:
+    """Whole-job throughput: every rank runs its own replica of the workload
+    (weak scaling, no data-path collective); the job time is the slowest
+    rank's.  Returns (max ms over ranks, aggregate GLUPS)."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, cells_per_rank * steps * world / (ms / 1e3) / 1e9
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -121,6 +135,31 @@ def cpu_baseline(n, scheme, max_seconds=20.0):
             "sample": f"{steps} steps of one {w.nx}x{w.ny} instance (alpha0={THETAS[3]} deg) of the 10, FP64, {dt:.1f} s"}
 
 
+def fp64_plain(stream, n=200, steps=2000):
+    """Comparator: the plain single-instance FP64 step (200 x 200 free
+    dendrite, one launch per step through pf_step), GLUPS and us/step."""
+    import torch
+
+    from paper_2110_12448_gb300 import native as N
+    from paper_2110_12448_gb300 import synth
+    w = synth.free_dendrite_2d(n)
+    s = N.Sim.from_workload(w, "f64", stream=stream)
+    s.set_tile(64, 1, 16)
+    s.step(10)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s.step(steps)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    o = s.observe(0)
+    s.close()
+    return {"value": w.n_cells * steps / (ms / 1e3) / 1e9, "unit": "GLUPS", "us_per_step": ms * 1e3 / steps,
+            "workload": f"free dendrite 2D {n}x{n}, SBAR21, FP64, {steps} steps, one launch per step",
+            "tip_y": o["tip"][1]}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -176,10 +215,16 @@ def run_native(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.Stream()
     ws = workloads(args.n, args.scheme)
+    tile = None
+    if not args.no_tune:
+        from paper_2110_12448_gb300 import autotune
+        tile, _ = autotune.tune(ws, args.precision)
     sims = []
     with torch.cuda.stream(stream):
         for w in ws:
             sims.append(N.Sim.from_workload(w, args.precision, stream=stream))
+            if tile:
+                sims[-1].set_tile(*tile)
     max_work = sum(N.Group.work_items(s) for s in sims)
     group = N.Group(len(sims), max_work, stream=stream)
     for s in sims:
@@ -222,11 +267,8 @@ def run_native(args):
     ms = e0.elapsed_time(e1)
     kern_ms = sum(a.elapsed_time(b) for a, b, _ in pairs)
     n_launch = sum(c for _, _, c in pairs)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = cells * args.steps * world / (ms / 1e3) / 1e9
+    per_step = sorted(a.elapsed_time(b) / c for a, b, c in pairs)
+    ms, value = aggregate(ms, cells, args.steps, world, device="cuda")
 
     # roofline of the fused step kernel: algorithmic bytes per launch / mean launch time
     peak, peak_kind = peaks()
@@ -275,7 +317,13 @@ def run_native(args):
                                        f"{OBS_EVERY} steps",
                            "cells_per_gpu": cells, "l2": f"state {cells * 16 / 1e6:.0f} MB per step > 129 MB L2"},
                 "roofline": roof, "e2e": e2e, "clocks": clocks.summary(),
+                "latency_ms_per_step": {"p50": statistics.median(per_step),
+                                        "p99": per_step[min(len(per_step) - 1, int(0.99 * len(per_step)))],
+                                        "over": f"{len(per_step)} chunks of up to {OBS_EVERY} steps"},
+                "tile": list(tile) if tile else None,
                 "gpu_launches": n_launch + 2 * len(sims) * (args.steps // OBS_EVERY)}
+        if world == 1 and not args.no_fp64:
+            line["fp64_plain"] = fp64_plain(stream)
         if world == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(args.n, args.scheme)
         print(json.dumps(line), flush=True)
@@ -288,7 +336,7 @@ def run_native(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
@@ -296,6 +344,8 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
+    ap.add_argument("--no-tune", action="store_true", help="use the default tile instead of the autotuner's")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1,0 +1,93 @@
+"""Tile autotuner for the fused step kernels.
+
+For a batch of instances of one class (dimension, scheme, precision, grid
+size) it times each candidate tile -- the sweep length in 2D; the block
+shape and sweep length in 3D -- on synthetic seed states, in one persistent
+launch per step exactly as the batched path runs, and keeps the fastest.
+Wave quantisation (work items vs resident warps or blocks) is what the
+choice mostly trades against the per-sweep prologue, so the answer depends
+on the batch size as well as the grid.  Results are cached per device in
+``_build/autotune.json``.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+CANDIDATES_2D = [(64, 1, s) for s in (16, 24, 32, 48, 64, 96, 128)]
+CANDIDATES_3D = [(34, by, s) for by in (18, 10) for s in (16, 32, 64)]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CACHE = os.path.join(_HERE, "_build", "autotune.json")
+_lock = threading.Lock()
+
+
+def _key(device_name, w, precision, count):
+    return f"{device_name}|{w.dim}|{w.scheme}|{precision}|{w.nx}x{w.ny}x{w.nz}|n{count}"
+
+
+def _load():
+    try:
+        with open(_CACHE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store(d):
+    os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+    tmp = _CACHE + f".{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, _CACHE)
+
+
+def tune(workloads, precision="f32", steps=24, repeats=2, use_cache=True, verbose=False):
+    """Best (block_x, block_y, sweep) for a batch shaped like `workloads`
+    (all of one class).  Returns (tile, {tile: seconds per step})."""
+    import torch
+
+    from . import native as N
+    w0 = workloads[0]
+    dev = torch.cuda.get_device_name()
+    key = _key(dev, w0, precision, len(workloads))
+    with _lock:
+        cache = _load() if use_cache else {}
+    if key in cache:
+        return tuple(cache[key]["tile"]), cache[key]["times"]
+    stream = torch.cuda.Stream()
+    sims = [N.Sim.from_workload(w, precision, stream=stream) for w in workloads]
+    cands = CANDIDATES_2D if w0.dim == 2 else CANDIDATES_3D
+    times = {}
+    for tile in cands:
+        try:
+            for s in sims:
+                s.set_tile(*tile)
+        except N.PfError:
+            continue
+        g = N.Group(len(sims), sum(N.Group.work_items(s) for s in sims), stream=stream)
+        for s in sims:
+            g.add(s)
+        g.step(4, use_graph=False)
+        best = float("inf")
+        for _ in range(repeats):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.step(steps, use_graph=True)
+            b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b) / 1e3 / steps)
+        g.close()
+        times[str(tile)] = best
+        if verbose:
+            print(f"autotune {key} {tile}: {best * 1e3:.3f} ms/step", flush=True)
+    for s in sims:
+        s.close()
+    tile = min(((t, tuple(int(x) for x in k.strip("()").split(","))) for k, t in times.items()))[1]
+    with _lock:
+        cache = _load()
+        cache[key] = {"tile": list(tile), "times": times}
+        _store(cache)
+    return tile, times

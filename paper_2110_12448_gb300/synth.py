@@ -139,6 +139,8 @@ def place_seeds(rng: np.random.Generator, dim: int, extent, n_seeds: int, r: flo
     """Rejection sampling: centres >= 2r from the walls and >= 4r apart;
     after `tries` failures the radius shrinks by 0.8 and placement restarts."""
     while True:
+        while any(e < 4 * r for e in extent[:dim]):
+            r *= 0.8  # the box cannot hold a centre 2r from both walls
         out = []
         fails = 0
         while len(out) < n_seeds and fails < tries:
