@@ -109,9 +109,20 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)}
 
 
-def workloads(n, scheme):
+def workloads(n, scheme, mode="sweep2d"):
     from paper_2110_12448_gb300 import synth
+    if mode == "dendrite3d":
+        return [synth.free_dendrite_3d(n, scheme=scheme)]
+    if mode == "poly2d":
+        return [w for w in synth.polycrystal_batch_2d(64)]
     return [synth.free_dendrite_2d(n, float(t), scheme, steps=20000) for t in THETAS]
+
+
+WORKLOAD_TEXT = {
+    "sweep2d": "orientation sweep 2D, 10 x {n}^2 instances (alpha0 = 0..45 deg), {scheme}",
+    "dendrite3d": "3D free dendrite {n}^3, random ZXZ orientation, {scheme}",
+    "poly2d": "batched 2D polycrystal, 64 instances 256^2..1536^2, 3-12 grains each, {scheme}",
+}
 
 
 def cpu_baseline(n, scheme, max_seconds=20.0):
@@ -158,6 +169,36 @@ def fp64_plain(stream, n=200, steps=2000):
     return {"value": w.n_cells * steps / (ms / 1e3) / 1e9, "unit": "GLUPS", "us_per_step": ms * 1e3 / steps,
             "workload": f"free dendrite 2D {n}x{n}, SBAR21, FP64, {steps} steps, one launch per step",
             "tip_y": o["tip"][1]}
+
+
+def run_serve(args):
+    """Served stream: Poisson arrivals of mixed 2D/3D runs (sizes and step
+    counts scaled by --serve-scale), continuous batching by an 80 % HBM
+    budget; reports aggregate GLUPS and p50/p99 time-to-result."""
+    import torch
+
+    from paper_2110_12448_gb300 import serve, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    reqs = synth.request_stream(rate_per_s=args.rate, window_s=args.window, size_scale=args.serve_scale,
+                                steps_scale=args.serve_scale)
+    rq = [serve.Request(i, r.workload, r.workload.steps, "f32", r.arrival_s) for i, r in enumerate(reqs)]
+    srv = serve.Server(budget_frac=0.8, chunk=100)
+    with Clocks(local) as clocks:
+        srv.run(rq)
+    summ = srv.summary()
+    srv.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": summ["glups"], "unit": "GLUPS", "n_gpus": world, "steps": len(rq),
+                "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"served mixed stream: Poisson {args.rate}/s over {args.window} s, 2D "
+                                       f"128..2048 and 3D 64..192 scaled by {args.serve_scale}, 1-16 seeds, U0 in "
+                                       f"[-0.7,-0.4], 1000..20000 steps scaled by {args.serve_scale}, 80% HBM budget"},
+                "latency_s": {"p50": summ["p50_s"], "p99": summ["p99_s"], "of": "time to result"},
+                "requests": summ["requests"], "wall_s": summ["wall_s"], "clocks": clocks.summary()}
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -214,7 +255,7 @@ def run_native(args):
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.Stream()
-    ws = workloads(args.n, args.scheme)
+    ws = workloads(args.n, args.scheme, args.workload)
     tile = None
     if not args.no_tune:
         from paper_2110_12448_gb300 import autotune
@@ -274,9 +315,9 @@ def run_native(args):
     peak, peak_kind = peaks()
     bpc = B_PER_CELL[args.precision]
     achieved = cells * bpc / (kern_ms / n_launch / 1e3) / 1e9
+    kname = ("k_step2d" if ws[0].dim == 2 else "k_step3d") + f"<{'float' if args.precision == 'f32' else 'double'},{args.scheme}>"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": peak_kind, "bytes_per_cell": bpc,
-            "kernel": f"k_step2d<{'float' if args.precision == 'f32' else 'double'},{args.scheme},128>"}
+            "traffic": None, "peak_source": peak_kind, "bytes_per_cell": bpc, "kernel": kname}
 
     # end to end through the public API: state in from pinned host buffers,
     # K steps, state and observation back, all inside the timed region
@@ -312,8 +353,8 @@ def run_native(args):
         line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-                "config": {"workload": f"orientation sweep 2D, 10 x {args.n}^2 instances (alpha0 = 0..45 deg), "
-                                       f"{args.scheme}, batched persistent launch + CUDA graph, observe every "
+                "config": {"workload": WORKLOAD_TEXT[args.workload].format(n=args.n, scheme=args.scheme) +
+                                       f", FP32 fields, batched persistent launch + CUDA graph, observe every "
                                        f"{OBS_EVERY} steps",
                            "cells_per_gpu": cells, "l2": f"state {cells * 16 / 1e6:.0f} MB per step > 129 MB L2"},
                 "roofline": roof, "e2e": e2e, "clocks": clocks.summary(),
@@ -324,7 +365,7 @@ def run_native(args):
                 "gpu_launches": n_launch + 2 * len(sims) * (args.steps // OBS_EVERY)}
         if world == 1 and not args.no_fp64:
             line["fp64_plain"] = fp64_plain(stream)
-        if world == 1 and not args.no_cpu:
+        if world == 1 and not args.no_cpu and args.workload == "sweep2d":
             line["cpu_baseline"] = cpu_baseline(args.n, args.scheme)
         print(json.dumps(line), flush=True)
     group.close()
@@ -340,8 +381,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--scheme", default="SBAR21", choices=["SBAR21", "S21", "S10"])
-    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--scheme", default="SBAR21", choices=["SBAR21", "S21", "S10", "SBAR120", "S100"])
+    ap.add_argument("--n", type=int, default=None, help="grid side (default 1024 in 2D, 256 in 3D)")
+    ap.add_argument("--workload", default="sweep2d", choices=["sweep2d", "dendrite3d", "poly2d", "serve"])
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
+    ap.add_argument("--window", type=float, default=20.0, help="serve: arrival window in seconds")
+    ap.add_argument("--serve-scale", type=float, default=0.25, help="serve: scale of sides and step counts")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
@@ -349,8 +394,14 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.n is None:
+        args.n = 256 if args.workload == "dendrite3d" else 1024
+    if args.workload == "dendrite3d" and args.scheme in ("SBAR21", "S21", "S10"):
+        args.scheme = {"S10": "S100"}.get(args.scheme, "SBAR120")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_native(args)
 
 
