@@ -45,6 +45,30 @@ def dist_env():
     return rank, world, local
 
 
+# DRAM traffic per launch of the dominant kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
+# source is byte-identical to the one captured (sha256 of the .cu file).
+TRAFFIC = {
+    # profiles/k_step2d_sbar21_f32_orientation_sweep_10x1024sq.md
+    "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
+                "sha256": "2db7f7df18e8b6c5764e3db0eb43958e565851df20283cc52cab5d778ff54dd2", "bytes": 151663360},
+    # profiles/k_step3d_sbar120_f32_dendrite_256cube.md
+    "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
+                   "sha256": "032df0bc367731da2d8baa166be0d86c25adbb2d885e6ee78385e437376231e9", "bytes": 262989824},
+}
+
+
+def traffic_for(workload):
+    import hashlib
+    t = TRAFFIC.get(workload)
+    if not t or not t["sha256"]:
+        return None
+    with open(os.path.join(ROOT, t["source"]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
+            return None
+    return t["bytes"]
+
+
 def aggregate(ms_local: float, cells_per_rank: int, steps: int, world: int, device=None) -> tuple:
     """Whole-job throughput: every rank runs its own replica of the workload
     (weak scaling, no data-path collective); the job time is the slowest
@@ -317,7 +341,7 @@ def run_native(args):
     achieved = cells * bpc / (kern_ms / n_launch / 1e3) / 1e9
     kname = ("k_step2d" if ws[0].dim == 2 else "k_step3d") + f"<{'float' if args.precision == 'f32' else 'double'},{args.scheme}>"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": peak_kind, "bytes_per_cell": bpc, "kernel": kname}
+            "traffic": traffic_for(args.workload), "peak_source": peak_kind, "bytes_per_cell": bpc, "kernel": kname}
 
     # end to end through the public API: state in from pinned host buffers,
     # K steps, state and observation back, all inside the timed region
