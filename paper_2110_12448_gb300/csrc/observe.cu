@@ -99,12 +99,27 @@ __global__ void __launch_bounds__(OBS_THREADS) k_observe(ObsArgs a, ObsPartial* 
     if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
 }
 
-__global__ void __launch_bounds__(32) k_observe_finish(const ObsPartial* __restrict__ partials, int n,
-                                                       ObsPartial* __restrict__ out) {
-    if (threadIdx.x != 0) return;
-    ObsPartial acc = partials[0];
-    for (int b = 1; b < n; ++b) combine(acc, partials[b]);
-    *out = acc;
+// Combine the block partials: thread t folds partials t, t + 256, ... in
+// index order, then a fixed tree; deterministic for a fixed partial count.
+__global__ void __launch_bounds__(OBS_THREADS) k_observe_finish(const ObsPartial* __restrict__ partials, int n,
+                                                                ObsPartial* __restrict__ out) {
+    __shared__ ObsPartial sh[OBS_THREADS];
+    ObsPartial acc;
+    acc.solute = 0.0;
+    acc.solid = 0.0;
+    acc.nonfinite = 0;
+    acc.score = -DBL_MAX;
+    acc.tip_index = -1;
+    acc.tip[0] = acc.tip[1] = acc.tip[2] = 0.0;
+    acc.pad = 0.0;
+    for (int b = threadIdx.x; b < n; b += OBS_THREADS) combine(acc, partials[b]);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = OBS_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) combine(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
 }
 
 template <typename T>
@@ -176,7 +191,7 @@ cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* r
         k_observe<float><<<OBS_BLOCKS, OBS_THREADS, 0, st>>>(a, partials);
     else
         k_observe<double><<<OBS_BLOCKS, OBS_THREADS, 0, st>>>(a, partials);
-    k_observe_finish<<<1, 32, 0, st>>>(partials, OBS_BLOCKS, result);
+    k_observe_finish<<<1, OBS_THREADS, 0, st>>>(partials, OBS_BLOCKS, result);
     return cudaGetLastError();
 }
 

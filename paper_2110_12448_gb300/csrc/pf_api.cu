@@ -186,6 +186,28 @@ InstRec make_rec(const pf_sim* s, int parity_offset) {
     r.eps4 = s->p.eps4;
     r.lambda = s->p.lambda;
     r.D = s->p.D;
+    const double h = s->p.h;
+    double c[NC];
+    c[C_IH] = 1.0 / h;
+    c[C_I4H] = 0.25 / h;
+    c[C_IH_HALF] = 0.5 / h;
+    c[C_HH] = h * h;
+    c[C_IH2] = 1.0 / (h * h);
+    c[C_I6H2] = 1.0 / (6.0 * h * h);
+    c[C_G10] = 2.0 / 3.0 / (4.0 * h * h);
+    c[C_G01] = 1.0 / 3.0 / (8.0 * h * h);
+    c[C_DT] = s->p.dt;
+    c[C_K] = s->p.k;
+    c[C_OMK] = 1.0 - s->p.k;
+    c[C_EPS] = s->p.eps4;
+    c[C_LAM] = s->p.lambda;
+    c[C_D] = s->p.D;
+    c[C_ISQ2DT] = 1.0 / (1.41421356237309504880 * s->p.dt);
+    c[C_I4H2] = 1.0 / (4.0 * h * h);
+    for (int i = 0; i < NC; ++i) {
+        r.cd[i] = c[i];
+        r.cf[i] = (float)c[i];
+    }
     return r;
 }
 

@@ -10,6 +10,27 @@ namespace pf {
 // Scheme identifiers (values of pf_scheme in include/pf.h).
 enum : int { S10 = 0, S21 = 1, SBAR21 = 2, S100 = 3, SBAR120 = 4 };
 
+// Derived per-instance constants (index into InstRec::cf / cd).
+enum : int {
+    C_IH = 0,    // 1/h
+    C_I4H,       // 1/(4h)
+    C_IH_HALF,   // 1/(2h)
+    C_HH,        // h^2
+    C_IH2,       // 1/h^2
+    C_I6H2,      // 1/(6h^2)
+    C_G10,       // (2/3)/(4h^2)
+    C_G01,       // (1/3)/(8h^2)
+    C_DT,        // dt
+    C_K,         // k
+    C_OMK,       // 1-k
+    C_EPS,       // eps4
+    C_LAM,       // lambda
+    C_D,         // D
+    C_ISQ2DT,    // 1/(sqrt2 dt)
+    C_I4H2,      // 1/(4h^2)
+    NC
+};
+
 // One simulation as the fused kernels see it.  psi/U hold the two time
 // levels; the current level of an instance in a launch is
 // parity_offset ^ launch_parity.
@@ -20,6 +41,9 @@ struct InstRec {
     const void* rot;       // n_grains x 9, crystal -> lab, in the field precision
     int32_t nx, ny, nz, parity_offset;
     double h, dt, k, eps4, lambda, D;
+    // derived constants, filled on the host (no FP64 arithmetic in FP32 kernels)
+    float cf[NC];
+    double cd[NC];
 };
 
 // A unit of work: one block sweeps `ext` rows (2D) or planes (3D) starting

@@ -7,8 +7,10 @@
 // no shared memory and no block barrier.  Neighbour columns come over warp
 // shuffles, rows live in a register ring, and every face flux is computed
 // once and handed to the other cell that uses it (shuffle across columns,
-// register carry across rows).  Global traffic per step: psi, U and the
-// int16 grain read once, psi' and U' written once (float2 / int32 vectors).
+// register carry across rows).  The two columns of a lane are processed as a
+// packed pair (FP32: the sm_100 float2 FMA/ADD/MUL instructions, one issue
+// slot for both columns).  Global traffic per step: psi, U and the int16
+// grain read once, psi' and U' written once (float2 / int32 vectors).
 //
 // Iteration r of a sweep (rows are virtual: mirrored at the walls):
 //   load psi(r+2), U(r+1), grain(r+1)            (prefetched one row ahead)
@@ -42,47 +44,155 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int WARP_COLS = 64;  // columns held by a warp (60 outputs + 4 halo)
 
+// ---------------------------------------------------------------------------
+// scalar helpers: FP32 uses the single-instruction approximate reciprocal and
+// base-2 exponential; FP64 uses IEEE operations
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 template <typename T> struct M;
+#ifndef PF_PRECISE_F32
 template <> struct M<float> {
-    // tanh x = 1 - 2 / (1 + e^{2x}) with the hardware exponential and
-    // reciprocal: absolute error ~2e-7 over the whole range
-    static __device__ __forceinline__ float tanh_(float x) {
-        return 1.0f - __fdividef(2.0f, 1.0f + __expf(2.0f * x));
+    // tanh(x / sqrt2) = 1 - 2 / (1 + e^{sqrt2 x}) = 1 - 2 / (1 + 2^{sqrt2 log2(e) x});
+    // absolute error ~2e-7 over the whole range
+    static __device__ __forceinline__ float tanh_isq2(float x) {
+        const float e = ex2_approx(x * 2.0402467570003297f);  // sqrt2 * log2(e)
+        return fmaf(-2.0f, rcp_approx(1.0f + e), 1.0f);
     }
-    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+    static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 };
+#else
+// correctly rounded division and the library tanh (slower; for accuracy studies)
+template <> struct M<float> {
+    static __device__ __forceinline__ float tanh_isq2(float x) { return tanhf(x * 0.70710678118654752440f); }
+    static __device__ __forceinline__ float rcp(float x) { return 1.0f / x; }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+};
+#endif
 template <> struct M<double> {
-    static __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
+    static __device__ __forceinline__ double tanh_isq2(double x) { return tanh(x * 0.70710678118654752440); }
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 };
 
+// ---------------------------------------------------------------------------
+// packed pair of the two columns of a lane
+// ---------------------------------------------------------------------------
+template <typename T> struct V;
+template <> struct V<float> {
+    float2 v;
+    __device__ __forceinline__ float x() const { return v.x; }
+    __device__ __forceinline__ float y() const { return v.y; }
+};
+template <> struct V<double> {
+    double vx, vy;
+    __device__ __forceinline__ double x() const { return vx; }
+    __device__ __forceinline__ double y() const { return vy; }
+};
+__device__ __forceinline__ V<float> mk(float a, float b) {
+    V<float> r;
+    r.v = make_float2(a, b);
+    return r;
+}
+__device__ __forceinline__ V<double> mk(double a, double b) {
+    V<double> r;
+    r.vx = a;
+    r.vy = b;
+    return r;
+}
+template <typename T> __device__ __forceinline__ V<T> bc(T a) { return mk(a, a); }
+__device__ __forceinline__ V<float> operator+(V<float> a, V<float> b) {
+    V<float> r;
+    r.v = __fadd2_rn(a.v, b.v);
+    return r;
+}
+__device__ __forceinline__ V<float> operator-(V<float> a, V<float> b) {
+    V<float> r;
+    r.v = __ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v);  // exactly a - b
+    return r;
+}
+__device__ __forceinline__ V<float> operator*(V<float> a, V<float> b) {
+    V<float> r;
+    r.v = __fmul2_rn(a.v, b.v);
+    return r;
+}
+__device__ __forceinline__ V<float> fma(V<float> a, V<float> b, V<float> c) {
+    V<float> r;
+    r.v = __ffma2_rn(a.v, b.v, c.v);
+    return r;
+}
+__device__ __forceinline__ V<double> operator+(V<double> a, V<double> b) { return mk(a.vx + b.vx, a.vy + b.vy); }
+__device__ __forceinline__ V<double> operator-(V<double> a, V<double> b) { return mk(a.vx - b.vx, a.vy - b.vy); }
+__device__ __forceinline__ V<double> operator*(V<double> a, V<double> b) { return mk(a.vx * b.vx, a.vy * b.vy); }
+__device__ __forceinline__ V<double> fma(V<double> a, V<double> b, V<double> c) {
+    return mk(::fma(a.vx, b.vx, c.vx), ::fma(a.vy, b.vy, c.vy));
+}
+template <typename T> __device__ __forceinline__ V<T> rcp2(V<T> a) { return mk(M<T>::rcp(a.x()), M<T>::rcp(a.y())); }
+
 template <typename T> __device__ __forceinline__ T shup(T v) { return __shfl_up_sync(FULL, v, 1); }
 template <typename T> __device__ __forceinline__ T shdn(T v) { return __shfl_down_sync(FULL, v, 1); }
 
-// A row as one lane sees it: columns L-2 .. L+3.
+// A row as one lane sees it: columns L-2 .. L+3 (m2/p2 only for S_{2,1}'s psi).
 template <typename T> struct Row {
     T m2, m1, l, r, p1, p2;
     __device__ __forceinline__ T at(int o) const {
         return o == -2 ? m2 : o == -1 ? m1 : o == 0 ? l : o == 1 ? r : o == 2 ? p1 : p2;
     }
+    __device__ __forceinline__ V<T> W() const { return mk(m1, l); }  // west neighbours of (L, R)
+    __device__ __forceinline__ V<T> C() const { return mk(l, r); }   // (L, R)
+    __device__ __forceinline__ V<T> E() const { return mk(r, p1); }  // east neighbours
+    __device__ __forceinline__ V<T> pat(int o) const { return mk(at(o), at(o + 1)); }
 };
 
-// Crystal frame of one grain (upper 2x2 of the crystal -> lab rotation).
-template <typename T> struct Rot {
-    T a, b, c, d;  // R00, R01, R10, R11
+// Crystal frames of the two columns (upper 2x2 of crystal -> lab rotations).
+template <typename T> struct Rot2 {
+    V<T> a, b, c, d;  // (R00, R01, R10, R11) of column L in .x, of column R in .y
 };
 
-// Normal component of (J - g) for a lab-frame face gradient (gx, gy).
+// Normal component of (J - g) for face gradients (gx, gy) of both columns.
 //   crystal components c = R^T g, r2 = |c|^2, s_p = c_p^2 / r2, q = sum s_p^2,
 //   a_s = 1 - 3 eps + 4 eps q (= 1 + eps cos 4 theta, Eq. anis_function),
 //   J'_p - c_p = c_p (a^2 - 1 - 16 eps a q + 16 eps a s_p)
-// i.e. d(a_s^2 |g|^2 / 2)/dg - g, rotated back to the lab frame.
+// i.e. d(a_s^2 |g|^2 / 2)/dg - g, rotated back to the lab frame; 0 below the
+// |g|^2 h^2 guard.
 template <typename T>
-__device__ __forceinline__ T aniso_qn(T gx, T gy, const Rot<T>& R, T eps, T hh, bool xface) {
-    const T cx = R.a * gx + R.c * gy;
-    const T cy = R.b * gx + R.d * gy;
+__device__ __forceinline__ V<T> aniso_qn2(V<T> gx, V<T> gy, const Rot2<T>& R, T eps, T hh, bool xface) {
+    const V<T> cx = fma(R.a, gx, R.c * gy);
+    const V<T> cy = fma(R.b, gx, R.d * gy);
+    const V<T> r2 = fma(cx, cx, cy * cy);
+    const V<T> inv = rcp2(r2);
+    const V<T> sx = cx * cx * inv, sy = cy * cy * inv;
+    const V<T> q = fma(sx, sx, sy * sy);
+    const V<T> a = fma(bc<T>(T(4) * eps), q, bc<T>(T(1) - T(3) * eps));
+    const V<T> c1 = bc<T>(T(16) * eps) * a;
+    const V<T> c0 = fma(a, a, bc<T>(T(-1))) - c1 * q;
+    const V<T> jx = cx * fma(c1, sx, c0), jy = cy * fma(c1, sy, c0);
+    const V<T> o = xface ? fma(R.a, jx, R.b * jy) : fma(R.c, jx, R.d * jy);
+    return mk(r2.x() * hh < Guard<T>::v ? T(0) : o.x(), r2.y() * hh < Guard<T>::v ? T(0) : o.y());
+}
+template <typename T> __device__ __forceinline__ V<T> aniso_a2(V<T> gx, V<T> gy, const Rot2<T>& R, T eps, T hh) {
+    const V<T> cx = fma(R.a, gx, R.c * gy);
+    const V<T> cy = fma(R.b, gx, R.d * gy);
+    const V<T> r2 = fma(cx, cx, cy * cy);
+    const V<T> inv = rcp2(r2);
+    const V<T> sx = cx * cx * inv, sy = cy * cy * inv;
+    const V<T> a = fma(bc<T>(T(4) * eps), fma(sx, sx, sy * sy), bc<T>(T(1) - T(3) * eps));
+    return mk(r2.x() * hh < Guard<T>::v ? T(1) : a.x(), r2.y() * hh < Guard<T>::v ? T(1) : a.y());
+}
+// scalar version for the rare faces between two grains
+template <typename T>
+__device__ __forceinline__ T aniso_qn1(T gx, T gy, T Ra, T Rb, T Rc, T Rd, T eps, T hh, bool xface) {
+    const T cx = Ra * gx + Rc * gy;
+    const T cy = Rb * gx + Rd * gy;
     const T r2 = cx * cx + cy * cy;
     if (r2 * hh < Guard<T>::v) return T(0);
     const T inv = M<T>::rcp(r2);
@@ -92,42 +202,46 @@ __device__ __forceinline__ T aniso_qn(T gx, T gy, const Rot<T>& R, T eps, T hh, 
     const T c1 = T(16) * eps * a;
     const T c0 = a * a - T(1) - c1 * q;
     const T jx = cx * (c0 + c1 * sx), jy = cy * (c0 + c1 * sy);
-    return xface ? (R.a * jx + R.b * jy) : (R.c * jx + R.d * jy);
+    return xface ? (Ra * jx + Rb * jy) : (Rc * jx + Rd * jy);
 }
 
-template <typename T> __device__ __forceinline__ T aniso_a(T gx, T gy, const Rot<T>& R, T eps, T hh) {
-    const T cx = R.a * gx + R.c * gy;
-    const T cy = R.b * gx + R.d * gy;
-    const T r2 = cx * cx + cy * cy;
-    if (r2 * hh < Guard<T>::v) return T(1);
-    const T inv = M<T>::rcp(r2);
-    const T sx = cx * cx * inv, sy = cy * cy * inv;
-    return T(1) - T(3) * eps + T(4) * eps * (sx * sx + sy * sy);
-}
-
-// App. B: |grad b| at a <10> face; B(p, q) = b at origin + p normal + q tangent.
-template <typename T, typename F> __device__ __forceinline__ T appb_face(F B, T ih) {
-    const T a1 = B(1, 1) - B(0, -1), a2 = B(0, 1) - B(1, -1);
-    const T b1 = B(2, 1) - B(-1, -1), b2 = B(-1, 1) - B(2, -1);
-    const T c1 = B(1, 2) - B(0, -2), c2 = B(0, 2) - B(1, -2);
-    const T dn = (T(35.0 / 48.0) * (a1 - a2) - T(1.0 / 48.0) * (b1 - b2) - T(1.0 / 6.0) * (c1 - c2)) * ih;
-    const T dt = (T(35.0 / 96.0) * (a1 + a2) - T(1.0 / 32.0) * (b1 + b2) - T(1.0 / 24.0) * (c1 + c2)) * ih;
-    return M<T>::sqrt_(dn * dn + dt * dt);
+// App. B: |grad b| at a <10> face (pairs); B(p, q) = b at origin + p normal + q tangent.
+template <typename T, typename F> __device__ __forceinline__ V<T> appb_face2(F B, T ih) {
+    const V<T> a1 = B(1, 1) - B(0, -1), a2 = B(0, 1) - B(1, -1);
+    const V<T> b1 = B(2, 1) - B(-1, -1), b2 = B(-1, 1) - B(2, -1);
+    const V<T> c1 = B(1, 2) - B(0, -2), c2 = B(0, 2) - B(1, -2);
+    const V<T> dn = (bc<T>(T(35.0 / 48.0)) * (a1 - a2) - bc<T>(T(1.0 / 48.0)) * (b1 - b2) -
+                     bc<T>(T(1.0 / 6.0)) * (c1 - c2)) * bc<T>(ih);
+    const V<T> dt = (bc<T>(T(35.0 / 96.0)) * (a1 + a2) - bc<T>(T(1.0 / 32.0)) * (b1 + b2) -
+                     bc<T>(T(1.0 / 24.0)) * (c1 + c2)) * bc<T>(ih);
+    const V<T> m2 = fma(dn, dn, dt * dt);
+    return mk(M<T>::sqrt_(m2.x()), M<T>::sqrt_(m2.y()));
 }
 // App. B: |grad b| at a corner; B(p, q) = b at origin + p x + q y.
-template <typename T, typename F> __device__ __forceinline__ T appb_corner(F B, T ih) {
-    const T a1 = B(1, 1) - B(0, 0), a2 = B(0, 1) - B(1, 0);
-    const T b1 = B(2, 1) - B(-1, 0), b2 = B(-1, 1) - B(2, 0);
-    const T c1 = B(1, 2) - B(0, -1), c2 = B(0, 2) - B(1, -1);
-    const T dx = (T(5.0 / 8.0) * (a1 - a2) - T(1.0 / 48.0) * (b1 - b2) - T(1.0 / 16.0) * (c1 - c2)) * ih;
-    const T dy = (T(5.0 / 8.0) * (a1 + a2) - T(1.0 / 16.0) * (b1 + b2) - T(1.0 / 48.0) * (c1 + c2)) * ih;
-    return M<T>::sqrt_(dx * dx + dy * dy);
+template <typename T, typename F> __device__ __forceinline__ V<T> appb_corner2(F B, T ih) {
+    const V<T> a1 = B(1, 1) - B(0, 0), a2 = B(0, 1) - B(1, 0);
+    const V<T> b1 = B(2, 1) - B(-1, 0), b2 = B(-1, 1) - B(2, 0);
+    const V<T> c1 = B(1, 2) - B(0, -1), c2 = B(0, 2) - B(1, -1);
+    const V<T> dx = (bc<T>(T(5.0 / 8.0)) * (a1 - a2) - bc<T>(T(1.0 / 48.0)) * (b1 - b2) -
+                     bc<T>(T(1.0 / 16.0)) * (c1 - c2)) * bc<T>(ih);
+    const V<T> dy = (bc<T>(T(5.0 / 8.0)) * (a1 + a2) - bc<T>(T(1.0 / 16.0)) * (b1 + b2) -
+                     bc<T>(T(1.0 / 48.0)) * (c1 + c2)) * bc<T>(ih);
+    const V<T> m2 = fma(dx, dx, dy * dy);
+    return mk(M<T>::sqrt_(m2.x()), M<T>::sqrt_(m2.y()));
+}
+// f / m per column with the guard on |grad psi| of the standard anti-trapping forms
+template <typename T> __device__ __forceinline__ V<T> guarded_div2(V<T> f, V<T> m, T hh) {
+    const V<T> q = f * rcp2(m);
+    return mk(m.x() * m.x() * hh < Guard<T>::v ? T(0) : q.x(), m.y() * m.y() * hh < Guard<T>::v ? T(0) : q.y());
 }
 
-// f / m with the guard on |grad psi| of the standard anti-trapping forms
-template <typename T> __device__ __forceinline__ T guarded_div(T f, T m, T hh) {
-    return (m * m * hh < Guard<T>::v) ? T(0) : f * M<T>::rcp(m);
-}
+template <typename T> struct ConstOf;
+template <> struct ConstOf<float> {
+    static __device__ __forceinline__ const float* get(const InstRec& r) { return r.cf; }
+};
+template <> struct ConstOf<double> {
+    static __device__ __forceinline__ const double* get(const InstRec& r) { return r.cd; }
+};
 
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using t = float2; };
@@ -158,34 +272,32 @@ __device__ __forceinline__ void load_grain_pair(const int16_t* __restrict__ row,
     }
 }
 template <typename T>
-__device__ __forceinline__ void store_pair(T* __restrict__ row, int c, bool vec, bool okL, bool okR, T a, T b) {
+__device__ __forceinline__ void store_pair(T* __restrict__ row, int c, bool vec, bool okL, bool okR, V<T> v) {
     if (vec && okL && okR) {
-        typename Vec2<T>::t v;
-        v.x = a;
-        v.y = b;
-        *reinterpret_cast<typename Vec2<T>::t*>(row + c) = v;
+        typename Vec2<T>::t o;
+        o.x = v.x();
+        o.y = v.y();
+        *reinterpret_cast<typename Vec2<T>::t*>(row + c) = o;
     } else {
-        if (okL) row[c] = a;
-        if (okR) row[c + 1] = b;
+        if (okL) row[c] = v.x();
+        if (okR) row[c + 1] = v.y();
     }
 }
 
-// FP32 kernels are capped at 128 registers (4 blocks of 4 warps per SM): the
-// sweep is latency-bound at 3 blocks.  FP64 kernels keep their registers.
+// FP32 kernels are capped at 128 registers (4 blocks of 4 warps per SM).
 #ifndef PF_STEP2D_MIN_BLOCKS_F32
 #define PF_STEP2D_MIN_BLOCKS_F32 4
 #endif
 
 template <typename T, int S>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? PF_STEP2D_MIN_BLOCKS_F32 : 1) k_step2d(const WorkItem* __restrict__ work, int n_work,
-                                                const InstRec* __restrict__ recs, int launch_parity) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? PF_STEP2D_MIN_BLOCKS_F32 : 1)
+    k_step2d(const WorkItem* __restrict__ work, int n_work, const InstRec* __restrict__ recs, int launch_parity) {
     constexpr bool ISO = (S == S21 || S == SBAR21);
     const int lane = threadIdx.x & 31;
     const int warps_per_block = blockDim.x >> 5;
     const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
     const int nw = gridDim.x * warps_per_block;
     const T SQ2 = T(1.41421356237309504880);
-    const T ISQ2 = T(0.70710678118654752440);
 
     for (int w = gw; w < n_work; w += nw) {
         const WorkItem wi = work[w];
@@ -198,13 +310,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? PF_STEP2D_MIN_BLOCKS_F32
         T* __restrict__ U_o = static_cast<T*>(rec.U[par ^ 1]);
         const int16_t* __restrict__ grain = rec.grain;
         const T* __restrict__ rot = static_cast<const T*>(rec.rot);
-        const T ih = T(1.0 / rec.h), hh = T(rec.h * rec.h), dt = T(rec.dt);
-        const T i4h = T(0.25 / rec.h);
-        const T kk = T(rec.k), omk = T(1.0 - rec.k), eps = T(rec.eps4), lam = T(rec.lambda), Dc = T(rec.D);
-        const T ih2 = T(1.0 / (rec.h * rec.h));
-        const T i6h2 = T(1.0 / (6.0 * rec.h * rec.h));
-        const T i4h2 = T(1.0 / (4.0 * rec.h * rec.h)), i8h2 = T(1.0 / (8.0 * rec.h * rec.h));
-        const T isq2dt = T(1.0 / (1.41421356237309504880 * rec.dt));
+        const T* cst = ConstOf<T>::get(rec);
+        const T ih = cst[C_IH], hh = cst[C_HH], dt = cst[C_DT];
+        const T i4h = cst[C_I4H], ih_half = cst[C_IH_HALF];
+        const T kk = cst[C_K], omk = cst[C_OMK], eps = cst[C_EPS], lam = cst[C_LAM], Dc = cst[C_D];
+        const T ih2 = cst[C_IH2], i6h2 = cst[C_I6H2], g10c = cst[C_G10], g01c = cst[C_G01];
+        const T isq2dt = cst[C_ISQ2DT];
         const bool vec = (nx & 1) == 0;
 
         const int x0 = wi.x0, y0 = wi.y0;
@@ -213,6 +324,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? PF_STEP2D_MIN_BLOCKS_F32
         const bool realL = cL >= 0 && cL < nx, realR = cL + 1 >= 0 && cL + 1 < nx;
         const bool outL = lane >= 1 && lane <= 30 && realL;
         const bool outR = lane >= 1 && lane <= 30 && realR;
+        const bool edge = (x0 - 2 < 0) || (x0 + 62 > nx);  // warp holds ghost columns
         // lanes holding the mirror images of ghost columns (phase-1 copies)
         const int mL = mirror_idx(cL, nx), mR = mirror_idx(cL + 1, nx);
         const int srcL = (mL - (x0 - 2)) >> 1, srcR = (mR - (x0 - 2)) >> 1;
@@ -221,226 +333,195 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? PF_STEP2D_MIN_BLOCKS_F32
         auto fetch_row = [&](const T* f, int vr, T& a, T& b) {
             load_pair<T>(f + (size_t)mirror_idx(vr, ny) * nx, cL, nx, vec, a, b);
         };
-        auto make_row = [&](T a, T b) {
+        auto make_row = [&](T a, T b, bool wide) {
             Row<T> row;
             row.l = a;
             row.r = b;
             row.m1 = shup(b);
             row.p1 = shdn(a);
-            row.m2 = shup(a);
-            row.p2 = shdn(b);
+            if (wide) {
+                row.m2 = shup(a);
+                row.p2 = shdn(b);
+            } else {
+                row.m2 = row.p2 = T(0);
+            }
             return row;
-        };
-        auto rot_of = [&](int g) {
-            const T* Rg = rot + 9 * g;
-            Rot<T> R;
-            R.a = __ldg(Rg + 0);
-            R.b = __ldg(Rg + 1);
-            R.c = __ldg(Rg + 3);
-            R.d = __ldg(Rg + 4);
-            return R;
         };
         auto phi_row = [&](const Row<T>& p) {
             Row<T> o;
-            o.l = M<T>::tanh_(p.l * ISQ2);
-            o.r = M<T>::tanh_(p.r * ISQ2);
+            o.l = M<T>::tanh_isq2(p.l);
+            o.r = M<T>::tanh_isq2(p.r);
             o.m1 = shup(o.r);
             o.p1 = shdn(o.l);
             o.m2 = o.p2 = T(0);
             return o;
         };
-        // delta phi row from the own values: ghost columns take their mirror
-        // cell's value, halo columns come from the neighbour lanes
-        auto dphi_row = [&](T dL, T dR) {
-            const T aL = __shfl_sync(FULL, dL, srcL), bL = __shfl_sync(FULL, dR, srcL);
-            const T aR = __shfl_sync(FULL, dL, srcR), bR = __shfl_sync(FULL, dR, srcR);
+        // delta phi row: ghost columns take their mirror cell's value (only in
+        // warps that hold ghost columns), halo columns come from the neighbours
+        auto dphi_row = [&](V<T> d) {
             Row<T> o;
-            o.l = realL ? dL : (hiL ? bL : aL);
-            o.r = realR ? dR : (hiR ? bR : aR);
+            o.l = d.x();
+            o.r = d.y();
+            if (edge) {
+                const T aL = __shfl_sync(FULL, d.x(), srcL), bL = __shfl_sync(FULL, d.y(), srcL);
+                const T aR = __shfl_sync(FULL, d.x(), srcR), bR = __shfl_sync(FULL, d.y(), srcR);
+                o.l = realL ? o.l : (hiL ? bL : aL);
+                o.r = realR ? o.r : (hiR ? bR : aR);
+            }
             o.m1 = shup(o.r);
             o.p1 = shdn(o.l);
             o.m2 = o.p2 = T(0);
             return o;
         };
 
-        // anisotropy y-face carries (face between rows p-1 and p, own columns)
-        T qyL_c = T(0), qyR_c = T(0);
+        // crystal frames of the own columns, reloaded when the grain changes
+        Rot2<T> RR;
+        int cgL = -1, cgR = -1;
+        auto set_rot = [&](int gL, int gR) {
+            if (gL != cgL || gR != cgR) {
+                const T* A = rot + 9 * gL;
+                const T* B = rot + 9 * gR;
+                RR.a = mk(__ldg(A + 0), __ldg(B + 0));
+                RR.b = mk(__ldg(A + 1), __ldg(B + 1));
+                RR.c = mk(__ldg(A + 3), __ldg(B + 3));
+                RR.d = mk(__ldg(A + 4), __ldg(B + 4));
+                cgL = gL;
+                cgR = gR;
+            }
+        };
+
+        // anisotropy y-face carry (face between rows p-1 and p, own columns)
+        V<T> qy_c = bc<T>(T(0));
         int gyL_c = -1, gyR_c = -1;
-        int prow_c = -100;  // row p the carried faces belong to
+        int prow_c = -100;
 
         // phase 1 at real row p (psi rows Pm = p-1, P0 = p, Pp = p+1), grains
-        // gL, gR: psi', phi' and delta phi for the own columns.
+        // gL, gR: returns psi' and phi' of the own columns and delta phi.
         auto phase1 = [&](int p, const Row<T>& Pm, const Row<T>& P0, const Row<T>& Pp, const Row<T>& ph0,
-                          const Row<T>& u0, int gL, int gR, T& psinL, T& psinR, T& fL, T& fR, T& dL, T& dR) {
-            const Rot<T> RL = rot_of(gL), RR = rot_of(gR);
+                          const Row<T>& u0, int gL, int gR, V<T>& psin, V<T>& phin, V<T>& dph) {
+            set_rot(gL, gR);
             const int gM = shup(gR);  // grain of column L-1
-            // x faces: (L|R) in L's frame, (R|R+1) in R's frame; (L-1|L) from lane-1
-            const T gxi = (P0.r - P0.l) * ih, gyi = (Pp.r + Pp.l - Pm.r - Pm.l) * i4h;
-            const T qx_lr_L = aniso_qn<T>(gxi, gyi, RL, eps, hh, true);
-            const T qx_rp =
-                aniso_qn<T>((P0.p1 - P0.r) * ih, (Pp.p1 + Pp.r - Pm.p1 - Pm.r) * i4h, RR, eps, hh, true);
-            T qx_lr_R = qx_lr_L;
-            if (gR != gL) qx_lr_R = aniso_qn<T>(gxi, gyi, RR, eps, hh, true);
-            T qx_ml = shup(qx_rp);
+            const V<T> W0 = P0.W(), C0 = P0.C(), E0 = P0.E();
+            const V<T> Wm = Pm.W(), Cm = Pm.C(), Em = Pm.E();
+            const V<T> Wp = Pp.W(), Cp = Pp.C(), Ep = Pp.E();
+            // x+ faces: (L|R) in L's frame, (R|R+1) in R's frame
+            const V<T> gxX = (E0 - C0) * bc<T>(ih), gyX = ((Ep + Cp) - (Em + Cm)) * bc<T>(i4h);
+            const V<T> Xp = aniso_qn2<T>(gxX, gyX, RR, eps, hh, true);
+            // x- faces: from the left column; recomputed across grain boundaries
+            T xmL = shup(Xp.y()), xmR = Xp.x();
             if (gM != gL || lane == 0)
-                qx_ml = aniso_qn<T>((P0.l - P0.m1) * ih, (Pp.l + Pp.m1 - Pm.l - Pm.m1) * i4h, RL, eps, hh, true);
-            // y faces: (p|p+1) computed here, (p-1|p) carried from row p-1
-            const T qyL_p =
-                aniso_qn<T>((Pp.r + P0.r - Pp.m1 - P0.m1) * i4h, (Pp.l - P0.l) * ih, RL, eps, hh, false);
-            const T qyR_p =
-                aniso_qn<T>((Pp.p1 + P0.p1 - Pp.l - P0.l) * i4h, (Pp.r - P0.r) * ih, RR, eps, hh, false);
-            T qyL_m = qyL_c, qyR_m = qyR_c;
-            if (prow_c != p || gyL_c != gL)
-                qyL_m = aniso_qn<T>((P0.r + Pm.r - P0.m1 - Pm.m1) * i4h, (P0.l - Pm.l) * ih, RL, eps, hh, false);
-            if (prow_c != p || gyR_c != gR)
-                qyR_m = aniso_qn<T>((P0.p1 + Pm.p1 - P0.l - Pm.l) * i4h, (P0.r - Pm.r) * ih, RR, eps, hh, false);
-            qyL_c = qyL_p;
-            qyR_c = qyR_p;
+                xmL = aniso_qn1<T>((P0.l - P0.m1) * ih, ((Pp.l + Pp.m1) - (Pm.l + Pm.m1)) * i4h, RR.a.x(), RR.b.x(),
+                                   RR.c.x(), RR.d.x(), eps, hh, true);
+            if (gR != gL)
+                xmR = aniso_qn1<T>(gxX.x(), gyX.x(), RR.a.y(), RR.b.y(), RR.c.y(), RR.d.y(), eps, hh, true);
+            // y+ faces; y- faces carried from row p-1 when valid
+            const V<T> Yp =
+                aniso_qn2<T>(((Ep + E0) - (Wp + W0)) * bc<T>(i4h), (Cp - C0) * bc<T>(ih), RR, eps, hh, false);
+            V<T> Ym = qy_c;
+            const bool okL = prow_c == p && gyL_c == gL, okR = prow_c == p && gyR_c == gR;
+            if (!(okL && okR)) {
+                const V<T> Yc =
+                    aniso_qn2<T>(((E0 + Em) - (W0 + Wm)) * bc<T>(i4h), (C0 - Cm) * bc<T>(ih), RR, eps, hh, false);
+                Ym = mk(okL ? Ym.x() : Yc.x(), okR ? Ym.y() : Yc.y());
+            }
+            qy_c = Yp;
             gyL_c = gL;
             gyR_c = gR;
             prow_c = p + 1;
-            const T NL = (qx_lr_L - qx_ml + qyL_p - qyL_m) * ih;
-            const T NR = (qx_rp - qx_lr_R + qyR_p - qyR_m) * ih;
-            T LL, LR, GL, GR;
+            const V<T> N = ((Xp - mk(xmL, xmR)) + (Yp - Ym)) * bc<T>(ih);
+            // Laplacian, gradient square, centred-gradient anisotropy
+            const V<T> ex = E0 - W0, ey = Cp - Cm;
+            V<T> L, G;
             if (ISO) {
-                LL = (T(4) * (P0.m1 + P0.r + Pm.l + Pp.l) + (Pm.m1 + Pm.r + Pp.m1 + Pp.r) - T(20) * P0.l) * i6h2;
-                LR = (T(4) * (P0.l + P0.p1 + Pm.r + Pp.r) + (Pm.l + Pm.p1 + Pp.l + Pp.p1) - T(20) * P0.r) * i6h2;
-                const T exL = P0.r - P0.m1, eyL = Pp.l - Pm.l, dpL = Pp.r - Pm.m1, dmL = Pm.r - Pp.m1;
-                const T exR = P0.p1 - P0.l, eyR = Pp.r - Pm.r, dpR = Pp.p1 - Pm.l, dmR = Pm.p1 - Pp.l;
-                GL = T(2.0 / 3.0) * (exL * exL + eyL * eyL) * i4h2 + T(1.0 / 3.0) * (dpL * dpL + dmL * dmL) * i8h2;
-                GR = T(2.0 / 3.0) * (exR * exR + eyR * eyR) * i4h2 + T(1.0 / 3.0) * (dpR * dpR + dmR * dmR) * i8h2;
+                L = fma(bc<T>(T(4)), (W0 + E0) + (Cm + Cp), ((Wm + Em) + (Wp + Ep)) - bc<T>(T(20)) * C0) *
+                    bc<T>(i6h2);
+                const V<T> dp = Ep - Wm, dm = Em - Wp;
+                G = fma(bc<T>(g10c), fma(ex, ex, ey * ey), bc<T>(g01c) * fma(dp, dp, dm * dm));
             } else {
-                LL = (P0.m1 + P0.r + Pm.l + Pp.l - T(4) * P0.l) * ih2;
-                LR = (P0.l + P0.p1 + Pm.r + Pp.r - T(4) * P0.r) * ih2;
-                const T exL = P0.r - P0.m1, eyL = Pp.l - Pm.l, exR = P0.p1 - P0.l, eyR = Pp.r - Pm.r;
-                GL = (exL * exL + eyL * eyL) * i4h2;
-                GR = (exR * exR + eyR * eyR) * i4h2;
+                L = ((W0 + E0) + (Cm + Cp) - bc<T>(T(4)) * C0) * bc<T>(ih2);
+                G = bc<T>(T(0.25) * ih2) * fma(ex, ex, ey * ey);
             }
-            const T acL = aniso_a<T>((P0.r - P0.m1) * T(0.5) * ih, (Pp.l - Pm.l) * T(0.5) * ih, RL, eps, hh);
-            const T acR = aniso_a<T>((P0.p1 - P0.l) * T(0.5) * ih, (Pp.r - Pm.r) * T(0.5) * ih, RR, eps, hh);
-            const T phL = ph0.l, phR = ph0.r, uL = u0.l, uR = u0.r;
-            const T rL =
-                (LL + NL + SQ2 * (phL - lam * (T(1) - phL * phL) * uL)) * M<T>::rcp(acL * acL) - SQ2 * phL * GL;
-            const T rR =
-                (LR + NR + SQ2 * (phR - lam * (T(1) - phR * phR) * uR)) * M<T>::rcp(acR * acR) - SQ2 * phR * GR;
-            psinL = P0.l + dt * rL;
-            psinR = P0.r + dt * rR;
-            fL = M<T>::tanh_(psinL * ISQ2);
-            fR = M<T>::tanh_(psinR * ISQ2);
-            dL = fL - phL;
-            dR = fR - phR;
+            const V<T> ac = aniso_a2<T>(ex * bc<T>(ih_half), ey * bc<T>(ih_half), RR, eps, hh);
+            const V<T> ph = ph0.C(), u = u0.C();
+            const V<T> src = bc<T>(SQ2) * (ph - bc<T>(lam) * (bc<T>(T(1)) - ph * ph) * u);
+            const V<T> rate = (L + N + src) * rcp2(ac * ac) - bc<T>(SQ2) * ph * G;
+            psin = fma(bc<T>(dt), rate, C0);
+            phin = mk(M<T>::tanh_isq2(psin.x()), M<T>::tanh_isq2(psin.y()));
+            dph = phin - ph;
         };
 
-        // phase-2 carries: fluxes of row q-1 that row q uses, negated on use
-        T cFYm_D[2] = {T(0), T(0)}, cFYm_A[2] = {T(0), T(0)};
-        T cFDmm_D[2] = {T(0), T(0)}, cFDmm_A[2] = {T(0), T(0)};
-        T cFDpm_D[2] = {T(0), T(0)}, cFDpm_A[2] = {T(0), T(0)};
-        T cK_D[2] = {T(0), T(0)}, cK_A[2] = {T(0), T(0)};
+        // phase-2 carries: fluxes of row q-1 that row q uses (subtracted)
+        V<T> cFYm_D = bc<T>(T(0)), cFYm_A = bc<T>(T(0));
+        V<T> cFDmm_D = bc<T>(T(0)), cFDmm_A = bc<T>(T(0));
+        V<T> cFDpm_D = bc<T>(T(0)), cFDpm_A = bc<T>(T(0));
+        V<T> cK_D = bc<T>(T(0)), cK_A = bc<T>(T(0));
 
-        // Phase-2 fluxes at row q: alpha rows q (a*0), q+1 (a*1); U rows q, q+1;
-        // psi rows q-2 .. q+2 (Pq[0..4]).  Writes the eight-flux sums of the own
-        // columns (times 6 h^2 for the D~_{2,1} forms, times h^2 for S_{1,0})
-        // and updates the carries.  need_x = false skips the x-face magnitudes
-        // of S_{2,1}, which would read row q-2.
+        // Phase-2 fluxes at row q: alpha rows q (a*0), q+1 (a*1); U rows q,
+        // q+1; psi rows q-2 .. q+2 (Pq[0..4]).  Returns the eight-flux sums of
+        // the own columns (x 6 h^2 for the D~_{2,1} forms, x h^2 for S_{1,0})
+        // and updates the carries.  need_x = false skips S_{2,1}'s x-face
+        // magnitudes, which would read row q-2.
         auto fluxes = [&](const Row<T>& aD0, const Row<T>& aD1, const Row<T>& aA0, const Row<T>& aA1,
-                          const Row<T>& bU0, const Row<T>& bU1, const Row<T>* Pq, bool need_x, T& sDL, T& sDR,
-                          T& sAL, T& sAR) {
+                          const Row<T>& bU0, const Row<T>& bU1, const Row<T>* Pq, bool need_x, V<T>& sD, V<T>& sA) {
             const Row<T>& b0 = Pq[2];
             const Row<T>& b1 = Pq[3];
             if (S == S10) {
-                T fxD[2], fyD[2], fxA[2], fyA[2];
-                fxD[0] = T(0.5) * (aD0.l + aD0.r) * (bU0.r - bU0.l);
-                fxD[1] = T(0.5) * (aD0.r + aD0.p1) * (bU0.p1 - bU0.r);
-                fyD[0] = T(0.5) * (aD0.l + aD1.l) * (bU1.l - bU0.l);
-                fyD[1] = T(0.5) * (aD0.r + aD1.r) * (bU1.r - bU0.r);
-                {
-                    const Row<T>& bm = Pq[1];
-                    const T gxl = (b0.r - b0.l) * ih, gyl = (b1.r + b1.l - bm.r - bm.l) * i4h;
-                    const T gxr = (b0.p1 - b0.r) * ih, gyr = (b1.p1 + b1.r - bm.p1 - bm.r) * i4h;
-                    fxA[0] = guarded_div<T>(T(0.5) * (aA0.l + aA0.r) * (b0.r - b0.l),
-                                            M<T>::sqrt_(gxl * gxl + gyl * gyl), hh);
-                    fxA[1] = guarded_div<T>(T(0.5) * (aA0.r + aA0.p1) * (b0.p1 - b0.r),
-                                            M<T>::sqrt_(gxr * gxr + gyr * gyr), hh);
-                    const T yxl = (b1.r + b0.r - b1.m1 - b0.m1) * i4h, yyl = (b1.l - b0.l) * ih;
-                    const T yxr = (b1.p1 + b0.p1 - b1.l - b0.l) * i4h, yyr = (b1.r - b0.r) * ih;
-                    fyA[0] = guarded_div<T>(T(0.5) * (aA0.l + aA1.l) * (b1.l - b0.l),
-                                            M<T>::sqrt_(yxl * yxl + yyl * yyl), hh);
-                    fyA[1] = guarded_div<T>(T(0.5) * (aA0.r + aA1.r) * (b1.r - b0.r),
-                                            M<T>::sqrt_(yxr * yxr + yyr * yyr), hh);
-                }
-                const T fxmD = shup(fxD[1]), fxmA = shup(fxA[1]);
-                sDL = fxD[0] - fxmD + fyD[0] - cFYm_D[0];
-                sDR = fxD[1] - fxD[0] + fyD[1] - cFYm_D[1];
-                sAL = fxA[0] - fxmA + fyA[0] - cFYm_A[0];
-                sAR = fxA[1] - fxA[0] + fyA[1] - cFYm_A[1];
-                cFYm_D[0] = fyD[0];
-                cFYm_D[1] = fyD[1];
-                cFYm_A[0] = fyA[0];
-                cFYm_A[1] = fyA[1];
+                const V<T> half = bc<T>(T(0.5));
+                const V<T> fxD = half * (aD0.C() + aD0.E()) * (bU0.E() - bU0.C());
+                const V<T> fyD = half * (aD0.C() + aD1.C()) * (bU1.C() - bU0.C());
+                const Row<T>& bm = Pq[1];
+                const V<T> dxp = b0.E() - b0.C(), dyp = b1.C() - b0.C();
+                const V<T> gx = dxp * bc<T>(ih), gy = ((b1.E() + b1.C()) - (bm.E() + bm.C())) * bc<T>(i4h);
+                const V<T> yx = ((b1.E() + b0.E()) - (b1.W() + b0.W())) * bc<T>(i4h), yy = dyp * bc<T>(ih);
+                const V<T> mx = fma(gx, gx, gy * gy), my = fma(yx, yx, yy * yy);
+                const V<T> fxA = guarded_div2<T>(half * (aA0.C() + aA0.E()) * dxp,
+                                                 mk(M<T>::sqrt_(mx.x()), M<T>::sqrt_(mx.y())), hh);
+                const V<T> fyA = guarded_div2<T>(half * (aA0.C() + aA1.C()) * dyp,
+                                                 mk(M<T>::sqrt_(my.x()), M<T>::sqrt_(my.y())), hh);
+                sD = (fxD - mk(shup(fxD.y()), fxD.x())) + (fyD - cFYm_D);
+                sA = (fxA - mk(shup(fxA.y()), fxA.x())) + (fyA - cFYm_A);
+                cFYm_D = fyD;
+                cFYm_A = fyA;
                 return;
             }
-            // corner means: the (+1/2, +1/2) corner of columns L-1, L, R at row q
-            const T KDm = T(0.25) * (aD0.m1 + aD0.l + aD1.m1 + aD1.l);
-            const T KDl = T(0.25) * (aD0.l + aD0.r + aD1.l + aD1.r);
-            const T KDr = T(0.25) * (aD0.r + aD0.p1 + aD1.r + aD1.p1);
-            const T KAm = T(0.25) * (aA0.m1 + aA0.l + aA1.m1 + aA1.l);
-            const T KAl = T(0.25) * (aA0.l + aA0.r + aA1.l + aA1.r);
-            const T KAr = T(0.25) * (aA0.r + aA0.p1 + aA1.r + aA1.p1);
-            // <10> faces x+, y+ (weight sum of Eq. flux_10) and <11> corners ++, -+
-            const T FXpD_L = (aD0.l + aD0.r + KDl + cK_D[0]) * (bU0.r - bU0.l);
-            const T FXpD_R = (aD0.r + aD0.p1 + KDr + cK_D[1]) * (bU0.p1 - bU0.r);
-            const T FYpD_L = (aD0.l + aD1.l + KDl + KDm) * (bU1.l - bU0.l);
-            const T FYpD_R = (aD0.r + aD1.r + KDr + KDl) * (bU1.r - bU0.r);
-            const T FPPD_L = KDl * (bU1.r - bU0.l), FPPD_R = KDr * (bU1.p1 - bU0.r);
-            const T FMPD_L = KDm * (bU1.m1 - bU0.l), FMPD_R = KDl * (bU1.l - bU0.r);
-            T FXpA_L = (aA0.l + aA0.r + KAl + cK_A[0]) * (b0.r - b0.l);
-            T FXpA_R = (aA0.r + aA0.p1 + KAr + cK_A[1]) * (b0.p1 - b0.r);
-            T FYpA_L = (aA0.l + aA1.l + KAl + KAm) * (b1.l - b0.l);
-            T FYpA_R = (aA0.r + aA1.r + KAr + KAl) * (b1.r - b0.r);
-            T FPPA_L = KAl * (b1.r - b0.l), FPPA_R = KAr * (b1.p1 - b0.r);
-            T FMPA_L = KAm * (b1.m1 - b0.l), FMPA_R = KAl * (b1.l - b0.r);
+            const V<T> q4 = bc<T>(T(0.25));
+            // corner means: the (+1/2, +1/2) corners of (L, R) and of (L-1, L)
+            const V<T> KC_D = q4 * ((aD0.C() + aD0.E()) + (aD1.C() + aD1.E()));
+            const V<T> KW_D = q4 * ((aD0.W() + aD0.C()) + (aD1.W() + aD1.C()));
+            const V<T> KC_A = q4 * ((aA0.C() + aA0.E()) + (aA1.C() + aA1.E()));
+            const V<T> KW_A = q4 * ((aA0.W() + aA0.C()) + (aA1.W() + aA1.C()));
+            // <10> faces x+, y+ (weight sums of Eq. flux_10) and <11> corners ++, -+
+            const V<T> u0c = bU0.C();
+            const V<T> FXpD = ((aD0.C() + aD0.E()) + (KC_D + cK_D)) * (bU0.E() - u0c);
+            const V<T> FYpD = ((aD0.C() + aD1.C()) + (KC_D + KW_D)) * (bU1.C() - u0c);
+            const V<T> FPPD = KC_D * (bU1.E() - u0c), FMPD = KW_D * (bU1.W() - u0c);
+            const V<T> p0c = b0.C();
+            V<T> FXpA = ((aA0.C() + aA0.E()) + (KC_A + cK_A)) * (b0.E() - p0c);
+            V<T> FYpA = ((aA0.C() + aA1.C()) + (KC_A + KW_A)) * (b1.C() - p0c);
+            V<T> FPPA = KC_A * (b1.E() - p0c), FMPA = KW_A * (b1.W() - p0c);
             if (S == S21) {
                 // App. B: each anti-trapping flux divided by |grad psi| at its point;
-                // ps(dx, dy) = psi at column L + dx, row q + dy
-                auto ps = [&](int dx, int dy) -> T { return Pq[2 + dy].at(dx); };
-                if (need_x) {
-                    FXpA_L = guarded_div<T>(FXpA_L, appb_face<T>([&](int p, int t) { return ps(p, t); }, ih), hh);
-                    FXpA_R =
-                        guarded_div<T>(FXpA_R, appb_face<T>([&](int p, int t) { return ps(1 + p, t); }, ih), hh);
-                }
-                FYpA_L = guarded_div<T>(FYpA_L, appb_face<T>([&](int p, int t) { return ps(t, p); }, ih), hh);
-                FYpA_R = guarded_div<T>(FYpA_R, appb_face<T>([&](int p, int t) { return ps(1 + t, p); }, ih), hh);
-                FPPA_L = guarded_div<T>(FPPA_L, appb_corner<T>([&](int p, int t) { return ps(p, t); }, ih), hh);
-                FPPA_R =
-                    guarded_div<T>(FPPA_R, appb_corner<T>([&](int p, int t) { return ps(1 + p, t); }, ih), hh);
-                FMPA_L =
-                    guarded_div<T>(FMPA_L, appb_corner<T>([&](int p, int t) { return ps(p - 1, t); }, ih), hh);
-                FMPA_R = guarded_div<T>(FMPA_R, appb_corner<T>([&](int p, int t) { return ps(p, t); }, ih), hh);
+                // ps(dx, dy) = psi at columns (L + dx, R + dx), row q + dy
+                auto ps = [&](int dx, int dy) -> V<T> { return Pq[2 + dy].pat(dx); };
+                if (need_x)
+                    FXpA = guarded_div2<T>(FXpA, appb_face2<T>([&](int p, int t) { return ps(p, t); }, ih), hh);
+                FYpA = guarded_div2<T>(FYpA, appb_face2<T>([&](int p, int t) { return ps(t, p); }, ih), hh);
+                FPPA = guarded_div2<T>(FPPA, appb_corner2<T>([&](int p, int t) { return ps(p, t); }, ih), hh);
+                FMPA = guarded_div2<T>(FMPA, appb_corner2<T>([&](int p, int t) { return ps(p - 1, t); }, ih), hh);
             }
-            const T FXmD_L = shup(FXpD_R), FXmA_L = shup(FXpA_R);
-            sDL = FXpD_L - FXmD_L + FYpD_L - cFYm_D[0] + FPPD_L + FMPD_L - cFDmm_D[0] - cFDpm_D[0];
-            sDR = FXpD_R - FXpD_L + FYpD_R - cFYm_D[1] + FPPD_R + FMPD_R - cFDmm_D[1] - cFDpm_D[1];
-            sAL = FXpA_L - FXmA_L + FYpA_L - cFYm_A[0] + FPPA_L + FMPA_L - cFDmm_A[0] - cFDpm_A[0];
-            sAR = FXpA_R - FXpA_L + FYpA_R - cFYm_A[1] + FPPA_R + FMPA_R - cFDmm_A[1] - cFDpm_A[1];
+            sD = ((FXpD - mk(shup(FXpD.y()), FXpD.x())) + (FYpD - cFYm_D)) + ((FPPD + FMPD) - (cFDmm_D + cFDpm_D));
+            sA = ((FXpA - mk(shup(FXpA.y()), FXpA.x())) + (FYpA - cFYm_A)) + ((FPPA + FMPA) - (cFDmm_A + cFDpm_A));
             // carries for row q+1: its y- face is this y+ face, its (-1/2,-1/2)
-            // corner is the (+1/2,+1/2) corner of the column to the left, its
+            // corner the (+1/2,+1/2) corner of the column to the left, its
             // (+1/2,-1/2) corner the (-1/2,+1/2) corner of the column to the right
-            cFYm_D[0] = FYpD_L;
-            cFYm_D[1] = FYpD_R;
-            cFYm_A[0] = FYpA_L;
-            cFYm_A[1] = FYpA_R;
-            cFDmm_D[0] = shup(FPPD_R);
-            cFDmm_D[1] = FPPD_L;
-            cFDmm_A[0] = shup(FPPA_R);
-            cFDmm_A[1] = FPPA_L;
-            cFDpm_D[0] = FMPD_R;
-            cFDpm_D[1] = shdn(FMPD_L);
-            cFDpm_A[0] = FMPA_R;
-            cFDpm_A[1] = shdn(FMPA_L);
-            cK_D[0] = KDl;
-            cK_D[1] = KDr;
-            cK_A[0] = KAl;
-            cK_A[1] = KAr;
+            cFYm_D = FYpD;
+            cFYm_A = FYpA;
+            cFDmm_D = mk(shup(FPPD.y()), FPPD.x());
+            cFDmm_A = mk(shup(FPPA.y()), FPPA.x());
+            cFDpm_D = mk(FMPD.y(), shdn(FMPD.x()));
+            cFDpm_A = mk(FMPA.y(), shdn(FMPA.x()));
+            cK_D = KC_D;
+            cK_A = KC_A;
         };
         auto alphaD = [&](const Row<T>& ph) {
             Row<T> a;
@@ -462,54 +543,50 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? PF_STEP2D_MIN_BLOCKS_F32
         };
 
         // ---------------- prologue ----------------
-        Row<T> P[5];   // psi rows r-2 .. r+2 (iteration r)
-        Row<T> PH[2];  // phi rows r, r+1
-        Row<T> UU[2];  // U rows r, r+1
-        Row<T> DP[2];  // delta phi rows r, r+1
-        T phinL, phinR;  // phi' at row r
+        Row<T> P[5];      // psi rows r-2 .. r+2 (iteration r)
+        Row<T> PH1, UU0, UU1, DP0;
+        Row<T> AD0, AA0;  // alpha rows of row r
+        V<T> phin_cur;    // phi' at row r
         {
             // psi rows y0-3 .. y0+1 (row y0-3 is read only by S_{2,1}'s x-face
             // magnitudes, which the prologue skips)
             T a, b;
             for (int i = 1; i <= 4; ++i) {
                 fetch_row(psi, y0 - 3 + i, a, b);
-                P[i] = make_row(a, b);
+                P[i] = make_row(a, b, S == S21);
             }
             P[0] = P[1];
-            Row<T> phm = phi_row(P[2]), ph0 = phi_row(P[3]);
+            const Row<T> phm = phi_row(P[2]), ph0 = phi_row(P[3]);
             fetch_row(Uf, y0 - 1, a, b);
-            Row<T> um = make_row(a, b);
+            const Row<T> um = make_row(a, b, false);
             fetch_row(Uf, y0, a, b);
-            Row<T> u0 = make_row(a, b);
+            const Row<T> u0 = make_row(a, b, false);
             // phase 1 at rows y0-1 and y0; the ghost row -1 copies row 0
             int gL, gR;
-            T psL, psR, fL, fR, dLm = T(0), dRm = T(0), dL0, dR0;
+            V<T> psn, fn, dm = bc<T>(T(0)), d0;
             const bool ghost = (y0 - 1) < 0;
             if (!ghost) {
                 load_grain_pair(grain + (size_t)(y0 - 1) * nx, cL, nx, vec, gL, gR);
-                phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, psL, psR, fL, fR, dLm, dRm);
+                phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, psn, fn, dm);
             }
             load_grain_pair(grain + (size_t)y0 * nx, cL, nx, vec, gL, gR);
-            phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, psL, psR, fL, fR, dL0, dR0);
-            if (ghost) {
-                dLm = dL0;
-                dRm = dR0;
-            }
-            phinL = fL;
-            phinR = fR;
-            if (y0 < y1) store_pair<T>(psi_o + (size_t)y0 * nx, cL, vec, outL, outR, psL, psR);
-            const Row<T> dm = dphi_row(dLm, dRm), d0 = dphi_row(dL0, dR0);
+            phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, psn, fn, d0);
+            if (ghost) dm = d0;
+            phin_cur = fn;
+            if (y0 < y1) store_pair<T>(psi_o + (size_t)y0 * nx, cL, vec, outL, outR, psn);
+            const Row<T> dmr = dphi_row(dm), d0r = dphi_row(d0);
             // phase-2 fluxes at row y0-1 (carries only); psi rows y0-3 .. y0+1
-            T s0, s1, s2, s3;
-            fluxes(alphaD(phm), alphaD(ph0), alphaA(um, dm), alphaA(u0, d0), um, u0, P, false, s0, s1, s2, s3);
-            // ring state for iteration r = y0
+            const Row<T> aDm = alphaD(phm), aAm = alphaA(um, dmr);
+            AD0 = alphaD(ph0);
+            AA0 = alphaA(u0, d0r);
+            V<T> s0, s1;
+            fluxes(aDm, AD0, aAm, AA0, um, u0, P, false, s0, s1);
             P[0] = P[1];
             P[1] = P[2];
             P[2] = P[3];
             P[3] = P[4];
-            PH[0] = ph0;
-            UU[0] = u0;
-            DP[0] = d0;
+            UU0 = u0;
+            DP0 = d0r;
         }
 
         // prefetch psi row y0+2 and U, grain row y0+1
@@ -521,47 +598,47 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? PF_STEP2D_MIN_BLOCKS_F32
 
         // ---------------- sweep ----------------
         for (int r = y0; r < y1; ++r) {
-            P[4] = make_row(nPa, nPb);
-            UU[1] = make_row(nUa, nUb);
-            PH[1] = phi_row(P[3]);
+            P[4] = make_row(nPa, nPb, S == S21);
+            UU1 = make_row(nUa, nUb, false);
+            PH1 = phi_row(P[3]);
             const int gL = nGa, gR = nGb;
             fetch_row(psi, r + 3, nPa, nPb);
             fetch_row(Uf, r + 2, nUa, nUb);
             if (r + 2 < ny) load_grain_pair(grain + (size_t)(r + 2) * nx, cL, nx, vec, nGa, nGb);
 
             // phase 1 at row r+1
-            T phnL = T(0), phnR = T(0);
+            V<T> phn = bc<T>(T(0));
+            Row<T> DP1;
             if (r + 1 < ny) {
-                T psL, psR, dL, dR;
-                phase1(r + 1, P[2], P[3], P[4], PH[1], UU[1], gL, gR, psL, psR, phnL, phnR, dL, dR);
-                if (r + 1 < y1) store_pair<T>(psi_o + (size_t)(r + 1) * nx, cL, vec, outL, outR, psL, psR);
-                DP[1] = dphi_row(dL, dR);
+                V<T> psn, d;
+                phase1(r + 1, P[2], P[3], P[4], PH1, UU1, gL, gR, psn, phn, d);
+                if (r + 1 < y1) store_pair<T>(psi_o + (size_t)(r + 1) * nx, cL, vec, outL, outR, psn);
+                DP1 = dphi_row(d);
             } else {
-                DP[1] = DP[0];  // ghost row ny mirrors row ny-1 = r
+                DP1 = DP0;  // ghost row ny mirrors row ny-1 = r
             }
 
             // phase 2 at row r
+            const Row<T> AD1 = alphaD(PH1), AA1 = alphaA(UU1, DP1);
             {
-                T sDL, sDR, sAL, sAR;
-                fluxes(alphaD(PH[0]), alphaD(PH[1]), alphaA(UU[0], DP[0]), alphaA(UU[1], DP[1]), UU[0], UU[1], P,
-                       true, sDL, sDR, sAL, sAR);
+                V<T> sD, sA;
+                fluxes(AD0, AD1, AA0, AA1, UU0, UU1, P, true, sD, sA);
                 const T cs = (S == S10) ? ih2 : i6h2;
-                const T uL = UU[0].l, uR = UU[0].r;
-                const T nL = uL + (dt * (Dc * sDL + sAL) * cs + (T(1) + omk * uL) * DP[0].l) *
-                                      M<T>::rcp(T(1) + kk - omk * phinL);
-                const T nR = uR + (dt * (Dc * sDR + sAR) * cs + (T(1) + omk * uR) * DP[0].r) *
-                                      M<T>::rcp(T(1) + kk - omk * phinR);
-                store_pair<T>(U_o + (size_t)r * nx, cL, vec, outL, outR, nL, nR);
+                const V<T> u = UU0.C();
+                const V<T> num =
+                    fma(bc<T>(dt * cs), fma(bc<T>(Dc), sD, sA), fma(bc<T>(omk), u, bc<T>(T(1))) * DP0.C());
+                const V<T> un = fma(num, rcp2(fma(bc<T>(-omk), phin_cur, bc<T>(T(1) + kk))), u);
+                store_pair<T>(U_o + (size_t)r * nx, cL, vec, outL, outR, un);
             }
-            phinL = phnL;
-            phinR = phnR;
+            phin_cur = phn;
             P[0] = P[1];
             P[1] = P[2];
             P[2] = P[3];
             P[3] = P[4];
-            PH[0] = PH[1];
-            UU[0] = UU[1];
-            DP[0] = DP[1];
+            UU0 = UU1;
+            DP0 = DP1;
+            AD0 = AD1;
+            AA0 = AA1;
         }
     }
 }

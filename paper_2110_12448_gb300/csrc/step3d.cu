@@ -78,6 +78,14 @@ template <typename T> __device__ __forceinline__ T aniso_a3(const T g[3], const 
     return T(1) - T(3) * eps + T(4) * eps * q;
 }
 
+template <typename T> struct ConstOf3;
+template <> struct ConstOf3<float> {
+    static __device__ __forceinline__ const float* get(const InstRec& r) { return r.cf; }
+};
+template <> struct ConstOf3<double> {
+    static __device__ __forceinline__ const double* get(const InstRec& r) { return r.cd; }
+};
+
 template <typename T, int S, int TX, int TY> struct Tile3 {
     static constexpr int AX = TX + 2, AY = TY + 2;  // ring-1 region = threads
     static constexpr int PX = TX + 4, PY = TY + 4;  // psi region (halo 2)
@@ -113,11 +121,12 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
         T* __restrict__ U_o = static_cast<T*>(rec.U[par ^ 1]);
         const int16_t* __restrict__ grain = rec.grain;
         const T* __restrict__ rot = static_cast<const T*>(rec.rot);
-        const T ih = T(1.0 / rec.h), hh = T(rec.h * rec.h), dt = T(rec.dt);
-        const T i4h = T(0.25 / rec.h);
-        const T kk = T(rec.k), omk = T(1.0 - rec.k), eps = T(rec.eps4), lam = T(rec.lambda), Dc = T(rec.D);
-        const T ih2 = T(1.0 / (rec.h * rec.h));
-        const T isq2dt = T(1.0 / (1.41421356237309504880 * rec.dt));
+        const T* cst = ConstOf3<T>::get(rec);
+        const T ih = cst[C_IH], hh = cst[C_HH], dt = cst[C_DT];
+        const T i4h = cst[C_I4H];
+        const T kk = cst[C_K], omk = cst[C_OMK], eps = cst[C_EPS], lam = cst[C_LAM], Dc = cst[C_D];
+        const T ih2 = cst[C_IH2];
+        const T isq2dt = cst[C_ISQ2DT];
         const int x0 = wi.x0, y0 = wi.y0, z0 = wi.z0;
         const int z1 = min(z0 + wi.ext, nz);
 

@@ -3,9 +3,11 @@
 Tolerances:
   * FP64 build: 1e-12 relative per step (max over cells of |d| / max(1, |x|)),
     the figure the design targets for an FP64 GPU build.
-  * FP32 build, one step from an FP64-exact state: FP32 rounding of psi
-    (|psi| up to ~1e2 in the bulk, ulp 8e-6) and of the rates; compared on
-    phi = tanh(psi/sqrt2) and U: 2e-6 absolute.
+  * FP32 build, one step from an FP32-representable state: FP32 rounding of
+    psi (|psi| up to ~1e2 in the bulk, ulp 8e-6) and of the rates; compared on
+    phi = tanh(psi/sqrt2): 2e-6 absolute.  U: the hardware exp2/reciprocal
+    form of tanh errs by <= 2.5e-7 per evaluation, delta phi by <= 5e-7, and U'
+    divides it by 1+k-(1-k)phi' >= 2k = 0.3: 5e-6 absolute.
   * Integer decisions (grain map, tip cell) are bit-exact.
 Grids span several tiles in x (ragged last strip) and several sweeps in y.
 """
@@ -86,7 +88,7 @@ def test_fp32_one_step_matches_oracle(native, scheme):
     phi_g = np.tanh(gp.astype(np.float64) / math.sqrt(2))
     phi_o = np.tanh(op / math.sqrt(2))
     assert max_abs(phi_g, phi_o) < 2e-6
-    assert max_abs(gu, ou) < 2e-6
+    assert max_abs(gu, ou) < 5e-6
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
