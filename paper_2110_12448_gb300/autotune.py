@@ -5,8 +5,10 @@ size) it times each candidate tile -- the sweep length in 2D; the block
 shape and sweep length in 3D -- on synthetic seed states, in one persistent
 launch per step exactly as the batched path runs, and keeps the fastest.
 Wave quantisation (work items vs resident warps or blocks) is what the
-choice mostly trades against the per-sweep prologue, so the answer depends
-on the batch size as well as the grid.  Results are cached per device in
+choice mostly trades against the per-sweep prologue (about 2.5 rows of extra
+work per work item), so the answer depends on the batch size as well as the
+grid; the 2D candidates are dense enough in the sweep length to land close
+below a whole number of waves.  Results are cached per device in
 ``_build/autotune.json``.
 """
 from __future__ import annotations
@@ -15,7 +17,7 @@ import json
 import os
 import threading
 
-CANDIDATES_2D = [(64, 1, s) for s in (16, 24, 32, 48, 64, 96, 128)]
+CANDIDATES_2D = [(64, 1, s) for s in (12, 14, 16, 18, 20, 22, 24, 26, 28, 32, 36, 40, 48, 64, 96, 128)]
 CANDIDATES_3D = [(34, by, s) for by in (18, 10) for s in (16, 32, 64)]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
