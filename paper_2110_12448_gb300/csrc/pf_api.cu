@@ -142,9 +142,9 @@ void default_tile(pf_sim* s) {
         s->by = 1;
         s->sweep = 32;
     } else {
-        // (TX + 4, TY + 4): 30 x 14 output columns in FP32, 30 x 6 in FP64
+        // (TX + 4, TY + 4): 30 x 6 output columns
         s->bx = 34;
-        s->by = s->p.precision == PF_F64 ? 10 : 18;
+        s->by = 10;
         s->sweep = 32;
     }
 }

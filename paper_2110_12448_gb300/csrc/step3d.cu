@@ -90,7 +90,12 @@ template <typename T, int S, int TX, int TY> struct Tile3 {
     static constexpr int AX = TX + 2, AY = TY + 2;  // ring-1 region = threads
     static constexpr int PX = TX + 4, PY = TY + 4;  // psi region (halo 2)
     static constexpr int NT = AX * AY;
-    static constexpr size_t smem = sizeof(T) * (8 * PX * PY + 8 * NT + 4 * NT + 4 * NT);
+    // owned phase-2 fluxes per field: in-plane (+x, +y faces [, +x+y, +x-y
+    // edges]) and toward the next plane (+z face [, +x+z, -x+z, +y+z, -y+z])
+    static constexpr int NFI = (S == SBAR120) ? 4 : 2;
+    static constexpr int NFZ = (S == SBAR120) ? 5 : 1;
+    static constexpr size_t smem =
+        sizeof(T) * (8 * PX * PY + 8 * NT + 4 * NT + 4 * NT + 2 * 4 * NT + 2 * NFI * NT + 2 * 2 * NFZ * NT);
 };
 
 template <typename T, int S, int TX, int TY>
@@ -98,12 +103,17 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                                                               const InstRec* __restrict__ recs, int launch_parity) {
     using TL = Tile3<T, S, TX, TY>;
     constexpr int AX = TL::AX, AY = TL::AY, PX = TL::PX, PY = TL::PY, NT = TL::NT;
+    constexpr int NFI = TL::NFI, NFZ = TL::NFZ;
     constexpr bool ISO = (S == SBAR120);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s_psi = reinterpret_cast<T*>(smem_raw);  // [8][PY][PX]
     T* s_phi = s_psi + 8 * PX * PY;             // [8][AY][AX]
     T* s_U = s_phi + 8 * NT;                    // [4][AY][AX]
     T* s_dphi = s_U + 4 * NT;                   // [4][AY][AX]
+    T* s_aD = s_dphi + 4 * NT;                  // [4][AY][AX] alpha of D = 1 - phi
+    T* s_aA = s_aD + 4 * NT;                    // [4][AY][AX] alpha of the anti-trapping term
+    T* s_fi = s_aA + 4 * NT;                    // [2 fields][NFI][NT] owned in-plane fluxes
+    T* s_fz = s_fi + 2 * NFI * NT;              // [2 buffers][2 fields][NFZ][NT] owned fluxes to the next plane
     const int tid = threadIdx.x;
     const int tx = tid % AX, ty = tid / AX;
     const T SQ2 = T(1.41421356237309504880);
@@ -158,7 +168,12 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             RG(s_U, 4, vz, ty, tx) = __ldg(Uf + rz * sxy + (long long)my * nx + mx);
         };
 
-        // phase 1 at real plane p for the cell (mx, my, p); returns phi', writes delta phi
+        // anisotropy: the +z face of the cell's previous plane is its -z face
+        T qz_c = T(0);
+        int gz_c = -1, pz_c = -100;
+
+        // phase 1 at real plane p for the cell (mx, my, p); returns phi',
+        // writes delta phi and the alphas of the U equation for this slot
         auto phase1 = [&](int p, T& psin) -> T {
             const int g = grain[p * sxy + (long long)my * nx + mx];
             T R[9];
@@ -166,13 +181,13 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             for (int q = 0; q < 9; ++q) R[q] = __ldg(rot + 9 * g + q);
             auto P = [&](int dx, int dy, int dz) -> T { return PS(p + dz, jy + dy, jx + dx); };
             const T pc = P(0, 0, 0);
-            T s100 = T(0), s110 = T(0);
-            s100 = P(1, 0, 0) + P(-1, 0, 0) + P(0, 1, 0) + P(0, -1, 0) + P(0, 0, 1) + P(0, 0, -1);
+            const T s100 = P(1, 0, 0) + P(-1, 0, 0) + P(0, 1, 0) + P(0, -1, 0) + P(0, 0, 1) + P(0, 0, -1);
             T L, G;
             {
                 const T ex = P(1, 0, 0) - P(-1, 0, 0), ey = P(0, 1, 0) - P(0, -1, 0), ez = P(0, 0, 1) - P(0, 0, -1);
                 const T g100 = (ex * ex + ey * ey + ez * ez) * T(0.25) * ih2;
                 if (ISO) {
+                    T s110 = T(0);
 #pragma unroll
                     for (int a = -1; a <= 1; a += 2)
 #pragma unroll
@@ -188,29 +203,29 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                     G = g100;
                 }
             }
-            // six <100> faces
-            T N = T(0);
+            // <100> faces; the -z face comes from the plane below when valid
+            auto face = [&](int ax, int sg) -> T {
+                const int e[3] = {ax == 0 ? sg : 0, ax == 1 ? sg : 0, ax == 2 ? sg : 0};
+                T gf[3];
 #pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-#pragma unroll
-                for (int sg = -1; sg <= 1; sg += 2) {
-                    const int e[3] = {ax == 0 ? sg : 0, ax == 1 ? sg : 0, ax == 2 ? sg : 0};
-                    T gf[3];
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        if (q == ax) {
-                            gf[q] = (P(e[0], e[1], e[2]) - pc) * ih * T(sg);
-                        } else {
-                            const int t[3] = {q == 0, q == 1, q == 2};
-                            gf[q] = (P(e[0] + t[0], e[1] + t[1], e[2] + t[2]) + P(t[0], t[1], t[2]) -
-                                     P(e[0] - t[0], e[1] - t[1], e[2] - t[2]) - P(-t[0], -t[1], -t[2])) *
-                                    i4h;
-                        }
+                for (int q = 0; q < 3; ++q) {
+                    if (q == ax) {
+                        gf[q] = (P(e[0], e[1], e[2]) - pc) * ih * T(sg);
+                    } else {
+                        const int t[3] = {q == 0, q == 1, q == 2};
+                        gf[q] = (P(e[0] + t[0], e[1] + t[1], e[2] + t[2]) + P(t[0], t[1], t[2]) -
+                                 P(e[0] - t[0], e[1] - t[1], e[2] - t[2]) - P(-t[0], -t[1], -t[2])) *
+                                i4h;
                     }
-                    N += T(sg) * aniso_q3<T>(gf, R, eps, hh, ax);
                 }
-            }
-            N *= ih;
+                return aniso_q3<T>(gf, R, eps, hh, ax);
+            };
+            const T qzp = face(2, 1);
+            const T qzm = (pz_c == p && gz_c == g) ? qz_c : face(2, -1);
+            qz_c = qzp;
+            gz_c = g;
+            pz_c = p + 1;
+            const T N = ((face(0, 1) - face(0, -1)) + (face(1, 1) - face(1, -1)) + (qzp - qzm)) * ih;
             T gc[3] = {(P(1, 0, 0) - P(-1, 0, 0)) * T(0.5) * ih, (P(0, 1, 0) - P(0, -1, 0)) * T(0.5) * ih,
                        (P(0, 0, 1) - P(0, 0, -1)) * T(0.5) * ih};
             const T ac = aniso_a3<T>(gc, R, eps, hh);
@@ -219,8 +234,175 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             const T rate = (L + N + SQ2 * (ph - lam * (T(1) - ph * ph) * u)) * M3<T>::rcp(ac * ac) - SQ2 * ph * G;
             psin = pc + dt * rate;
             const T phn = M3<T>::tanh_(psin * ISQ2);
-            RG(s_dphi, 4, p, ty, tx) = phn - ph;
+            const T dph = phn - ph;
+            RG(s_dphi, 4, p, ty, tx) = dph;
+            RG(s_aD, 4, p, ty, tx) = T(1) - ph;
+            RG(s_aA, 4, p, ty, tx) = (T(1) + omk * u) * dph * isq2dt;
             return phn;
+        };
+        // ghost plane vz takes the slot values of plane mz
+        auto copy_plane = [&](int vz, int mz) {
+            RG(s_dphi, 4, vz, ty, tx) = RG(s_dphi, 4, mz, ty, tx);
+            RG(s_aD, 4, vz, ty, tx) = RG(s_aD, 4, mz, ty, tx);
+            RG(s_aA, 4, vz, ty, tx) = RG(s_aA, 4, mz, ty, tx);
+        };
+
+        // Owned phase-2 fluxes of this ring cell: in-plane at plane r (into
+        // s_fi) and toward plane r+1 (into s_fz[buf]).  A flux is stored times
+        // 6 h^2 for D~_{1,2,0} (faces weight 2, edges weight 1) and times h^2
+        // for S_{1,0,0}; fluxes whose stencil leaves the ring region are set to
+        // zero (no output cell uses them).
+        auto owned_fluxes = [&](int r, int buf) {
+            auto aD = [&](int dx, int dy, int dz) -> T { return RG(s_aD, 4, r + dz, ty + dy, tx + dx); };
+            auto aA = [&](int dx, int dy, int dz) -> T { return RG(s_aA, 4, r + dz, ty + dy, tx + dx); };
+            auto bU = [&](int dx, int dy, int dz) -> T { return RG(s_U, 4, r + dz, ty + dy, tx + dx); };
+            auto bP = [&](int dx, int dy, int dz) -> T { return PS(r + dz, ty + 1 + dy, tx + 1 + dx); };
+            const bool xm = tx >= 1, xp = tx + 1 < AX, ym = ty >= 1, yp = ty + 1 < AY;
+            T* fiD = s_fi + tid;
+            T* fiA = s_fi + NFI * NT + tid;
+            T* fzD = s_fz + (buf * 2 * NFZ) * NT + tid;
+            T* fzA = s_fz + (buf * 2 * NFZ + NFZ) * NT + tid;
+            const T u0 = bU(0, 0, 0), p0 = bP(0, 0, 0);
+            // face toward e: returns (D, A) flux
+            auto face = [&](const int e[3], T& fD, T& fA) {
+                if (ISO) {
+                    T nD = aD(0, 0, 0) + aD(e[0], e[1], e[2]), nA = aA(0, 0, 0) + aA(e[0], e[1], e[2]);
+                    T mD = T(0), mA = T(0);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (e[q] != 0) continue;
+#pragma unroll
+                        for (int s2 = -1; s2 <= 1; s2 += 2) {
+                            const int t[3] = {q == 0 ? s2 : 0, q == 1 ? s2 : 0, q == 2 ? s2 : 0};
+                            mD += aD(t[0], t[1], t[2]) + aD(e[0] + t[0], e[1] + t[1], e[2] + t[2]);
+                            mA += aA(t[0], t[1], t[2]) + aA(e[0] + t[0], e[1] + t[1], e[2] + t[2]);
+                        }
+                    }
+                    fD = T(2) * (T(0.25) * nD + T(1.0 / 16.0) * mD) * (bU(e[0], e[1], e[2]) - u0);
+                    fA = T(2) * (T(0.25) * nA + T(1.0 / 16.0) * mA) * (bP(e[0], e[1], e[2]) - p0);
+                } else {
+                    fD = T(0.5) * (aD(0, 0, 0) + aD(e[0], e[1], e[2])) * (bU(e[0], e[1], e[2]) - u0);
+                    T gf[3];
+                    int ax = e[0] != 0 ? 0 : (e[1] != 0 ? 1 : 2);
+                    const int sg = e[ax];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (q == ax) {
+                            gf[q] = (bP(e[0], e[1], e[2]) - p0) * ih * T(sg);
+                        } else {
+                            const int t[3] = {q == 0, q == 1, q == 2};
+                            gf[q] = (bP(e[0] + t[0], e[1] + t[1], e[2] + t[2]) + bP(t[0], t[1], t[2]) -
+                                     bP(e[0] - t[0], e[1] - t[1], e[2] - t[2]) - bP(-t[0], -t[1], -t[2])) *
+                                    i4h;
+                        }
+                    }
+                    const T m2 = gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2];
+                    fA = (m2 * hh < Guard<T>::v) ? T(0)
+                                                  : T(0.5) * (aA(0, 0, 0) + aA(e[0], e[1], e[2])) *
+                                                        (bP(e[0], e[1], e[2]) - p0) * M3<T>::rcp(M3<T>::sqrt_(m2));
+                }
+            };
+            // edge toward d = e1 + e2 (e3 the third axis)
+            auto edge = [&](const int e1[3], const int e2[3], int ax3, T& fD, T& fA) {
+                const int d[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
+                T nD = aD(0, 0, 0) + aD(e1[0], e1[1], e1[2]) + aD(e2[0], e2[1], e2[2]) + aD(d[0], d[1], d[2]);
+                T nA = aA(0, 0, 0) + aA(e1[0], e1[1], e1[2]) + aA(e2[0], e2[1], e2[2]) + aA(d[0], d[1], d[2]);
+                T mD = T(0), mA = T(0);
+#pragma unroll
+                for (int s3 = -1; s3 <= 1; s3 += 2) {
+                    int t[3] = {0, 0, 0};
+                    t[ax3] = s3;
+                    mD += aD(t[0], t[1], t[2]) + aD(e1[0] + t[0], e1[1] + t[1], e1[2] + t[2]) +
+                          aD(e2[0] + t[0], e2[1] + t[1], e2[2] + t[2]) + aD(d[0] + t[0], d[1] + t[1], d[2] + t[2]);
+                    mA += aA(t[0], t[1], t[2]) + aA(e1[0] + t[0], e1[1] + t[1], e1[2] + t[2]) +
+                          aA(e2[0] + t[0], e2[1] + t[1], e2[2] + t[2]) + aA(d[0] + t[0], d[1] + t[1], d[2] + t[2]);
+                }
+                fD = (T(3.0 / 16.0) * nD + T(1.0 / 32.0) * mD) * (bU(d[0], d[1], d[2]) - u0);
+                fA = (T(3.0 / 16.0) * nA + T(1.0 / 32.0) * mA) * (bP(d[0], d[1], d[2]) - p0);
+            };
+            T fD, fA;
+            // in-plane: +x face, +y face [, +x+y, +x-y edges]
+            {
+                const int e[3] = {1, 0, 0};
+                fD = fA = T(0);
+                if (xp && ym && yp) face(e, fD, fA);
+                fiD[0] = fD;
+                fiA[0] = fA;
+            }
+            {
+                const int e[3] = {0, 1, 0};
+                fD = fA = T(0);
+                if (yp && xm && xp) face(e, fD, fA);
+                fiD[NT] = fD;
+                fiA[NT] = fA;
+            }
+            if (ISO) {
+                const int ex[3] = {1, 0, 0}, eyp[3] = {0, 1, 0}, eym[3] = {0, -1, 0};
+                fD = fA = T(0);
+                if (xp && yp) edge(ex, eyp, 2, fD, fA);
+                fiD[2 * NT] = fD;
+                fiA[2 * NT] = fA;
+                fD = fA = T(0);
+                if (xp && ym) edge(ex, eym, 2, fD, fA);
+                fiD[3 * NT] = fD;
+                fiA[3 * NT] = fA;
+            }
+            // toward plane r+1: +z face [, +x+z, -x+z, +y+z, -y+z edges]
+            {
+                const int e[3] = {0, 0, 1};
+                fD = fA = T(0);
+                if (xm && xp && ym && yp) face(e, fD, fA);
+                fzD[0] = fD;
+                fzA[0] = fA;
+            }
+            if (ISO) {
+                const int ez[3] = {0, 0, 1}, exp_[3] = {1, 0, 0}, exm[3] = {-1, 0, 0}, eyp[3] = {0, 1, 0},
+                          eym[3] = {0, -1, 0};
+                fD = fA = T(0);
+                if (xp && ym && yp) edge(exp_, ez, 1, fD, fA);
+                fzD[NT] = fD;
+                fzA[NT] = fA;
+                fD = fA = T(0);
+                if (xm && ym && yp) edge(exm, ez, 1, fD, fA);
+                fzD[2 * NT] = fD;
+                fzA[2 * NT] = fA;
+                fD = fA = T(0);
+                if (yp && xm && xp) edge(eyp, ez, 0, fD, fA);
+                fzD[3 * NT] = fD;
+                fzA[3 * NT] = fA;
+                fD = fA = T(0);
+                if (ym && xm && xp) edge(eym, ez, 0, fD, fA);
+                fzD[4 * NT] = fD;
+                fzA[4 * NT] = fA;
+            }
+        };
+        // eight/eighteen-flux sums of an output cell at plane r: own fluxes
+        // plus the negated owned fluxes of the neighbours that share them
+        auto flux_sum = [&](int bufz_cur, int bufz_prev, T& sD, T& sA) {
+            auto FI = [&](int f, int k, int dx, int dy) -> T { return s_fi[(f * NFI + k) * NT + tid + dy * AX + dx]; };
+            auto FZ = [&](int b, int f, int k, int dx, int dy) -> T {
+                return s_fz[((b * 2 + f) * NFZ + k) * NT + tid + dy * AX + dx];
+            };
+            T s[2];
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                T a = (FI(f, 0, 0, 0) - FI(f, 0, -1, 0)) + (FI(f, 1, 0, 0) - FI(f, 1, 0, -1));
+                a += FZ(bufz_cur, f, 0, 0, 0) - FZ(bufz_prev, f, 0, 0, 0);
+                if (ISO) {
+                    // in-plane edges: own +x+y, +x-y; received -x-y from (-1,-1), -x+y from (-1,+1)
+                    a += (FI(f, 2, 0, 0) - FI(f, 2, -1, -1)) + (FI(f, 3, 0, 0) - FI(f, 3, -1, 1));
+                    // edges to the next plane (own) and from the previous plane (received):
+                    // +x-z = -(-x+z of (+1,0)), -x-z = -(+x+z of (-1,0)),
+                    // +y-z = -(-y+z of (0,+1)), -y-z = -(+y+z of (0,-1))
+                    a += (FZ(bufz_cur, f, 1, 0, 0) + FZ(bufz_cur, f, 2, 0, 0) + FZ(bufz_cur, f, 3, 0, 0) +
+                          FZ(bufz_cur, f, 4, 0, 0)) -
+                         (FZ(bufz_prev, f, 2, 1, 0) + FZ(bufz_prev, f, 1, -1, 0) + FZ(bufz_prev, f, 4, 0, 1) +
+                          FZ(bufz_prev, f, 3, 0, -1));
+                }
+                s[f] = a;
+            }
+            sD = s[0];
+            sA = s[1];
         };
 
         // ---- prologue ----
@@ -231,15 +413,17 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
         T phin_cur = T(0);
         if (do_p1) {
             T psn;
-            phin_cur = phase1(z0, psn);
-            if (do_p2 && z0 < z1) psi_o[z0 * sxy + (long long)vy * nx + vx] = psn;
             if (z0 - 1 >= 0) {
                 T d;
                 (void)phase1(z0 - 1, d);
-            } else {
-                RG(s_dphi, 4, z0 - 1, ty, tx) = RG(s_dphi, 4, z0, ty, tx);
             }
+            phin_cur = phase1(z0, psn);
+            if (do_p2 && z0 < z1) psi_o[z0 * sxy + (long long)vy * nx + vx] = psn;
+            if (z0 - 1 < 0) copy_plane(z0 - 1, z0);
         }
+        __syncthreads();
+        // fluxes from plane z0-1 to z0 (buffer of plane z0-1)
+        owned_fluxes(z0 - 1, (z0 - 1) & 1);
         __syncthreads();
 
         for (int r = z0; r < z1; ++r) {
@@ -253,110 +437,20 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                     phin_next = phase1(r + 1, psn);
                     if (do_p2 && r + 1 < z1) psi_o[(r + 1) * sxy + (long long)vy * nx + vx] = psn;
                 } else {
-                    RG(s_dphi, 4, r + 1, ty, tx) = RG(s_dphi, 4, r, ty, tx);
+                    copy_plane(r + 1, r);
                 }
             }
             __syncthreads();
+            owned_fluxes(r, r & 1);
+            __syncthreads();
             if (do_p2) {
-                // 3x3x3 neighbourhoods around (tx, ty, r) in the ring region
-                auto PH = [&](int dx, int dy, int dz) -> T { return RG(s_phi, 8, r + dz, ty + dy, tx + dx); };
-                auto UU = [&](int dx, int dy, int dz) -> T { return RG(s_U, 4, r + dz, ty + dy, tx + dx); };
-                auto DP = [&](int dx, int dy, int dz) -> T { return RG(s_dphi, 4, r + dz, ty + dy, tx + dx); };
-                auto PSI = [&](int dx, int dy, int dz) -> T { return PS(r + dz, ty + 1 + dy, tx + 1 + dx); };
-                auto aD = [&](int dx, int dy, int dz) -> T { return T(1) - PH(dx, dy, dz); };
-                auto aA = [&](int dx, int dy, int dz) -> T {
-                    return (T(1) + omk * UU(dx, dy, dz)) * DP(dx, dy, dz) * isq2dt;
-                };
-                T Dt = T(0), At = T(0);
-                const T u0 = UU(0, 0, 0), p0 = PSI(0, 0, 0);
-                if (ISO) {
-                    // D~_{1,2,0} * 6 h^2 = 2 sum_<100> abar db + sum_<110> abar db
-                    T sD = T(0), sA = T(0);
-#pragma unroll
-                    for (int ax = 0; ax < 3; ++ax)
-#pragma unroll
-                        for (int sg = -1; sg <= 1; sg += 2) {
-                            const int e[3] = {ax == 0 ? sg : 0, ax == 1 ? sg : 0, ax == 2 ? sg : 0};
-                            T nD = aD(0, 0, 0) + aD(e[0], e[1], e[2]);
-                            T nA = aA(0, 0, 0) + aA(e[0], e[1], e[2]);
-                            T mD = T(0), mA = T(0);
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) {
-                                if (q == ax) continue;
-#pragma unroll
-                                for (int s2 = -1; s2 <= 1; s2 += 2) {
-                                    const int t[3] = {q == 0 ? s2 : 0, q == 1 ? s2 : 0, q == 2 ? s2 : 0};
-                                    mD += aD(t[0], t[1], t[2]) + aD(e[0] + t[0], e[1] + t[1], e[2] + t[2]);
-                                    mA += aA(t[0], t[1], t[2]) + aA(e[0] + t[0], e[1] + t[1], e[2] + t[2]);
-                                }
-                            }
-                            const T abD = T(0.25) * nD + T(1.0 / 16.0) * mD;
-                            const T abA = T(0.25) * nA + T(1.0 / 16.0) * mA;
-                            sD += T(2) * abD * (UU(e[0], e[1], e[2]) - u0);
-                            sA += T(2) * abA * (PSI(e[0], e[1], e[2]) - p0);
-                        }
-#pragma unroll
-                    for (int ax3 = 0; ax3 < 3; ++ax3)
-#pragma unroll
-                        for (int s1 = -1; s1 <= 1; s1 += 2)
-#pragma unroll
-                            for (int s2 = -1; s2 <= 1; s2 += 2) {
-                                int e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
-                                const int a1 = ax3 == 0 ? 1 : 0, a2 = ax3 == 2 ? 1 : 2;
-                                e1[a1] = s1;
-                                e2[a2] = s2;
-                                const int d[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
-                                T nD = aD(0, 0, 0) + aD(e1[0], e1[1], e1[2]) + aD(e2[0], e2[1], e2[2]) + aD(d[0], d[1], d[2]);
-                                T nA = aA(0, 0, 0) + aA(e1[0], e1[1], e1[2]) + aA(e2[0], e2[1], e2[2]) + aA(d[0], d[1], d[2]);
-                                T mD = T(0), mA = T(0);
-#pragma unroll
-                                for (int s3 = -1; s3 <= 1; s3 += 2) {
-                                    int t[3] = {0, 0, 0};
-                                    t[ax3] = s3;
-                                    mD += aD(t[0], t[1], t[2]) + aD(e1[0] + t[0], e1[1] + t[1], e1[2] + t[2]) +
-                                          aD(e2[0] + t[0], e2[1] + t[1], e2[2] + t[2]) + aD(d[0] + t[0], d[1] + t[1], d[2] + t[2]);
-                                    mA += aA(t[0], t[1], t[2]) + aA(e1[0] + t[0], e1[1] + t[1], e1[2] + t[2]) +
-                                          aA(e2[0] + t[0], e2[1] + t[1], e2[2] + t[2]) + aA(d[0] + t[0], d[1] + t[1], d[2] + t[2]);
-                                }
-                                const T abD = T(3.0 / 16.0) * nD + T(1.0 / 32.0) * mD;
-                                const T abA = T(3.0 / 16.0) * nA + T(1.0 / 32.0) * mA;
-                                sD += abD * (UU(d[0], d[1], d[2]) - u0);
-                                sA += abA * (PSI(d[0], d[1], d[2]) - p0);
-                            }
-                    Dt = sD * T(1.0 / 6.0) * ih2;
-                    At = sA * T(1.0 / 6.0) * ih2;
-                } else {
-                    // S_{1,0,0}: <100> faces, two-point face mean; anti-trapping
-                    // normalised by the face gradient
-                    T sD = T(0), sA = T(0);
-#pragma unroll
-                    for (int ax = 0; ax < 3; ++ax)
-#pragma unroll
-                        for (int sg = -1; sg <= 1; sg += 2) {
-                            const int e[3] = {ax == 0 ? sg : 0, ax == 1 ? sg : 0, ax == 2 ? sg : 0};
-                            sD += T(0.5) * (aD(0, 0, 0) + aD(e[0], e[1], e[2])) * (UU(e[0], e[1], e[2]) - u0);
-                            T gf[3];
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) {
-                                if (q == ax) {
-                                    gf[q] = (PSI(e[0], e[1], e[2]) - p0) * ih * T(sg);
-                                } else {
-                                    const int t[3] = {q == 0, q == 1, q == 2};
-                                    gf[q] = (PSI(e[0] + t[0], e[1] + t[1], e[2] + t[2]) + PSI(t[0], t[1], t[2]) -
-                                             PSI(e[0] - t[0], e[1] - t[1], e[2] - t[2]) - PSI(-t[0], -t[1], -t[2])) *
-                                            i4h;
-                                }
-                            }
-                            const T m2 = gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2];
-                            if (!(m2 * hh < Guard<T>::v))
-                                sA += T(0.5) * (aA(0, 0, 0) + aA(e[0], e[1], e[2])) * (PSI(e[0], e[1], e[2]) - p0) *
-                                      M3<T>::rcp(M3<T>::sqrt_(m2));
-                        }
-                    Dt = sD * ih2;
-                    At = sA * ih2;
-                }
-                const T dph = DP(0, 0, 0);
-                const T un = u0 + (dt * (Dc * Dt + At) + (T(1) + omk * u0) * dph) * M3<T>::rcp(T(1) + kk - omk * phin_cur);
+                T sD, sA;
+                flux_sum(r & 1, (r - 1) & 1, sD, sA);
+                const T cs = ISO ? T(1.0 / 6.0) * ih2 : ih2;
+                const T u0 = RG(s_U, 4, r, ty, tx);
+                const T dph = RG(s_dphi, 4, r, ty, tx);
+                const T un = u0 + (dt * (Dc * sD + sA) * cs + (T(1) + omk * u0) * dph) *
+                                      M3<T>::rcp(T(1) + kk - omk * phin_cur);
                 U_o[r * sxy + (long long)vy * nx + vx] = un;
             }
             phin_cur = phin_next;

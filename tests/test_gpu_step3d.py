@@ -48,7 +48,7 @@ def gpu_sim(N, w, scheme, prec, g, rots, psi, U, tile=None):
     return s
 
 
-@pytest.mark.parametrize("prec,tile", [("f64", None), ("f64", (34, 18, 16))])
+@pytest.mark.parametrize("prec,tile", [("f64", None), ("f64", (34, 10, 8))])
 @pytest.mark.parametrize("scheme", SCHEMES_3D)
 def test_fp64_one_step_matches_oracle(native, scheme, prec, tile):
     w, psi, U, g, rots = make_state(1, 70, 33, 40)
