@@ -51,11 +51,19 @@ def dist_env():
 TRAFFIC = {
     # profiles/k_step2d_sbar21_f32_orientation_sweep_10x1024sq.md
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
-                "sha256": "2db7f7df18e8b6c5764e3db0eb43958e565851df20283cc52cab5d778ff54dd2", "bytes": 151663360},
+                "sha256": "6fdd6e0aeda9abc429149b9c0ff48d504f1c76d1610f550ac5cb20a52d5082dd", "bytes": 156316416},
     # profiles/k_step3d_sbar120_f32_dendrite_256cube.md
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
-                   "sha256": "032df0bc367731da2d8baa166be0d86c25adbb2d885e6ee78385e437376231e9", "bytes": 262989824},
+                   "sha256": "ad21cb7b5a928f5140a7d47e71ecf7e0fccb23b3a7814314563354ef2944ccbf", "bytes": 264033792},
 }
+
+
+# FP32 floating-point operations per cell update (FADD + FMUL + 2 FFMA thread
+# instructions per cell from ncu on the scalar build of the same arithmetic)
+# and the FP32 peak from the unit counts and the maximum clock: 152 SMs x 128
+# FP32 lanes x 2 (FMA) x 2.07 GHz.
+FLOP_PER_CELL = {("sweep2d", "SBAR21"): 315, ("poly2d", "SBAR21"): 315, ("dendrite3d", "SBAR120"): 1150}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def traffic_for(workload):
@@ -342,6 +350,13 @@ def run_native(args):
     kname = ("k_step2d" if ws[0].dim == 2 else "k_step3d") + f"<{'float' if args.precision == 'f32' else 'double'},{args.scheme}>"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic_for(args.workload), "peak_source": peak_kind, "bytes_per_cell": bpc, "kernel": kname}
+    fpc = FLOP_PER_CELL.get((args.workload, args.scheme)) if args.precision == "f32" else None
+    roof_alu = None
+    if fpc:
+        tf = cells * fpc / (kern_ms / n_launch / 1e3) / 1e12
+        roof_alu = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tf / FP32_PEAK_TFLOPS, "flop_per_cell": fpc, "kernel": kname,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
     # end to end through the public API: state in from pinned host buffers,
     # K steps, state and observation back, all inside the timed region
@@ -381,7 +396,7 @@ def run_native(args):
                                        f", FP32 fields, batched persistent launch + CUDA graph, observe every "
                                        f"{OBS_EVERY} steps",
                            "cells_per_gpu": cells, "l2": f"state {cells * 16 / 1e6:.0f} MB per step > 129 MB L2"},
-                "roofline": roof, "e2e": e2e, "clocks": clocks.summary(),
+                "roofline": roof, "roofline_alu": roof_alu, "e2e": e2e, "clocks": clocks.summary(),
                 "latency_ms_per_step": {"p50": statistics.median(per_step),
                                         "p99": per_step[min(len(per_step) - 1, int(0.99 * len(per_step)))],
                                         "over": f"{len(per_step)} chunks of up to {OBS_EVERY} steps"},
