@@ -42,7 +42,11 @@ class Params(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP64, no FMA contraction, OpenMP rows)."""
+    """Compile the oracle with gcc (FP64, no FMA contraction, OpenMP rows).
+    The ORACLE_LIB environment variable names a prebuilt library to use
+    instead (the mutation tests point it at deliberately broken builds)."""
+    if os.environ.get("ORACLE_LIB"):
+        return os.environ["ORACLE_LIB"]
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         tmp = _OUT + f".{os.getpid()}.tmp"

@@ -14,7 +14,9 @@ the mathematics fix (none re-types the oracle's formulas):
 * exact solute conservation with no-flux walls (Eq. Supersaturation, T1);
 * Fourier-mode decay of U in an all-liquid box (closed form);
 * lattice symmetry: transposing or mirroring the grid maps the step exactly
-  when the orientation maps to -alpha0.
+  when the orientation maps to -alpha0;
+* the anti-trapping current of an advancing planar interface carries solute
+  from the solid side into the liquid with the magnitude of Eq. Anti_convention.
 """
 import math
 
@@ -472,3 +474,38 @@ def test_observe_closed_forms(oracle):
     for th in (10.0, 30.0, -20.0):
         o = oracle.observe(p, synth.rot2d(th), np.array([[c[0], c[1], 0]]), g, psi, U, 0)
         assert abs(o["angle_xy_deg"] - th) < math.degrees(h / r)
+
+
+@pytest.mark.parametrize("scheme,dim", PLANAR)
+def test_antitrapping_moves_solute_from_solid_to_liquid(oracle, scheme, dim):
+    """Sec. 2.3: the anti-trapping current (1+(1-k)U) d phi/dt n / sqrt2 with
+    n = grad psi / |grad psi| (Eq. Anti_convention; Anti_approx for the barred
+    schemes) carries solute out of an advancing solid into the liquid: for a
+    planar interface psi = -(x - x0) advancing into a uniformly supersaturated
+    liquid, its divergence A is negative on the solid side, positive on the
+    liquid side, sums to zero, and equals (1+(1-k)U) / sqrt2 * (-d/dx dphi/dt)
+    (unit |grad psi|).  With U uniform the diffusion term vanishes, so one step
+    of the U equation isolates A:  A dt = (U' - U)(1+k-(1-k)phi') - (1+(1-k)U) dphi."""
+    n, h, dt, k, U0 = 96, 0.25, 0.002, 0.15, -0.5
+    x = np.arange(n) * h
+    x0 = (n - 1) / 2 * h + 0.13
+    shape = (6, n) if dim == 2 else (4, 4, n)
+    psi = np.broadcast_to(-(x - x0), shape).copy()
+    U = np.full(shape, U0)
+    p = oracle.params(dim=dim, nx=n, ny=shape[-2], nz=shape[0] if dim == 3 else 1, scheme=synth.SCHEMES[scheme],
+                      h=h, dt=dt, k=k, eps4=0.0, lam=10.0, D=6.267)
+    g = np.zeros(shape, np.int16)
+    psi1, U1 = oracle.step(p, np.eye(3), g, psi, U, 1)
+    line = (3,) if dim == 2 else (2, 2)
+    phi0 = np.tanh(psi[line] / math.sqrt(2))
+    phi1 = np.tanh(psi1[line] / math.sqrt(2))
+    dphi = phi1 - phi0
+    A = ((U1[line] - U0) * (1 + k - (1 - k) * phi1) - (1 + (1 - k) * U0) * dphi) / dt
+    inner = slice(10, n - 10)
+    assert np.all(dphi[inner] >= 0) and dphi.max() > 1e-5  # the interface advances
+    solid, liquid = x[inner] < x0, x[inner] > x0
+    assert abs(A[inner].sum()) < 1e-9 * np.abs(A[inner]).sum()
+    assert A[inner][solid].sum() < -0.4 * np.abs(A[inner]).sum()
+    assert A[inner][liquid].sum() > 0.4 * np.abs(A[inner]).sum()
+    want = (1 + (1 - k) * U0) / math.sqrt(2) * -np.gradient(dphi / dt, h)
+    assert np.max(np.abs(A[inner] - want[inner])) < 0.03 * np.max(np.abs(want[inner]))
