@@ -413,9 +413,10 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             // x+ faces: (L|R) in L's frame, (R|R+1) in R's frame
             const V<T> gxX = (E0 - C0) * bc<T>(ih), gyX = ((Ep + Cp) - (Em + Cm)) * bc<T>(i4h);
             const V<T> Xp = aniso_qn2<T>(gxX, gyX, RR, eps, hh, true);
-            // x- faces: from the left column; recomputed across grain boundaries
+            // x- faces: from the left column; recomputed across grain boundaries.
+            // Lane 0 receives its own value: its column L (x0-2) feeds no output.
             T xmL = shup(Xp.y()), xmR = Xp.x();
-            if (gM != gL || lane == 0)
+            if (gM != gL)
                 xmL = aniso_qn1<T>((P0.l - P0.m1) * ih, ((Pp.l + Pp.m1) - (Pm.l + Pm.m1)) * i4h, RR.a.x(), RR.b.x(),
                                    RR.c.x(), RR.d.x(), eps, hh, true);
             if (gR != gL)

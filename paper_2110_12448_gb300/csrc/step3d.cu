@@ -3,8 +3,11 @@
 //
 // 2.5D blocking: a block owns a TX x TY column of cells and sweeps it along z
 // with shared-memory plane rings (psi with a 2-cell halo in x and y, phi, U and
-// delta phi on the 1-cell ring).  Iteration z:
-//   load psi plane z+2 (and phi on the ring region), U plane z+1
+// delta phi on the 1-cell ring).  Global loads are issued one plane ahead into
+// registers, and each thread keeps the crystal frame of its phase-1 cell in
+// registers until the cell's grain changes.  Iteration z:
+//   store psi plane z+2 (and phi on the ring region), U plane z+1 into the
+//     rings; fetch psi plane z+3, U and grain plane z+2
 //   phase 1 at plane z+1 on the (TX+2) x (TY+2) ring region: d psi/dt, psi',
 //     phi', delta phi; ring cells outside the domain take their mirror cell's
 //     values (the thread computes the mirror cell)
@@ -152,21 +155,49 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             return base[((z & (slots - 1)) * AY + y) * AX + x];
         };
 
-        auto load_psi_plane = [&](int vz) {
-            const int rz = mirror_idx(vz, nz);
-            for (int i = tid; i < PX * PY; i += NT) {
-                const int px = i % PX, py = i / PX;
-                const int gx = mirror_idx(x0 - 2 + px, nx), gy = mirror_idx(y0 - 2 + py, ny);
-                const T v = __ldg(psi + rz * sxy + (long long)gy * nx + gx);
-                PS(vz, py, px) = v;
-                if (px >= 1 && px <= PX - 2 && py >= 1 && py <= PY - 2)
-                    RG(s_phi, 8, vz, py - 1, px - 1) = M3<T>::tanh_(v * ISQ2);
+        // plane loads, split into a global fetch into registers (issued one
+        // plane ahead) and a store into the shared-memory rings
+        constexpr int NPL = (PX * PY + NT - 1) / NT;  // psi cells per thread and plane
+        T pv[NPL];
+        T uv = T(0);
+        auto fetch_psi = [&](int vz) {
+            const long long rz = mirror_idx(vz, nz);
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                const int i = tid + k * NT;
+                if (i < PX * PY) {
+                    const int px = i % PX, py = i / PX;
+                    const int gx = mirror_idx(x0 - 2 + px, nx), gy = mirror_idx(y0 - 2 + py, ny);
+                    pv[k] = __ldg(psi + rz * sxy + (long long)gy * nx + gx);
+                }
             }
         };
-        auto load_U_plane = [&](int vz) {
-            const int rz = mirror_idx(vz, nz);
-            RG(s_U, 4, vz, ty, tx) = __ldg(Uf + rz * sxy + (long long)my * nx + mx);
+        auto put_psi = [&](int vz) {
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                const int i = tid + k * NT;
+                if (i < PX * PY) {
+                    const int px = i % PX, py = i / PX;
+                    PS(vz, py, px) = pv[k];
+                    if (px >= 1 && px <= PX - 2 && py >= 1 && py <= PY - 2)
+                        RG(s_phi, 8, vz, py - 1, px - 1) = M3<T>::tanh_(pv[k] * ISQ2);
+                }
+            }
         };
+        auto load_psi_plane = [&](int vz) {
+            fetch_psi(vz);
+            put_psi(vz);
+        };
+        auto fetch_U = [&](int vz) { uv = __ldg(Uf + mirror_idx(vz, nz) * sxy + (long long)my * nx + mx); };
+        auto put_U = [&](int vz) { RG(s_U, 4, vz, ty, tx) = uv; };
+        auto load_U_plane = [&](int vz) {
+            fetch_U(vz);
+            put_U(vz);
+        };
+        auto grain_at = [&](int p) -> int { return grain[mirror_idx(p, nz) * sxy + (long long)my * nx + mx]; };
+        // crystal frame of the phase-1 cell, reloaded only when its grain changes
+        T R[9];
+        int gR = -1;
 
         // anisotropy: the +z face of the cell's previous plane is its -z face
         T qz_c = T(0);
@@ -174,11 +205,12 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
 
         // phase 1 at real plane p for the cell (mx, my, p); returns phi',
         // writes delta phi and the alphas of the U equation for this slot
-        auto phase1 = [&](int p, T& psin) -> T {
-            const int g = grain[p * sxy + (long long)my * nx + mx];
-            T R[9];
+        auto phase1 = [&](int p, int g, T& psin) -> T {
+            if (g != gR) {
 #pragma unroll
-            for (int q = 0; q < 9; ++q) R[q] = __ldg(rot + 9 * g + q);
+                for (int q = 0; q < 9; ++q) R[q] = __ldg(rot + 9 * g + q);
+                gR = g;
+            }
             auto P = [&](int dx, int dy, int dz) -> T { return PS(p + dz, jy + dy, jx + dx); };
             const T pc = P(0, 0, 0);
             const T s100 = P(1, 0, 0) + P(-1, 0, 0) + P(0, 1, 0) + P(0, -1, 0) + P(0, 0, 1) + P(0, 0, -1);
@@ -320,60 +352,57 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                 fD = (T(3.0 / 16.0) * nD + T(1.0 / 32.0) * mD) * (bU(d[0], d[1], d[2]) - u0);
                 fA = (T(3.0 / 16.0) * nA + T(1.0 / 32.0) * mA) * (bP(d[0], d[1], d[2]) - p0);
             };
-            T fD, fA;
-            // in-plane: +x face, +y face [, +x+y, +x-y edges]
+            // Every flux is evaluated unconditionally and zeroed afterwards where
+            // its stencil leaves the ring region, so that the compiler can share
+            // the neighbourhood loads between fluxes; all stores come last.
+            // Out-of-ring neighbours read the adjacent ring slot or array, always
+            // inside the block's shared memory (values discarded).
+            T oD[NFI + NFZ], oA[NFI + NFZ];
+            bool ok[NFI + NFZ];
             {
                 const int e[3] = {1, 0, 0};
-                fD = fA = T(0);
-                if (xp && ym && yp) face(e, fD, fA);
-                fiD[0] = fD;
-                fiA[0] = fA;
+                face(e, oD[0], oA[0]);
+                ok[0] = xp && ym && yp;
             }
             {
                 const int e[3] = {0, 1, 0};
-                fD = fA = T(0);
-                if (yp && xm && xp) face(e, fD, fA);
-                fiD[NT] = fD;
-                fiA[NT] = fA;
+                face(e, oD[1], oA[1]);
+                ok[1] = yp && xm && xp;
             }
             if (ISO) {
                 const int ex[3] = {1, 0, 0}, eyp[3] = {0, 1, 0}, eym[3] = {0, -1, 0};
-                fD = fA = T(0);
-                if (xp && yp) edge(ex, eyp, 2, fD, fA);
-                fiD[2 * NT] = fD;
-                fiA[2 * NT] = fA;
-                fD = fA = T(0);
-                if (xp && ym) edge(ex, eym, 2, fD, fA);
-                fiD[3 * NT] = fD;
-                fiA[3 * NT] = fA;
+                edge(ex, eyp, 2, oD[2], oA[2]);
+                ok[2] = xp && yp;
+                edge(ex, eym, 2, oD[3], oA[3]);
+                ok[3] = xp && ym;
             }
             // toward plane r+1: +z face [, +x+z, -x+z, +y+z, -y+z edges]
             {
                 const int e[3] = {0, 0, 1};
-                fD = fA = T(0);
-                if (xm && xp && ym && yp) face(e, fD, fA);
-                fzD[0] = fD;
-                fzA[0] = fA;
+                face(e, oD[NFI], oA[NFI]);
+                ok[NFI] = xm && xp && ym && yp;
             }
             if (ISO) {
                 const int ez[3] = {0, 0, 1}, exp_[3] = {1, 0, 0}, exm[3] = {-1, 0, 0}, eyp[3] = {0, 1, 0},
                           eym[3] = {0, -1, 0};
-                fD = fA = T(0);
-                if (xp && ym && yp) edge(exp_, ez, 1, fD, fA);
-                fzD[NT] = fD;
-                fzA[NT] = fA;
-                fD = fA = T(0);
-                if (xm && ym && yp) edge(exm, ez, 1, fD, fA);
-                fzD[2 * NT] = fD;
-                fzA[2 * NT] = fA;
-                fD = fA = T(0);
-                if (yp && xm && xp) edge(eyp, ez, 0, fD, fA);
-                fzD[3 * NT] = fD;
-                fzA[3 * NT] = fA;
-                fD = fA = T(0);
-                if (ym && xm && xp) edge(eym, ez, 0, fD, fA);
-                fzD[4 * NT] = fD;
-                fzA[4 * NT] = fA;
+                edge(exp_, ez, 1, oD[NFI + 1], oA[NFI + 1]);
+                ok[NFI + 1] = xp && ym && yp;
+                edge(exm, ez, 1, oD[NFI + 2], oA[NFI + 2]);
+                ok[NFI + 2] = xm && ym && yp;
+                edge(eyp, ez, 0, oD[NFI + 3], oA[NFI + 3]);
+                ok[NFI + 3] = yp && xm && xp;
+                edge(eym, ez, 0, oD[NFI + 4], oA[NFI + 4]);
+                ok[NFI + 4] = ym && xm && xp;
+            }
+#pragma unroll
+            for (int q = 0; q < NFI; ++q) {
+                fiD[q * NT] = ok[q] ? oD[q] : T(0);
+                fiA[q * NT] = ok[q] ? oA[q] : T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < NFZ; ++q) {
+                fzD[q * NT] = ok[NFI + q] ? oD[NFI + q] : T(0);
+                fzA[q * NT] = ok[NFI + q] ? oA[NFI + q] : T(0);
             }
         };
         // eight/eighteen-flux sums of an output cell at plane r: own fluxes
@@ -415,9 +444,9 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             T psn;
             if (z0 - 1 >= 0) {
                 T d;
-                (void)phase1(z0 - 1, d);
+                (void)phase1(z0 - 1, grain_at(z0 - 1), d);
             }
-            phin_cur = phase1(z0, psn);
+            phin_cur = phase1(z0, grain_at(z0), psn);
             if (do_p2 && z0 < z1) psi_o[z0 * sxy + (long long)vy * nx + vx] = psn;
             if (z0 - 1 < 0) copy_plane(z0 - 1, z0);
         }
@@ -426,15 +455,25 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
         owned_fluxes(z0 - 1, (z0 - 1) & 1);
         __syncthreads();
 
+        // prefetch psi plane z0+2, U and grain plane z0+1
+        fetch_psi(z0 + 2);
+        fetch_U(z0 + 1);
+        int gv = do_p1 ? grain_at(z0 + 1) : 0;
         for (int r = z0; r < z1; ++r) {
-            load_psi_plane(r + 2);
-            load_U_plane(r + 1);
+            put_psi(r + 2);
+            put_U(r + 1);
+            const int g1 = gv;
+            if (r + 1 < z1) {
+                fetch_psi(r + 3);
+                fetch_U(r + 2);
+                if (do_p1) gv = grain_at(r + 2);
+            }
             __syncthreads();
             T phin_next = T(0);
             if (do_p1) {
                 if (r + 1 < nz) {
                     T psn;
-                    phin_next = phase1(r + 1, psn);
+                    phin_next = phase1(r + 1, g1, psn);
                     if (do_p2 && r + 1 < z1) psi_o[(r + 1) * sxy + (long long)vy * nx + vx] = psn;
                 } else {
                     copy_plane(r + 1, r);
