@@ -160,6 +160,12 @@ int pf_device_fields(pf_sim* s, void** psi, void** U, void** grain);
  * Used by the autotuner.  block_x must be one of the compiled widths. */
 int pf_set_tile(pf_sim* s, int block_x, int block_y, int sweep);
 int pf_get_tile(pf_sim* s, int* block_x, int* block_y, int* sweep);
+/* Work units of the current tile that are resident on the device at once
+ * (warps in 2D, blocks in 3D).  A persistent launch runs min(work items,
+ * this) units, so a work list just below a whole multiple of it balances
+ * best; the autotuner picks sweep lengths from it.  Returns the count (> 0)
+ * or a negative PF_ERR_* code; needs a current CUDA device. */
+int pf_resident_units(pf_sim* s);
 
 int pf_destroy(pf_sim* s);
 const char* pf_status_string(int code);

@@ -7,8 +7,10 @@ launch per step exactly as the batched path runs, and keeps the fastest.
 Wave quantisation (work items vs resident warps or blocks) is what the
 choice mostly trades against the per-sweep prologue (about 2.5 rows of extra
 work per work item), so the answer depends on the batch size as well as the
-grid; the 2D candidates are dense enough in the sweep length to land close
-below a whole number of waves.  Results are cached per device in
+grid.  Besides a fixed list, the candidates include, for k = 1, 2, ... waves,
+the shortest sweep whose work list fits in k waves of resident units
+(``pf_resident_units``), which balances the persistent launch with the least
+prologue for that wave count.  Results are cached per device in
 ``_build/autotune.json``.
 """
 from __future__ import annotations
@@ -23,6 +25,29 @@ CANDIDATES_3D = [(34, by, s) for by in (18, 10) for s in (16, 32, 64)]
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _CACHE = os.path.join(_HERE, "_build", "autotune.json")
 _lock = threading.Lock()
+
+
+def work_items(w, tile) -> int:
+    """Work items of one instance for tile (block_x, block_y, sweep), the
+    library's decomposition: 2D (block_x - 4)-column strips times sweep-row
+    bands; 3D (block_x - 4) x (block_y - 4) columns times sweep-plane bands."""
+    bx, by, sw = tile
+    n = -(-w.nx // (bx - 4)) * -(-(w.ny if w.dim == 2 else w.nz) // sw)
+    return n if w.dim == 2 else n * -(-w.ny // (by - 4))
+
+
+def wave_aligned(workloads, bx, by, resident, max_waves=8, min_sweep=8):
+    """For k = 1 .. max_waves: the shortest sweep whose work list over all
+    `workloads` fits in k waves of `resident` units."""
+    depth = max(w.ny if w.dim == 2 else w.nz for w in workloads)
+    out = []
+    for k in range(1, max_waves + 1):
+        for sw in range(min_sweep, depth + 1):
+            if sum(work_items(w, (bx, by, sw)) for w in workloads) <= k * resident:
+                if (bx, by, sw) not in out:
+                    out.append((bx, by, sw))
+                break
+    return out
 
 
 def _key(device_name, w, precision, count):
@@ -60,7 +85,15 @@ def tune(workloads, precision="f32", steps=24, repeats=2, use_cache=True, verbos
         return tuple(cache[key]["tile"]), cache[key]["times"]
     stream = torch.cuda.Stream()
     sims = [N.Sim.from_workload(w, precision, stream=stream) for w in workloads]
-    cands = CANDIDATES_2D if w0.dim == 2 else CANDIDATES_3D
+    cands = list(CANDIDATES_2D if w0.dim == 2 else CANDIDATES_3D)
+    for bx, by in sorted({(t[0], t[1]) for t in cands}):
+        try:
+            for s in sims:
+                s.set_tile(bx, by, 0)
+            resident = sims[0].resident_units()
+        except N.PfError:
+            continue
+        cands += [t for t in wave_aligned(workloads, bx, by, resident) if t not in cands]
     times = {}
     for tile in cands:
         try:

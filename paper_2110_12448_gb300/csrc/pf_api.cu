@@ -528,6 +528,12 @@ int pf_get_tile(pf_sim* s, int* block_x, int* block_y, int* sweep) {
     return PF_OK;
 }
 
+int pf_resident_units(pf_sim* s) {
+    if (!s) return PF_ERR_INVALID;
+    const int occ = occupancy(s);
+    return occ > 0 ? occ * num_sms() : PF_ERR_INVALID;
+}
+
 int pf_destroy(pf_sim* s) {
     if (!s) return PF_ERR_INVALID;
     if (s->group) return PF_ERR_STATE;

@@ -85,6 +85,7 @@ def lib():
                 "pf_device_fields": (C.c_int, [vp, P(vp), P(vp), P(vp)]),
                 "pf_set_tile": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
                 "pf_get_tile": (C.c_int, [vp, P(C.c_int), P(C.c_int), P(C.c_int)]),
+                "pf_resident_units": (C.c_int, [vp]),
                 "pf_destroy": (C.c_int, [vp]),
                 "pf_status_string": (C.c_char_p, [C.c_int]),
                 "pf_last_cuda_error": (C.c_char_p, []),
@@ -193,6 +194,12 @@ class Sim:
 
     def set_tile(self, bx=0, by=0, sweep=0):
         _check(lib().pf_set_tile(self.h, int(bx), int(by), int(sweep)), "pf_set_tile")
+
+    def resident_units(self) -> int:
+        """Warps (2D) or blocks (3D) of the current tile resident at once."""
+        n = lib().pf_resident_units(self.h)
+        _check(min(n, 0), "pf_resident_units")
+        return n
 
     def get_tile(self):
         a, b, c = C.c_int(), C.c_int(), C.c_int()
