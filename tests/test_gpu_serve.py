@@ -67,7 +67,14 @@ def test_autotuner_picks_a_valid_tile(native):
     from paper_2110_12448_gb300 import autotune
     ws = [synth.free_dendrite_2d(256, theta_deg=t) for t in (0.0, 10.0)]
     tile, times = autotune.tune(ws, "f32", steps=8, repeats=1, use_cache=False)
-    assert tile in autotune.CANDIDATES_2D and len(times) == len(autotune.CANDIDATES_2D)
+    timed = {tuple(int(x) for x in k.strip("()").split(",")): t for k, t in times.items()}
+    # every fixed candidate is timed, the extra ones are wave-aligned sweeps,
+    # and the answer is the fastest
+    assert set(autotune.CANDIDATES_2D) <= set(timed)
+    assert all(t[:2] == (64, 1) and t[2] >= 8 for t in timed)
+    assert tile in timed and timed[tile] == min(timed.values())
     w3 = [synth.free_dendrite_3d(40)]
-    tile3, _ = autotune.tune(w3, "f32", steps=4, repeats=1, use_cache=False)
-    assert tile3 in autotune.CANDIDATES_3D
+    tile3, times3 = autotune.tune(w3, "f32", steps=4, repeats=1, use_cache=False)
+    timed3 = {tuple(int(x) for x in k.strip("()").split(",")): t for k, t in times3.items()}
+    assert tile3 in timed3 and timed3[tile3] == min(timed3.values())
+    assert all(t[:2] in {c[:2] for c in autotune.CANDIDATES_3D} for t in timed3)
