@@ -73,6 +73,7 @@ def lib():
             L.or_appb_grad.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp]
             L.or_dt_max.argtypes = [C.POINTER(Params)]
             L.or_dt_max.restype = C.c_double
+            L.or_tip_radius.argtypes = [C.POINTER(Params), dp, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -184,3 +185,18 @@ def appb_grad(field, i, j, kind, h=1.0):
 
 def dt_max(p: Params) -> float:
     return float(lib().or_dt_max(C.byref(p)))
+
+
+def tip_radius(p: Params, psi, tip, axis):
+    """Tip radius by the parabola fit of the psi = 0 contour (reading R-RHO):
+    returns dict(rho, rho_x, rho_z, n_x, n_z); rho_z is NaN in 2D."""
+    shape = _shape(p)
+    t = np.zeros(3)
+    t[: len(tip)] = tip
+    a = np.zeros(3)
+    a[: len(axis)] = axis
+    out = np.zeros(5)
+    rc = lib().or_tip_radius(C.byref(p), _dp(_f64(psi, shape)), _dp(t), _dp(a), _dp(out))
+    if rc != 0:
+        raise ValueError("or_tip_radius failed")
+    return dict(rho=out[0], rho_x=out[1], rho_z=out[2], n_x=int(out[3]), n_z=int(out[4]))

@@ -898,3 +898,155 @@ double or_dt_max(const or_params* q) {
     double c = q->D > 1.0 ? q->D : 1.0;
     return 2.0 * q->h * q->h / (lam * c);
 }
+
+/* ------------------------------------------------------------------------- */
+/* tip radius (Sec. 3.3.2, Sec. 6.2.2; reading R-RHO)                         */
+/* ------------------------------------------------------------------------- */
+/* The paper takes the psi = 0 contour, rotates it by minus the measured
+ * growth angle so that the growth direction becomes the vertical axis, and
+ * fits the parabola y = y_tip - (x - x_tip)^2 / (2 rho) to the part of the
+ * contour within one radius behind the tip; in 3D it fits rho_x in the plane
+ * spanned by the growth axis and the in-plane transverse axis, rho_z in the
+ * plane spanned by the growth axis and z, and combines 1/rho = (1/rho_x +
+ * 1/rho_z) / 2.  Steps here:
+ *   frame   e_par = axis / |axis|; 2D: e_x = (e_par_y, -e_par_x); 3D: e_z = z
+ *           minus its e_par component, normalised (x instead when the axis is
+ *           within 1e-6 of z), e_x = e_z cross e_par
+ *   contour for each transverse axis e and s = j h (j = -TR_J..-1, 1..TR_J):
+ *           march r(t) = (tip + s e) - t e_par, t = m h / 4, m = 0..TR_M, psi
+ *           interpolated multilinearly between cell centres; the first m >= 1
+ *           with psi >= 0 gives the crossing t_j by linear interpolation
+ *           between samples m-1 and m.  No sample if psi >= 0 at m = 0, if r
+ *           leaves [0, (n-1) h] on an axis, or if no crossing by m = TR_M.
+ *   fit     c = sum t_j s^2 / sum s^4 over the samples with t_j <= w, rho =
+ *           1 / (2 c); w = TR_M h / 4 in the first round, then the previous
+ *           rho (one radius behind the tip); TR_ROUNDS rounds.
+ * out[0] rho, out[1] rho_x, out[2] rho_z (NaN in 2D), out[3] samples in the
+ * last x fit, out[4] samples in the last z fit.  A fit without samples, or
+ * with c <= 0, gives NaN. */
+#define TR_J 32
+#define TR_M 160
+#define TR_ROUNDS 4
+
+static double interp_psi(const or_params* q, const double* psi, const double r[3], int* inside) {
+    const int n[3] = {q->nx, q->ny, q->dim == 3 ? q->nz : 1};
+    int i0[3];
+    double f[3];
+    *inside = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (a == 2 && q->dim == 2) {
+            i0[a] = 0;
+            f[a] = 0.0;
+            continue;
+        }
+        double u = r[a] / q->h;
+        if (!(u >= 0.0) || u > (double)(n[a] - 1)) {
+            *inside = 0;
+            return 0.0;
+        }
+        int i = (int)floor(u);
+        if (i > n[a] - 2) i = n[a] - 2;
+        i0[a] = i;
+        f[a] = u - (double)i;
+    }
+#define TRV(di, dj, dk) psi[((size_t)(i0[2] + (dk)) * q->ny + (i0[1] + (dj))) * q->nx + (i0[0] + (di))]
+    double v0 = (1.0 - f[1]) * ((1.0 - f[0]) * TRV(0, 0, 0) + f[0] * TRV(1, 0, 0)) +
+                f[1] * ((1.0 - f[0]) * TRV(0, 1, 0) + f[0] * TRV(1, 1, 0));
+    if (q->dim == 2) return v0;
+    double v1 = (1.0 - f[1]) * ((1.0 - f[0]) * TRV(0, 0, 1) + f[0] * TRV(1, 0, 1)) +
+                f[1] * ((1.0 - f[0]) * TRV(0, 1, 1) + f[0] * TRV(1, 1, 1));
+#undef TRV
+    return (1.0 - f[2]) * v0 + f[2] * v1;
+}
+
+/* crossings t_j of the lines along transverse axis e; t[j] = NaN: no sample */
+static void tip_contour(const or_params* q, const double* psi, const double tip[3], const double epar[3],
+                        const double e[3], double t[2 * TR_J]) {
+    const double dt = q->h / 4.0;
+    for (int l = 0; l < 2 * TR_J; ++l) {
+        const int j = l < TR_J ? l - TR_J : l - TR_J + 1; /* -TR_J..-1, 1..TR_J */
+        const double s = (double)j * q->h;
+        double base[3];
+        for (int a = 0; a < 3; ++a) base[a] = tip[a] + s * e[a];
+        t[l] = NAN;
+        double prev = 0.0;
+        for (int m = 0; m <= TR_M; ++m) {
+            const double tm = (double)m * dt;
+            double r[3];
+            for (int a = 0; a < 3; ++a) r[a] = base[a] - tm * epar[a];
+            int inside;
+            const double v = interp_psi(q, psi, r, &inside);
+            if (!inside) break;
+            if (v >= 0.0) {
+                if (m >= 1) t[l] = (double)(m - 1) * dt + dt * (prev / (prev - v));
+                break;
+            }
+            prev = v;
+        }
+    }
+}
+
+static double tip_fit(const or_params* q, const double t[2 * TR_J], int* used) {
+    double w = (double)TR_M * (q->h / 4.0), rho = NAN;
+    *used = 0;
+    for (int round = 0; round < TR_ROUNDS; ++round) {
+        double st = 0.0, s4 = 0.0;
+        int n = 0;
+        for (int l = 0; l < 2 * TR_J; ++l) {
+            const int j = l < TR_J ? l - TR_J : l - TR_J + 1;
+            const double s = (double)j * q->h;
+            if (!(t[l] <= w)) continue;
+            st += t[l] * (s * s);
+            s4 += (s * s) * (s * s);
+            ++n;
+        }
+        *used = n;
+        if (n == 0 || !(st > 0.0)) return NAN;
+        rho = 0.5 * (s4 / st);
+        w = rho;
+    }
+    return rho;
+}
+
+int or_tip_radius(const or_params* q, const double* psi, const double tip[3], const double axis[3], double* out) {
+    if (check_params(q)) return -1;
+    const int dim = q->dim;
+    double epar[3] = {axis[0], axis[1], dim == 3 ? axis[2] : 0.0};
+    const double na = sqrt(epar[0] * epar[0] + epar[1] * epar[1] + epar[2] * epar[2]);
+    if (!(na > 0.0)) return -1;
+    for (int a = 0; a < 3; ++a) epar[a] /= na;
+    double ex[3], ez[3] = {0.0, 0.0, 0.0};
+    if (dim == 2) {
+        ex[0] = epar[1];
+        ex[1] = -epar[0];
+        ex[2] = 0.0;
+    } else {
+        double ref[3] = {0.0, 0.0, 1.0};
+        if (fabs(epar[2]) > 1.0 - 1e-6) {
+            ref[0] = 1.0;
+            ref[2] = 0.0;
+        }
+        const double pr = ref[0] * epar[0] + ref[1] * epar[1] + ref[2] * epar[2];
+        for (int a = 0; a < 3; ++a) ez[a] = ref[a] - pr * epar[a];
+        const double nz = sqrt(ez[0] * ez[0] + ez[1] * ez[1] + ez[2] * ez[2]);
+        for (int a = 0; a < 3; ++a) ez[a] /= nz;
+        ex[0] = ez[1] * epar[2] - ez[2] * epar[1];
+        ex[1] = ez[2] * epar[0] - ez[0] * epar[2];
+        ex[2] = ez[0] * epar[1] - ez[1] * epar[0];
+    }
+    double t[2 * TR_J];
+    int nx_used = 0, nz_used = 0;
+    tip_contour(q, psi, tip, epar, ex, t);
+    const double rx = tip_fit(q, t, &nx_used);
+    double rz = NAN;
+    if (dim == 3) {
+        tip_contour(q, psi, tip, epar, ez, t);
+        rz = tip_fit(q, t, &nz_used);
+    }
+    out[0] = dim == 2 ? rx : 2.0 / (1.0 / rx + 1.0 / rz);
+    out[1] = rx;
+    out[2] = rz;
+    out[3] = (double)nx_used;
+    out[4] = (double)nz_used;
+    return 0;
+}

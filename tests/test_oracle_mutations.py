@@ -2,8 +2,9 @@
 
 Each case plants one mistake in a temporary copy of oracle/pf_oracle.c
 (never in the committed file), builds it, and runs the pin suites
-(test_oracle_symbols.py, test_oracle_step.py) against that build through the
-ORACLE_LIB override: at least one pin must fail."""
+(test_oracle_symbols.py, test_oracle_step.py, test_oracle_tip_radius.py)
+against that build through the ORACLE_LIB override: at least one pin must
+fail."""
 import os
 import subprocess
 import sys
@@ -53,6 +54,13 @@ MUTATIONS = [
      "sol += (1.0 + k + (1.0 - k) * ph) * (1.0 + (1.0 - k) * u) / 2.0;"),
     ("init_radius_sign", "double v = seeds[4 * s + 3] - sqrt(dx * dx + dy * dy + dz * dz);",
      "double v = seeds[4 * s + 3] + sqrt(dx * dx + dy * dy + dz * dz);"),
+    ("tip_radius_fit_factor", "rho = 0.5 * (s4 / st);", "rho = (s4 / st);"),
+    ("tip_radius_interp_swapped", "f[1] * ((1.0 - f[0]) * TRV(0, 1, 0) + f[0] * TRV(1, 1, 0));\n    if",
+     "f[1] * ((1.0 - f[0]) * TRV(1, 1, 0) + f[0] * TRV(0, 1, 0));\n    if"),
+    ("tip_radius_crossing", "dt * (prev / (prev - v))", "dt * (v / (prev - v))"),
+    ("tip_radius_no_window", "        w = rho;\n", "        w = w;\n"),
+    ("tip_radius_combination_3d", "2.0 / (1.0 / rx + 1.0 / rz)", "0.5 * (rx + rz)"),
+    ("tip_radius_transverse_axis", "ex[0] = ez[1] * epar[2] - ez[2] * epar[1];", "ex[0] = ez[1] * epar[2] + ez[2] * epar[1];"),
 ]
 
 
@@ -74,6 +82,7 @@ def test_pins_catch_mutation(source, name, old, new):
         env = dict(os.environ, ORACLE_LIB=lib, OMP_NUM_THREADS="2")
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             os.path.join(ROOT, "tests", "test_oracle_symbols.py"),
-                            os.path.join(ROOT, "tests", "test_oracle_step.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_step.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_tip_radius.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"mutation {name} survived every pin:\n{r.stdout[-2000:]}"
