@@ -104,6 +104,20 @@ typedef struct {
     int32_t nonfinite;        /* number of cells with NaN/Inf psi or U */
 } pf_obs;
 
+/* Tip operating state (Sec. 3.3.2 and 6.2.2): tip radius from a parabola fit
+ * of the psi = 0 contour and the selection constant sigma* = 2 D d0* /
+ * (rho^2 V) (Sec. 1 and 3.3.2), in units of W and tau0. */
+typedef struct {
+    double rho;         /* tip radius; 3D: 2 / (1/rho_x + 1/rho_z) (NaN: no fit) */
+    double rho_x;       /* fit across the growth axis in its plane with x/y */
+    double rho_z;       /* fit across the growth axis toward z (NaN in 2D) */
+    double sigma_star;  /* 2 D d0* / (rho^2 v_tip); NaN if v_tip <= 0 or no fit */
+    double d0_star;     /* (1 - (1-k) Omega) / k * a1 / lambda with Omega = -U0,
+                           a1 = 5 sqrt2 / 8 (Sec. 2.1, isothermal) */
+    double axis[3];     /* unit growth axis: tip minus the grain's centre */
+    int32_t n_x, n_z;   /* contour samples in the final fits */
+} pf_tip;
+
 /* Device bytes the caller must supply to pf_create for these parameters
  * (0 if the parameters are invalid). */
 size_t pf_required_bytes(const pf_params* p);
@@ -143,6 +157,22 @@ int pf_step(pf_sim* s, int64_t n);
  * largest +y component); ties go to the lowest cell index.  Returns
  * PF_ERR_NONFINITE (with *out filled) when NaN/Inf cells exist. */
 int pf_observe(pf_sim* s, int grain, pf_obs* out);
+
+/* Synchronise the stream and measure the tip radius of grain g (-1 as in
+ * pf_observe) at tip[3] (from pf_observe; z ignored in 2D), entirely on the
+ * device.  The paper rotates the psi = 0 contour so that the measured growth
+ * direction is vertical and fits y = y_tip - (x - x_tip)^2 / (2 rho) up to one
+ * radius behind the tip (in 3D separately across the two transverse axes).
+ * Here: growth axis e = tip - centre of g, normalised; transverse axes (2D)
+ * e_x = (e_y, -e_x), (3D) e_z = z minus its e component, normalised (x when e
+ * is within 1e-6 of z), e_x = e_z cross e.  For s = j h, j = -32..-1, 1..32,
+ * psi is interpolated multilinearly along tip + s e_x - t e (and e_z), t =
+ * m h / 4 up to 40 h; the first psi >= 0 gives the crossing t(s) by linear
+ * interpolation.  rho = sum s^4 / (2 sum t s^2) over the crossings with t <=
+ * w, w = 40 h and then the previous rho, four rounds.  sigma* uses v_tip (from
+ * pf_observe; pass 0 to skip).  Returns PF_ERR_INVALID for a bad grain or a
+ * non-finite tip; PF_OK with rho = NaN when the contour gives no fit. */
+int pf_tip_radius(pf_sim* s, int grain, const double tip[3], double v_tip, pf_tip* out);
 
 /* Checkpoint / restore of the current fields (nx*ny*nz elements of the
  * handle's precision each) and of the step counter. */

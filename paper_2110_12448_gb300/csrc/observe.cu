@@ -10,6 +10,7 @@
 // formed with explicitly rounded FP64 operations (no contraction) so that the
 // choice is reproducible on any FP64 implementation of the same formula.
 #include <cfloat>
+#include <math_constants.h>
 #include <mutex>
 
 #include "pf_internal.cuh"
@@ -127,6 +128,156 @@ __global__ void __launch_bounds__(OBS_THREADS) k_observe_finish(const ObsPartial
     if (threadIdx.x == 0) *out = sh[0];
 }
 
+// ---------------------------------------------------------------------------
+// Tip radius (Sec. 3.3.2, Sec. 6.2.2): the paper fits the parabola
+// y = y_tip - (x - x_tip)^2 / (2 rho) to the psi = 0 contour rotated so that
+// the measured growth direction is vertical, up to one radius behind the tip
+// (3D: rho_x in the plane of the growth axis and its in-plane normal, rho_z in
+// the plane of the growth axis and z, 1/rho = (1/rho_x + 1/rho_z) / 2).
+// Contour: 64 lines per transverse axis e, r(t) = (tip + s e) - t e_par with
+// s = j h (j = -32..-1, 1..32) and t = m h / 4 (m <= 160); psi is interpolated
+// multilinearly between cell centres and the first sample with psi >= 0 gives
+// the crossing by linear interpolation.  Fit: c = sum t s^2 / sum s^4 over the
+// crossings with t <= w, rho = 1 / (2c); w = 40 h, then the previous rho; four
+// rounds.  Thread l of each 64-thread half marches line l; one thread per half
+// fits in line order.  All FP64 operations are explicitly rounded (no
+// contraction), so the crossings are reproducible.
+constexpr int TIP_J = 32, TIP_M = 160, TIP_ROUNDS = 4;
+
+template <typename T>
+__device__ double tip_interp(const TipArgs& a, const T* __restrict__ psi, const double r[3], bool& inside) {
+    const int n[3] = {a.nx, a.ny, a.dim == 3 ? a.nz : 1};
+    int i0[3] = {0, 0, 0};
+    double f[3] = {0.0, 0.0, 0.0};
+    inside = true;
+    for (int q = 0; q < a.dim; ++q) {
+        const double u = __ddiv_rn(r[q], a.h);
+        if (!(u >= 0.0) || u > (double)(n[q] - 1)) {
+            inside = false;
+            return 0.0;
+        }
+        int i = (int)floor(u);
+        if (i > n[q] - 2) i = n[q] - 2;
+        i0[q] = i;
+        f[q] = __dsub_rn(u, (double)i);
+    }
+    auto P = [&](int di, int dj, int dk) -> double {
+        return (double)psi[((long long)(i0[2] + dk) * a.ny + (i0[1] + dj)) * a.nx + (i0[0] + di)];
+    };
+    auto plane = [&](int dk) -> double {
+        const double g0 = __dsub_rn(1.0, f[0]);
+        const double lo = __dadd_rn(__dmul_rn(g0, P(0, 0, dk)), __dmul_rn(f[0], P(1, 0, dk)));
+        const double hi = __dadd_rn(__dmul_rn(g0, P(0, 1, dk)), __dmul_rn(f[0], P(1, 1, dk)));
+        return __dadd_rn(__dmul_rn(__dsub_rn(1.0, f[1]), lo), __dmul_rn(f[1], hi));
+    };
+    const double v0 = plane(0);
+    if (a.dim == 2) return v0;
+    return __dadd_rn(__dmul_rn(__dsub_rn(1.0, f[2]), v0), __dmul_rn(f[2], plane(1)));
+}
+
+template <typename T> __global__ void __launch_bounds__(TIP_THREADS) k_tip_radius(TipArgs a, double* __restrict__ out) {
+    __shared__ double ts[2][2 * TIP_J];
+    __shared__ double frame[3][3];  // e_par, e_x, e_z
+    const T* __restrict__ psi = static_cast<const T*>(a.psi);
+    if (threadIdx.x == 0) {
+        double ep[3] = {a.axis[0], a.axis[1], a.dim == 3 ? a.axis[2] : 0.0};
+        const double na =
+            __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ep[0], ep[0]), __dmul_rn(ep[1], ep[1])), __dmul_rn(ep[2], ep[2])));
+        for (int q = 0; q < 3; ++q) ep[q] = __ddiv_rn(ep[q], na);
+        double ex[3], ez[3] = {0.0, 0.0, 0.0};
+        if (a.dim == 2) {
+            ex[0] = ep[1];
+            ex[1] = -ep[0];
+            ex[2] = 0.0;
+        } else {
+            double ref[3] = {0.0, 0.0, 1.0};
+            if (fabs(ep[2]) > 1.0 - 1e-6) {
+                ref[0] = 1.0;
+                ref[2] = 0.0;
+            }
+            const double pr =
+                __dadd_rn(__dadd_rn(__dmul_rn(ref[0], ep[0]), __dmul_rn(ref[1], ep[1])), __dmul_rn(ref[2], ep[2]));
+            for (int q = 0; q < 3; ++q) ez[q] = __dsub_rn(ref[q], __dmul_rn(pr, ep[q]));
+            const double nz = __dsqrt_rn(
+                __dadd_rn(__dadd_rn(__dmul_rn(ez[0], ez[0]), __dmul_rn(ez[1], ez[1])), __dmul_rn(ez[2], ez[2])));
+            for (int q = 0; q < 3; ++q) ez[q] = __ddiv_rn(ez[q], nz);
+            ex[0] = __dsub_rn(__dmul_rn(ez[1], ep[2]), __dmul_rn(ez[2], ep[1]));
+            ex[1] = __dsub_rn(__dmul_rn(ez[2], ep[0]), __dmul_rn(ez[0], ep[2]));
+            ex[2] = __dsub_rn(__dmul_rn(ez[0], ep[1]), __dmul_rn(ez[1], ep[0]));
+        }
+        for (int q = 0; q < 3; ++q) {
+            frame[0][q] = ep[q];
+            frame[1][q] = ex[q];
+            frame[2][q] = ez[q];
+        }
+    }
+    __syncthreads();
+    const int l = threadIdx.x & 63, half = threadIdx.x >> 6;  // half 0: e_x lines, 1: e_z lines
+    const bool active = half == 0 || a.dim == 3;
+    const double dt = __dmul_rn(a.h, 0.25);
+    if (active) {
+        const double* e = frame[1 + half];
+        const int j = l < TIP_J ? l - TIP_J : l - TIP_J + 1;
+        const double s = __dmul_rn((double)j, a.h);
+        double base[3];
+        for (int q = 0; q < 3; ++q) base[q] = __dadd_rn(a.tip[q], __dmul_rn(s, e[q]));
+        double tc = CUDART_NAN, prev = 0.0;
+        for (int m = 0; m <= TIP_M; ++m) {
+            const double tm = __dmul_rn((double)m, dt);
+            double r[3];
+            for (int q = 0; q < 3; ++q) r[q] = __dsub_rn(base[q], __dmul_rn(tm, frame[0][q]));
+            bool inside;
+            const double v = tip_interp<T>(a, psi, r, inside);
+            if (!inside) break;
+            if (v >= 0.0) {
+                if (m >= 1)
+                    tc = __dadd_rn(__dmul_rn((double)(m - 1), dt), __dmul_rn(dt, __ddiv_rn(prev, __dsub_rn(prev, v))));
+                break;
+            }
+            prev = v;
+        }
+        ts[half][l] = tc;
+    }
+    __syncthreads();
+    if (active && l == 0) {
+        double w = __dmul_rn((double)TIP_M, dt), rho = CUDART_NAN;
+        int used = 0;
+        for (int round = 0; round < TIP_ROUNDS; ++round) {
+            double st = 0.0, s4 = 0.0;
+            int n = 0;
+            for (int k = 0; k < 2 * TIP_J; ++k) {
+                const int j = k < TIP_J ? k - TIP_J : k - TIP_J + 1;
+                const double s = __dmul_rn((double)j, a.h);
+                const double t = ts[half][k];
+                if (!(t <= w)) continue;
+                const double s2 = __dmul_rn(s, s);
+                st = __dadd_rn(st, __dmul_rn(t, s2));
+                s4 = __dadd_rn(s4, __dmul_rn(s2, s2));
+                ++n;
+            }
+            used = n;
+            if (n == 0 || !(st > 0.0)) {
+                rho = CUDART_NAN;
+                break;
+            }
+            rho = __dmul_rn(0.5, __ddiv_rn(s4, st));
+            w = rho;
+        }
+        out[1 + half] = rho;
+        out[3 + half] = (double)used;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (a.dim == 2) {
+            out[2] = CUDART_NAN;
+            out[4] = 0.0;
+            out[0] = out[1];
+        } else {
+            out[0] = __ddiv_rn(2.0, __dadd_rn(__ddiv_rn(1.0, out[1]), __ddiv_rn(1.0, out[2])));
+        }
+    }
+}
+
 template <typename T>
 __global__ void k_init_seeds(int dim, int nx, int ny, int nz, double h, double U0, const SeedDev* __restrict__ seeds,
                              int n_seeds, T* __restrict__ psi, T* __restrict__ U, int16_t* __restrict__ grain) {
@@ -197,6 +348,14 @@ cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* r
     else
         k_observe<double><<<OBS_BLOCKS, OBS_THREADS, 0, st>>>(a, partials);
     k_observe_finish<<<1, OBS_THREADS, 0, st>>>(partials, OBS_BLOCKS, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tip_radius(const TipArgs& a, double* out, cudaStream_t st) {
+    if (a.prec == 0)
+        k_tip_radius<float><<<1, TIP_THREADS, 0, st>>>(a, out);
+    else
+        k_tip_radius<double><<<1, TIP_THREADS, 0, st>>>(a, out);
     return cudaGetLastError();
 }
 

@@ -457,6 +457,48 @@ int pf_get_fields(pf_sim* s, void* psi_host, void* U_host) {
     return PF_OK;
 }
 
+int pf_tip_radius(pf_sim* s, int grain, const double tip[3], double v_tip, pf_tip* out) {
+    if (!s || !out || !tip || grain < -1 || grain >= s->n_grains) return PF_ERR_INVALID;
+    const int dim = s->p.dim;
+    for (int q = 0; q < dim; ++q)
+        if (!std::isfinite(tip[q])) return PF_ERR_INVALID;
+    const int gg = grain < 0 ? 0 : grain;
+    TipArgs a{};
+    const int cur = (int)(s->step & 1);
+    a.psi = s->psi[cur];
+    a.prec = s->p.precision == PF_F64 ? 1 : 0;
+    a.dim = dim;
+    a.nx = s->p.nx;
+    a.ny = s->p.ny;
+    a.nz = dim == 3 ? s->p.nz : 1;
+    a.h = s->p.h;
+    double na = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        a.tip[q] = q < dim ? tip[q] : 0.0;
+        a.axis[q] = q < dim ? tip[q] - s->centres_h[3 * gg + q] : 0.0;
+        na += a.axis[q] * a.axis[q];
+    }
+    if (!(na > 0.0)) return PF_ERR_INVALID;
+    // the observe scratch holds the five results
+    double* dres = reinterpret_cast<double*>(s->partials);
+    CK(launch_tip_radius(a, dres, s->st));
+    double r[5];
+    CK(cudaMemcpyAsync(r, dres, sizeof(r), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    std::memset(out, 0, sizeof(*out));
+    out->rho = r[0];
+    out->rho_x = r[1];
+    out->rho_z = r[2];
+    out->n_x = (int32_t)r[3];
+    out->n_z = (int32_t)r[4];
+    const double nrm = std::sqrt(na);
+    for (int q = 0; q < 3; ++q) out->axis[q] = a.axis[q] / nrm;
+    const double a1 = 5.0 * std::sqrt(2.0) / 8.0, omega = -s->p.U0, k = s->p.k;
+    out->d0_star = (1.0 - (1.0 - k) * omega) / k * a1 / s->p.lambda;
+    out->sigma_star = (v_tip > 0.0 && std::isfinite(r[0])) ? 2.0 * s->p.D * out->d0_star / (r[0] * r[0] * v_tip) : NAN;
+    return PF_OK;
+}
+
 int pf_set_fields(pf_sim* s, const void* psi_host, const void* U_host) {
     if (!s || (!psi_host && !U_host)) return PF_ERR_INVALID;
     const int cur = (int)(s->step & 1);

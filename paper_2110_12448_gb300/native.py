@@ -53,6 +53,11 @@ class Obs(C.Structure):
                 ("found", C.c_int32), ("nonfinite", C.c_int32)]
 
 
+class Tip(C.Structure):
+    _fields_ = [("rho", C.c_double), ("rho_x", C.c_double), ("rho_z", C.c_double), ("sigma_star", C.c_double),
+                ("d0_star", C.c_double), ("axis", C.c_double * 3), ("n_x", C.c_int32), ("n_z", C.c_int32)]
+
+
 def lib_path() -> str:
     """Path of libpf.so; the PF_LIBRARY environment variable overrides it."""
     return os.environ.get("PF_LIBRARY", _build.LIB)
@@ -78,6 +83,7 @@ def lib():
                 "pf_get_grain_index": (C.c_int, [vp, P(C.c_int16)]),
                 "pf_step": (C.c_int, [vp, i64]),
                 "pf_observe": (C.c_int, [vp, C.c_int, P(Obs)]),
+                "pf_tip_radius": (C.c_int, [vp, C.c_int, P(C.c_double), C.c_double, P(Tip)]),
                 "pf_get_fields": (C.c_int, [vp, vp, vp]),
                 "pf_set_fields": (C.c_int, [vp, vp, vp]),
                 "pf_get_step": (C.c_int, [vp, P(i64)]),
@@ -218,6 +224,16 @@ class Sim:
         d = {f: getattr(o, f) for f, _ in Obs._fields_}
         d["tip"] = tuple(o.tip)
         d["status"] = rc
+        return d
+
+    def tip_radius(self, obs: dict, grain: int = -1) -> dict:
+        """pf_tip_radius at the tip of an observe() result of the same grain:
+        tip radius, its fits, sigma* (with the observed tip velocity)."""
+        t = (C.c_double * 3)(*obs["tip"])
+        o = Tip()
+        _check(lib().pf_tip_radius(self.h, int(grain), t, float(obs.get("v_tip", 0.0)), C.byref(o)), "pf_tip_radius")
+        d = {f: getattr(o, f) for f, _ in Tip._fields_}
+        d["axis"] = tuple(o.axis)
         return d
 
     def get_fields(self):
