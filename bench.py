@@ -344,6 +344,24 @@ def run_native(args):
     per_step = sorted(a.elapsed_time(b) / c for a, b, c in pairs)
     ms, value = aggregate(ms, cells, args.steps, world, device="cuda")
 
+    # tip operating state per instance of the orientation sweep (growth angle
+    # vs crystal angle, tip velocity, tip radius and sigma*), measured on the
+    # device after the timed region
+    sweep = None
+    if args.workload == "sweep2d" and rank == 0:
+        sweep = {"theta_deg": [], "alpha_deg": [], "v_tip": [], "rho": [], "sigma_star": []}
+        tr_s = []
+        for t, s in zip(THETAS, sims):
+            ob = s.observe(0)
+            t0 = time.perf_counter()
+            tr = s.tip_radius(ob, 0)
+            tr_s.append(time.perf_counter() - t0)
+            for key, v in (("theta_deg", float(t)), ("alpha_deg", ob["angle_xy_deg"]), ("v_tip", ob["v_tip"]),
+                           ("rho", tr["rho"]), ("sigma_star", tr["sigma_star"])):
+                sweep[key].append(None if v != v else round(v, 6))
+        sweep["at_step"] = sims[0].steps_done
+        sweep["tip_radius_call_ms_p50"] = statistics.median(tr_s) * 1e3
+
     # roofline of the fused step kernel: algorithmic bytes per launch / mean launch time
     peak, peak_kind = peaks()
     bpc = B_PER_CELL[args.precision]
@@ -403,6 +421,8 @@ def run_native(args):
                                         "over": f"{len(per_step)} chunks of up to {OBS_EVERY} steps"},
                 "tile": list(tile) if tile else None,
                 "gpu_launches": n_launch + 2 * len(sims) * (args.steps // OBS_EVERY)}
+        if sweep:
+            line["orientation_sweep"] = sweep
         if world == 1 and not args.no_fp64:
             line["fp64_plain"] = fp64_plain(stream)
         if world == 1 and not args.no_cpu and args.workload == "sweep2d":
