@@ -57,11 +57,18 @@
 
 #define OR_BC_MIRROR 0
 #define OR_BC_PERIODIC 1
+#define OR_BC_PERIODIC_X 2 /* periodic in x, cell-centred mirror in y (and z) */
 
+/* thermal = 0: isothermal (F1 = 1, F2 = U, Sec. 2.1).  thermal = 1: frozen
+ * temperature for directional solidification along +y (Eqs. Thermal_F1,
+ * Thermal_F2): zeta = (y - yT - Vp t) / lT, F1 = 1 - (1-k) zeta, F2 = U +
+ * zeta, with y = j h and t = t0 + s dt at step s of a call. */
 typedef struct {
     int dim, nx, ny, nz;
     int scheme, bc;
     double h, dt, k, eps4, lambda, D;
+    int thermal, pad;
+    double Vp, lT, yT, t0;
 } or_params;
 
 static const double SQ2 = 1.41421356237309504880;
@@ -76,6 +83,12 @@ typedef struct {
     int oz;          /* z offset (2 in 3D, 0 in 2D) */
     double* v;
 } pad_t;
+
+/* boundary rule of axis `axis` under the parameter bc */
+static int axis_bc(int bc, int axis) {
+    if (bc == OR_BC_PERIODIC_X) return axis == 0 ? OR_BC_PERIODIC : OR_BC_MIRROR;
+    return bc;
+}
 
 static int map_index(int i, int n, int bc) {
     if (bc == OR_BC_PERIODIC) return ((i % n) + n) % n;
@@ -107,8 +120,8 @@ static void pad_fill(pad_t* p, const double* src, int bc) {
     for (int k = zl; k < zh; ++k)
         for (int j = -2; j < p->ny + 2; ++j)
             for (int i = -2; i < p->nx + 2; ++i) {
-                int ii = map_index(i, p->nx, bc), jj = map_index(j, p->ny, bc);
-                int kk = p->dim == 3 ? map_index(k, p->nz, bc) : 0;
+                int ii = map_index(i, p->nx, axis_bc(bc, 0)), jj = map_index(j, p->ny, axis_bc(bc, 1));
+                int kk = p->dim == 3 ? map_index(k, p->nz, axis_bc(bc, 2)) : 0;
                 *PA(p, i, j, k) = src[((size_t)kk * p->ny + jj) * p->nx + ii];
             }
 }
@@ -539,7 +552,7 @@ static double guard_of(void) { return 1e-20; }
  * grad2 / lap are the scheme's G and L; N = div(J - grad psi) on <10>/<100>
  * faces; a_c from the centred gradient. */
 static double dpsi_dt_2d(const or_params* q, const pad_t* psi, const pad_t* phi, const pad_t* U, const pad_t* gr,
-                         const double* rot, int i, int j) {
+                         const double* rot, int i, int j, double t) {
     double h = q->h;
     const double* R = rot + 9 * (int)V2(gr, i, j);
     double L = is_iso(q->scheme) ? lap_21(psi, i, j, h) : lap_10(psi, i, j, h);
@@ -557,6 +570,12 @@ static double dpsi_dt_2d(const or_params* q, const pad_t* psi, const pad_t* phi,
     }
     N /= h;
     double ph = V2(phi, i, j), u = V2(U, i, j);
+    if (q->thermal) {
+        /* Eq. PF_a with the frozen-temperature functions F1, F2 */
+        double zeta = (j * h - q->yT - q->Vp * t) / q->lT;
+        double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u + zeta;
+        return ((L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * F2)) / (ac * ac) - SQ2 * ph * G) / F1;
+    }
     return (L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * u)) / (ac * ac) - SQ2 * ph * G;
 }
 
@@ -591,6 +610,7 @@ static int check_params(const or_params* q) {
     if (q->dim == 2 && q->scheme > OR_SBAR21) return -1;
     if (q->dim == 3 && q->scheme != OR_S100 && q->scheme != OR_SBAR120) return -1;
     if (!(q->h > 0) || !(q->dt > 0)) return -1;
+    if (q->thermal && (q->dim != 2 || !(q->lT > 0))) return -1;
     return 0;
 }
 
@@ -631,7 +651,7 @@ int or_step(const or_params* q, int n_grains, const double* rot, const int16_t* 
             for (int j = 0; j < q->ny; ++j)
                 for (int i = 0; i < q->nx; ++i) {
                     size_t c = ((size_t)kk * q->ny + j) * q->nx + i;
-                    double r = q->dim == 2 ? dpsi_dt_2d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j)
+                    double r = q->dim == 2 ? dpsi_dt_2d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, q->t0 + (double)s * dt)
                                            : dpsi_dt_3d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, kk);
                     dpsi[c] = r;
                     psin[c] = psi[c] + dt * r;

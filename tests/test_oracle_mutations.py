@@ -2,8 +2,8 @@
 
 Each case plants one mistake in a temporary copy of oracle/pf_oracle.c
 (never in the committed file), builds it, and runs the pin suites
-(test_oracle_symbols.py, test_oracle_step.py, test_oracle_tip_radius.py)
-against that build through the ORACLE_LIB override: at least one pin must
+(test_oracle_symbols.py, test_oracle_step.py, test_oracle_tip_radius.py,
+test_oracle_directional.py) against that build through the ORACLE_LIB override: at least one pin must
 fail."""
 import os
 import subprocess
@@ -61,6 +61,21 @@ MUTATIONS = [
     ("tip_radius_no_window", "        w = rho;\n", "        w = w;\n"),
     ("tip_radius_combination_3d", "2.0 / (1.0 / rx + 1.0 / rz)", "0.5 * (rx + rz)"),
     ("tip_radius_transverse_axis", "ex[0] = ez[1] * epar[2] - ez[2] * epar[1];", "ex[0] = ez[1] * epar[2] + ez[2] * epar[1];"),
+    ("thermal_F1_dropped",
+     "return ((L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * F2)) / (ac * ac) - SQ2 * ph * G) / F1;",
+     "return ((L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * F2)) / (ac * ac) - SQ2 * ph * G);"),
+    ("thermal_F2_sign", "double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u + zeta;",
+     "double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u - zeta;"),
+    ("thermal_F1_sign", "double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u + zeta;",
+     "double F1 = 1.0 + (1.0 - q->k) * zeta, F2 = u + zeta;"),
+    ("thermal_pulling_sign", "double zeta = (j * h - q->yT - q->Vp * t) / q->lT;",
+     "double zeta = (j * h - q->yT + q->Vp * t) / q->lT;"),
+    ("thermal_row_offset", "double zeta = (j * h - q->yT - q->Vp * t) / q->lT;",
+     "double zeta = ((j + 1) * h - q->yT - q->Vp * t) / q->lT;"),
+    ("thermal_clock_frozen", "dpsi_dt_2d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, q->t0 + (double)s * dt)",
+     "dpsi_dt_2d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, q->t0)"),
+    ("periodic_x_as_mirror", "if (bc == OR_BC_PERIODIC_X) return axis == 0 ? OR_BC_PERIODIC : OR_BC_MIRROR;",
+     "if (bc == OR_BC_PERIODIC_X) return OR_BC_MIRROR;"),
 ]
 
 
@@ -83,6 +98,7 @@ def test_pins_catch_mutation(source, name, old, new):
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             os.path.join(ROOT, "tests", "test_oracle_symbols.py"),
                             os.path.join(ROOT, "tests", "test_oracle_step.py"),
-                            os.path.join(ROOT, "tests", "test_oracle_tip_radius.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_tip_radius.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_directional.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"mutation {name} survived every pin:\n{r.stdout[-2000:]}"
