@@ -62,14 +62,31 @@ enum {
     PF_ERR_STATE = -6      /* call not valid in the handle's state */
 };
 
+/* Boundary rule along x (y and z always use cell-centred mirrors). */
+enum { PF_BC_MIRROR = 0, PF_BC_PERIODIC = 1 };
+/* Thermal condition (Sec. 2.1). */
+enum { PF_ISOTHERMAL = 0, PF_FROZEN_GRADIENT = 1 };
+
 /* Problem statement (Sec. 2.1): grid, lattice spacing h (units of W), time
  * step dt (units of tau0), partition coefficient k, anisotropy strength
  * eps4, coupling lambda, diffusivity D (= a1 a2 W/d0), initial
  * supersaturation U0, scheme, arithmetic precision of the fields, capacity
  * of the grain table (>= 1) and of the seed list used by pf_init_seeds
- * (0 = 64).  dt must not exceed the explicit-Euler bound
- * 2 h^2 / (Lambda max(D, 1)), Lambda = 16/3 for the isotropic Laplacians,
- * 8 for L_{1,0}, 12 for L_{1,0,0}.  Every axis needs at least 4 cells. */
+ * (0 = 64).  Every axis needs at least 4 cells.
+ *
+ * Thermal condition: PF_ISOTHERMAL (F1 = 1, F2 = U) or, in 2D,
+ * PF_FROZEN_GRADIENT: directional solidification in a frozen temperature
+ * field pulled along +y (Eqs. Thermal_F1, Thermal_F2): with
+ * zeta = (y - yT - Vp t) / lT, y = j h and t = step * dt,
+ *   F1 = 1 - (1-k) zeta multiplies a_s^2 dpsi/dt in Eq. PF_a,
+ *   F2 = U + zeta replaces U in its coupling term;
+ * Vp >= 0 (pulling speed, W / tau0), lT > 0 (thermal length, W), yT the
+ * position of the reference isotherm T0 at t = 0.  F1 must stay above 0.05
+ * over the grid at t = 0.  bc_x = PF_BC_PERIODIC makes x periodic (2D).
+ *
+ * dt must not exceed the explicit-Euler bound 2 h^2 / (Lambda max(D, 1/F1min)),
+ * Lambda = 16/3 for the isotropic Laplacians, 8 for L_{1,0}, 12 for L_{1,0,0};
+ * F1min = 1 except with PF_FROZEN_GRADIENT. */
 typedef struct {
     int32_t dim, nx, ny, nz;
     double h, dt, k, eps4, lambda, D, U0;
@@ -77,6 +94,9 @@ typedef struct {
     int32_t precision;  /* pf_precision */
     int32_t max_grains;
     int32_t max_seeds;
+    int32_t bc_x;       /* PF_BC_MIRROR or PF_BC_PERIODIC (2D) */
+    int32_t thermal;    /* PF_ISOTHERMAL or PF_FROZEN_GRADIENT (2D) */
+    double Vp, lT, yT;  /* frozen gradient: pulling speed, thermal length, isotherm T0 at t = 0 */
 } pf_params;
 
 /* A spherical (circular in 2D) seed: centre (x, y, z) and radius r in units
@@ -244,7 +264,10 @@ int pf_group_create(int max_instances, int max_work, void* dev_mem, size_t bytes
 int pf_group_add(pf_group* g, pf_sim* s);
 int pf_group_remove(pf_group* g, pf_sim* s);
 /* Advance every member by n steps.  With use_graph != 0, even-length runs
- * of launches are captured once per membership change and replayed. */
+ * of launches are captured once per membership change and replayed; on the
+ * legacy default stream (NULL), which cannot be captured, every step is
+ * launched directly.  Frozen-temperature members read their step from a
+ * device counter that every launch advances, so replays keep the time. */
 int pf_group_step(pf_group* g, int64_t n, int use_graph);
 int pf_group_size(const pf_group* g);
 int pf_group_destroy(pf_group* g);

@@ -306,6 +306,9 @@ __global__ void k_init_seeds(int dim, int nx, int ny, int nz, double h, double U
     }
 }
 
+// advances the step clock of a group (one thread, after every step launch)
+__global__ void k_tick(long long* clock) { *clock += 1; }
+
 template <typename T> __global__ void k_fill(T* __restrict__ p, T v, long long n) {
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
         p[c] = v;
@@ -356,6 +359,11 @@ cudaError_t launch_tip_radius(const TipArgs& a, double* out, cudaStream_t st) {
         k_tip_radius<float><<<1, TIP_THREADS, 0, st>>>(a, out);
     else
         k_tip_radius<double><<<1, TIP_THREADS, 0, st>>>(a, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tick(long long* clock, cudaStream_t st) {
+    k_tick<<<1, 1, 0, st>>>(clock);
     return cudaGetLastError();
 }
 

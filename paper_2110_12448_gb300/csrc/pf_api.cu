@@ -45,10 +45,23 @@ bool valid_params(const pf_params* p) {
     if (!(p->eps4 >= 0 && p->eps4 < 0.25)) return false;
     if (!(p->D > 0) || !(p->lambda >= 0) || !std::isfinite(p->U0)) return false;
     if (p->max_grains < 1 || p->max_grains > 32767 || p->max_seeds < 0 || p->max_seeds > (1 << 20)) return false;
-    // explicit Euler bound: dt <= 2 h^2 / (Lambda max(D, 1))
+    if (p->bc_x != PF_BC_MIRROR && p->bc_x != PF_BC_PERIODIC) return false;
+    if (p->bc_x == PF_BC_PERIODIC && p->dim != 2) return false;
+    if (p->thermal != PF_ISOTHERMAL && p->thermal != PF_FROZEN_GRADIENT) return false;
+    double F1min = 1.0;
+    if (p->thermal == PF_FROZEN_GRADIENT) {
+        if (p->dim != 2 || !(p->lT > 0) || !std::isfinite(p->lT) || !(p->Vp >= 0) || !std::isfinite(p->Vp) ||
+            !std::isfinite(p->yT))
+            return false;
+        // F1 = 1 - (1-k) zeta is smallest at the top row at t = 0 (the isotherm only moves up)
+        F1min = 1.0 - (1.0 - p->k) * (((p->ny - 1) * p->h - p->yT) / p->lT);
+        if (!(F1min >= 0.05)) return false;
+        F1min = std::min(F1min, 1.0);
+    }
+    // explicit Euler bound: dt <= 2 h^2 / (Lambda max(D, 1 / F1min))
     const bool iso = p->scheme == PF_S21 || p->scheme == PF_SBAR21 || p->scheme == PF_SBAR120;
     const double lam = iso ? 16.0 / 3.0 : (p->dim == 2 ? 8.0 : 12.0);
-    const double bound = 2.0 * p->h * p->h / (lam * std::max(p->D, 1.0));
+    const double bound = 2.0 * p->h * p->h / (lam * std::max(p->D, 1.0 / F1min));
     if (p->dt > bound) return false;
     return true;
 }
@@ -163,9 +176,13 @@ void build_work(const pf_sim* s, int inst, std::vector<WorkItem>& out) {
     }
 }
 
+// the 2D kernel variant with frozen temperature / periodic x
+bool ds_of(const pf_params& p) { return p.thermal == PF_FROZEN_GRADIENT || p.bc_x == PF_BC_PERIODIC; }
+
 int occupancy(const pf_sim* s) {
     const int prec = s->p.precision == PF_F64 ? 1 : 0;
-    return s->p.dim == 2 ? occupancy_step2d(prec, s->p.scheme, s->bx) : occupancy_step3d(prec, s->p.scheme, s->bx, s->by);
+    return s->p.dim == 2 ? occupancy_step2d(prec, s->p.scheme, s->bx, ds_of(s->p))
+                         : occupancy_step3d(prec, s->p.scheme, s->bx, s->by);
 }
 
 InstRec make_rec(const pf_sim* s, int parity_offset) {
@@ -180,6 +197,13 @@ InstRec make_rec(const pf_sim* s, int parity_offset) {
     r.ny = s->p.ny;
     r.nz = s->p.dim == 3 ? s->p.nz : 1;
     r.parity_offset = parity_offset;
+    r.thermal = s->p.thermal == PF_FROZEN_GRADIENT ? 1 : 0;
+    r.bcx = s->p.bc_x == PF_BC_PERIODIC ? 1 : 0;
+    if (r.thermal) {
+        r.zA = s->p.h / s->p.lT;
+        r.zB = s->p.yT / s->p.lT;
+        r.zC = s->p.Vp * s->p.dt / s->p.lT;
+    }
     r.h = s->p.h;
     r.dt = s->p.dt;
     r.k = s->p.k;
@@ -240,10 +264,14 @@ int upload_rot(pf_sim* s) {
     return PF_OK;
 }
 
-bool launch_sim_step(const pf_sim* s, int launch_parity) {
+// One step of a handle from step `step` (its parity selects the time level).
+bool launch_sim_step(const pf_sim* s, int64_t step) {
     const int prec = s->p.precision == PF_F64 ? 1 : 0;
-    if (s->p.dim == 2) return launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, launch_parity);
-    return launch_step3d(prec, s->p.scheme, s->bx, s->by, s->grid, s->st, s->work, s->n_work, s->rec, launch_parity);
+    const int lp = (int)(step & 1);
+    if (s->p.dim == 2)
+        return launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp,
+                             StepClock{nullptr, nullptr, (long long)step}, ds_of(s->p));
+    return launch_step3d(prec, s->p.scheme, s->bx, s->by, s->grid, s->st, s->work, s->n_work, s->rec, lp);
 }
 
 }  // namespace
@@ -367,7 +395,7 @@ int pf_step(pf_sim* s, int64_t n) {
         if (rc != PF_OK) return rc;
     }
     for (int64_t i = 0; i < n; ++i) {
-        if (!launch_sim_step(s, (int)((s->step + i) & 1))) return PF_ERR_INVALID;
+        if (!launch_sim_step(s, s->step + i)) return PF_ERR_INVALID;
     }
     if (n > 0) CK(cudaGetLastError());
     s->step += n;
@@ -684,8 +712,15 @@ struct pf_group {
     bool dirty;
     struct Cls {
         int dim, scheme, prec, bx, by, w0, n, grid;
+        bool ds;  // 2D kernel variant with frozen temperature / periodic x
     };
     std::vector<Cls> classes;
+    // step counter of frozen-temperature members: member m is at step
+    // step_base[m] + *clock; the clock is advanced on the device after every
+    // launch (also inside captured graphs) when any member is thermal
+    long long* clock;
+    long long* step_base;
+    bool thermal_any;
     cudaGraphExec_t graph;
     int graph_len;
     int graph_parity;
@@ -702,8 +737,8 @@ int group_rebuild(pf_group* g) {
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
     auto key = [&](int i) {
         const pf_sim* s = g->members[i];
-        return ((long long)s->p.dim << 40) | ((long long)s->p.scheme << 32) | ((long long)s->p.precision << 24) |
-               ((long long)s->bx << 12) | (long long)s->by;
+        return ((long long)ds_of(s->p) << 48) | ((long long)s->p.dim << 40) | ((long long)s->p.scheme << 32) |
+               ((long long)s->p.precision << 24) | ((long long)s->bx << 12) | (long long)s->by;
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
     for (size_t m = 0; m < g->members.size(); ++m) {
@@ -715,7 +750,8 @@ int group_rebuild(pf_group* g) {
         const pf_sim* s = g->members[i];
         const long long k = key(i);
         if (k != prev) {
-            pf_group::Cls c{s->p.dim, s->p.scheme, s->p.precision == PF_F64 ? 1 : 0, s->bx, s->by, (int)work.size(), 0, 0};
+            pf_group::Cls c{s->p.dim, s->p.scheme, s->p.precision == PF_F64 ? 1 : 0, s->bx, s->by, (int)work.size(), 0, 0,
+                            ds_of(s->p)};
             g->classes.push_back(c);
             prev = k;
         }
@@ -724,11 +760,18 @@ int group_rebuild(pf_group* g) {
     }
     if ((int)work.size() > g->max_work) return PF_ERR_BUDGET;
     for (auto& c : g->classes) {
-        int occ = c.dim == 2 ? occupancy_step2d(c.prec, c.scheme, c.bx) : occupancy_step3d(c.prec, c.scheme, c.bx, c.by);
+        int occ = c.dim == 2 ? occupancy_step2d(c.prec, c.scheme, c.bx, c.ds) : occupancy_step3d(c.prec, c.scheme, c.bx, c.by);
         if (occ <= 0) return PF_ERR_INVALID;
         c.grid = std::min(c.n, occ * num_sms());
     }
     if (!recs.empty()) CK(cudaMemcpyAsync(g->recs, recs.data(), recs.size() * sizeof(InstRec), cudaMemcpyHostToDevice, g->st));
+    g->thermal_any = false;
+    std::vector<long long> steps(g->members.size() + 1, 0);  // [0] = clock, then the step of each member
+    for (size_t m = 0; m < g->members.size(); ++m) {
+        steps[m + 1] = g->members[m]->step;
+        if (g->members[m]->p.thermal == PF_FROZEN_GRADIENT) g->thermal_any = true;
+    }
+    CK(cudaMemcpyAsync(g->clock, steps.data(), steps.size() * sizeof(long long), cudaMemcpyHostToDevice, g->st));
     if (!work.empty()) CK(cudaMemcpyAsync(g->work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, g->st));
     CK(cudaStreamSynchronize(g->st));
     if (g->graph) {
@@ -740,13 +783,16 @@ int group_rebuild(pf_group* g) {
 }
 
 bool group_launch_once(pf_group* g, int launch_parity) {
+    const StepClock clk{g->clock, g->step_base, 0};
     for (const auto& c : g->classes) {
         if (c.n == 0) continue;
-        bool ok = c.dim == 2 ? launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs, launch_parity)
+        bool ok = c.dim == 2 ? launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs,
+                                             launch_parity, clk, c.ds)
                              : launch_step3d(c.prec, c.scheme, c.bx, c.by, c.grid, g->st, g->work + c.w0, c.n, g->recs,
                                              launch_parity);
         if (!ok) return false;
     }
+    if (g->thermal_any && launch_tick(g->clock, g->st) != cudaSuccess) return false;
     return true;
 }
 
@@ -756,7 +802,8 @@ extern "C" {
 
 size_t pf_group_required_bytes(int max_instances, int max_work) {
     if (max_instances < 1 || max_work < 1) return 0;
-    return align256((size_t)max_instances * sizeof(InstRec)) + align256((size_t)max_work * sizeof(WorkItem));
+    return align256((size_t)max_instances * sizeof(InstRec)) + align256((size_t)max_work * sizeof(WorkItem)) +
+           align256((size_t)(max_instances + 1) * sizeof(long long));
 }
 
 int pf_group_work_items(const pf_sim* s) {
@@ -779,6 +826,10 @@ int pf_group_create(int max_instances, int max_work, void* dev_mem, size_t bytes
     g->base = static_cast<char*>(dev_mem);
     g->recs = reinterpret_cast<InstRec*>(g->base);
     g->work = reinterpret_cast<WorkItem*>(g->base + align256((size_t)max_instances * sizeof(InstRec)));
+    g->clock = reinterpret_cast<long long*>(g->base + align256((size_t)max_instances * sizeof(InstRec)) +
+                                            align256((size_t)max_work * sizeof(WorkItem)));
+    g->step_base = g->clock + 1;
+    g->thermal_any = false;
     g->launches = 0;
     g->dirty = true;
     g->graph = nullptr;
@@ -821,7 +872,8 @@ int pf_group_step(pf_group* g, int64_t n, int use_graph) {
     }
     int64_t done = 0;
     const int GL = 16;  // launches per graph replay (even)
-    if (use_graph && n >= GL) {
+    // the legacy default stream cannot be captured into a graph
+    if (use_graph && n >= GL && g->st != nullptr && g->st != cudaStreamPerThread) {
         if ((g->launches & 1) != 0) {
             if (!group_launch_once(g, 1)) return PF_ERR_INVALID;
             ++done;

@@ -40,7 +40,12 @@ struct InstRec {
     const int16_t* grain;  // per-cell grain index
     const void* rot;       // n_grains x 9, crystal -> lab, in the field precision
     int32_t nx, ny, nz, parity_offset;
+    int32_t thermal;  // 1: frozen temperature along +y (2D)
+    int32_t bcx;      // 1: periodic x (2D)
     double h, dt, k, eps4, lambda, D;
+    // frozen temperature: zeta(row j, step n) = j zA - zB - n zC
+    // (zA = h / lT, zB = yT / lT, zC = Vp dt / lT)
+    double zA, zB, zC;
     // derived constants, filled on the host (no FP64 arithmetic in FP32 kernels)
     float cf[NC];
     double cd[NC];
@@ -69,12 +74,24 @@ __device__ __forceinline__ int mirror_idx(int i, int n) {
 
 // Launchers (defined in step2d.cu / step3d.cu).  prec: 0 float, 1 double.
 // Return false if (prec, scheme, block) has no compiled kernel.
+// Step counter of the instances in a launch (only read for frozen-temperature
+// instances): with clock == nullptr every instance is at step `step`;
+// otherwise instance i is at step base[i] + *clock (groups: the clock is
+// advanced on the device after every launch, so graph replays stay exact).
+struct StepClock {
+    const long long* clock;
+    const long long* base;
+    long long step;
+};
 bool launch_step2d(int prec, int scheme, int bx, int grid, cudaStream_t st, const WorkItem* work, int n_work,
-                   const InstRec* recs, int launch_parity);
+                   const InstRec* recs, int launch_parity, StepClock clk, bool ds);
 bool launch_step3d(int prec, int scheme, int bx, int by, int grid, cudaStream_t st, const WorkItem* work,
                    int n_work, const InstRec* recs, int launch_parity);
+// clock += 1 (one thread)
+cudaError_t launch_tick(long long* clock, cudaStream_t st);
 // Blocks of the fused kernel that fit on one SM (0 if not compiled).
-int occupancy_step2d(int prec, int scheme, int bx);
+// ds: the kernel variant for frozen-temperature / periodic-x instances
+int occupancy_step2d(int prec, int scheme, int bx, bool ds);
 int occupancy_step3d(int prec, int scheme, int bx, int by);
 
 // Observation / initialisation kernels (observe.cu).

@@ -247,28 +247,34 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using t = float2; };
 template <> struct Vec2<double> { using t = double2; };
 
+// Column index of a ghost column: periodic wrap or cell-centred mirror.
+__device__ __forceinline__ int col_idx(int c, int nx, bool per) {
+    return per ? ((c % nx) + nx) % nx : mirror_idx(c, nx);
+}
+
 // Load the pair (c, c+1) of a row; c is even.  Vector load when both columns
-// are inside and the row is 2-element aligned, mirrored scalar loads otherwise.
+// are inside and the row is 2-element aligned, wrapped or mirrored scalar
+// loads otherwise.
 template <typename T>
-__device__ __forceinline__ void load_pair(const T* __restrict__ row, int c, int nx, bool vec, T& a, T& b) {
+__device__ __forceinline__ void load_pair(const T* __restrict__ row, int c, int nx, bool vec, bool per, T& a, T& b) {
     if (vec && c >= 0 && c + 1 < nx) {
         const typename Vec2<T>::t v = __ldg(reinterpret_cast<const typename Vec2<T>::t*>(row + c));
         a = v.x;
         b = v.y;
     } else {
-        a = __ldg(row + mirror_idx(c, nx));
-        b = __ldg(row + mirror_idx(c + 1, nx));
+        a = __ldg(row + col_idx(c, nx, per));
+        b = __ldg(row + col_idx(c + 1, nx, per));
     }
 }
-__device__ __forceinline__ void load_grain_pair(const int16_t* __restrict__ row, int c, int nx, bool vec, int& a,
-                                                int& b) {
+__device__ __forceinline__ void load_grain_pair(const int16_t* __restrict__ row, int c, int nx, bool vec, bool per,
+                                                int& a, int& b) {
     if (vec && c >= 0 && c + 1 < nx) {
         const int v = __ldg(reinterpret_cast<const int*>(row + c));
         a = (int)(int16_t)(v & 0xffff);
         b = (int)(int16_t)((unsigned)v >> 16);
     } else {
-        a = __ldg(row + mirror_idx(c, nx));
-        b = __ldg(row + mirror_idx(c + 1, nx));
+        a = __ldg(row + col_idx(c, nx, per));
+        b = __ldg(row + col_idx(c + 1, nx, per));
     }
 }
 template <typename T>
@@ -295,9 +301,13 @@ __device__ __forceinline__ void store_pair(T* __restrict__ row, int c, bool vec,
 #define PF_STEP2D_MIN_BLOCKS_F32 16
 #endif
 
-template <typename T, int S>
+// DS = false: isothermal instances with mirror walls (the flags below are
+// compile-time false and their code disappears); DS = true: instances with a
+// frozen temperature and/or periodic x.
+template <typename T, int S, bool DS>
 __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D_MIN_BLOCKS_F32 : 1)
-    k_step2d(const WorkItem* __restrict__ work, int n_work, const InstRec* __restrict__ recs, int launch_parity) {
+    k_step2d(const WorkItem* __restrict__ work, int n_work, const InstRec* __restrict__ recs, int launch_parity,
+             StepClock clk) {
     constexpr bool ISO = (S == S21 || S == SBAR21);
     const int lane = threadIdx.x & 31;
     const int warps_per_block = blockDim.x >> 5;
@@ -323,6 +333,15 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         const T ih2 = cst[C_IH2], i6h2 = cst[C_I6H2], g10c = cst[C_G10], g01c = cst[C_G01];
         const T isq2dt = cst[C_ISQ2DT];
         const bool vec = (nx & 1) == 0;
+        const bool per = DS && rec.bcx != 0;
+        // frozen temperature: zeta at row p = zeta_y0 + (p - y0) zA (Eqs. Thermal_F1/_F2)
+        const bool thermal = DS && rec.thermal != 0;
+        T zeta_y0 = T(0), zA = T(0);
+        if (thermal) {
+            const long long n = clk.clock ? clk.base[wi.inst] + *clk.clock : clk.step;
+            zeta_y0 = (T)((double)wi.y0 * rec.zA - rec.zB - (double)n * rec.zC);
+            zA = (T)rec.zA;
+        }
 
         const int x0 = wi.x0, y0 = wi.y0;
         const int y1 = min(y0 + wi.ext, ny);
@@ -330,14 +349,15 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         const bool realL = cL >= 0 && cL < nx, realR = cL + 1 >= 0 && cL + 1 < nx;
         const bool outL = lane >= 1 && lane <= 30 && realL;
         const bool outR = lane >= 1 && lane <= 30 && realR;
-        const bool edge = (x0 - 2 < 0) || (x0 + 62 > nx);  // warp holds ghost columns
+        // warp holds mirror ghost columns (periodic ghosts are real cells, computed in place)
+        const bool edge = !per && ((x0 - 2 < 0) || (x0 + 62 > nx));
         // lanes holding the mirror images of ghost columns (phase-1 copies)
         const int mL = mirror_idx(cL, nx), mR = mirror_idx(cL + 1, nx);
         const int srcL = (mL - (x0 - 2)) >> 1, srcR = (mR - (x0 - 2)) >> 1;
         const bool hiL = ((mL - (x0 - 2)) & 1) != 0, hiR = ((mR - (x0 - 2)) & 1) != 0;
 
         auto fetch_row = [&](const T* f, int vr, T& a, T& b) {
-            load_pair<T>(f + (size_t)mirror_idx(vr, ny) * nx, cL, nx, vec, a, b);
+            load_pair<T>(f + (size_t)mirror_idx(vr, ny) * nx, cL, nx, vec, per, a, b);
         };
         auto make_row = [&](T a, T b, bool wide) {
             Row<T> row;
@@ -449,9 +469,17 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
                 G = bc<T>(T(0.25) * ih2) * fma(ex, ex, ey * ey);
             }
             const V<T> ac = aniso_a2<T>(ex * bc<T>(ih_half), ey * bc<T>(ih_half), RR, eps, hh);
-            const V<T> ph = ph0.C(), u = u0.C();
+            const V<T> ph = ph0.C();
+            V<T> u = u0.C();  // F2 of Eq. PF_a
+            T iF1 = T(1);     // 1 / F1
+            if (thermal) {
+                const T z = zeta_y0 + T(p - y0) * zA;
+                u = u + bc<T>(z);
+                iF1 = M<T>::rcp(T(1) - omk * z);
+            }
             const V<T> src = bc<T>(SQ2) * (ph - bc<T>(lam) * (bc<T>(T(1)) - ph * ph) * u);
-            const V<T> rate = (L + N + src) * rcp2(ac * ac) - bc<T>(SQ2) * ph * G;
+            V<T> rate = (L + N + src) * rcp2(ac * ac) - bc<T>(SQ2) * ph * G;
+            if (thermal) rate = rate * bc<T>(iF1);
             psin = fma(bc<T>(dt), rate, C0);
             phin = mk(M<T>::tanh_isq2(psin.x()), M<T>::tanh_isq2(psin.y()));
             dph = phin - ph;
@@ -573,10 +601,10 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             V<T> psn, fn, dm = bc<T>(T(0)), d0;
             const bool ghost = (y0 - 1) < 0;
             if (!ghost) {
-                load_grain_pair(grain + (size_t)(y0 - 1) * nx, cL, nx, vec, gL, gR);
+                load_grain_pair(grain + (size_t)(y0 - 1) * nx, cL, nx, vec, per, gL, gR);
                 phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, psn, fn, dm);
             }
-            load_grain_pair(grain + (size_t)y0 * nx, cL, nx, vec, gL, gR);
+            load_grain_pair(grain + (size_t)y0 * nx, cL, nx, vec, per, gL, gR);
             phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, psn, fn, d0);
             if (ghost) dm = d0;
             phin_cur = fn;
@@ -601,7 +629,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         int nGa = 0, nGb = 0;
         fetch_row(psi, y0 + 2, nPa, nPb);
         fetch_row(Uf, y0 + 1, nUa, nUb);
-        if (y0 + 1 < ny) load_grain_pair(grain + (size_t)(y0 + 1) * nx, cL, nx, vec, nGa, nGb);
+        if (y0 + 1 < ny) load_grain_pair(grain + (size_t)(y0 + 1) * nx, cL, nx, vec, per, nGa, nGb);
 
         // ---------------- sweep ----------------
         for (int r = y0; r < y1; ++r) {
@@ -611,7 +639,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             const int gL = nGa, gR = nGb;
             fetch_row(psi, r + 3, nPa, nPb);
             fetch_row(Uf, r + 2, nUa, nUb);
-            if (r + 2 < ny) load_grain_pair(grain + (size_t)(r + 2) * nx, cL, nx, vec, nGa, nGb);
+            if (r + 2 < ny) load_grain_pair(grain + (size_t)(r + 2) * nx, cL, nx, vec, per, nGa, nGb);
 
             // phase 1 at row r+1
             V<T> phn = bc<T>(T(0));
@@ -653,17 +681,22 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
 constexpr int WARPS_PER_BLOCK = PF_STEP2D_WPB;
 
 template <typename T, int S>
-bool launch_one(int grid_warps, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp) {
+bool launch_one(int grid_warps, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp,
+                StepClock clk, bool ds) {
     const int blocks = (grid_warps + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-    k_step2d<T, S><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp);
+    if (ds)
+        k_step2d<T, S, true><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
+    else
+        k_step2d<T, S, false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
     return true;
 }
 
-template <typename T, int S> int occ_one() {
+template <typename T, int S> int occ_one(bool ds) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S>, 32 * WARPS_PER_BLOCK, 0) != cudaSuccess)
-        return 0;
-    return n * WARPS_PER_BLOCK;
+    const cudaError_t e =
+        ds ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, true>, 32 * WARPS_PER_BLOCK, 0)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, false>, 32 * WARPS_PER_BLOCK, 0);
+    return e == cudaSuccess ? n * WARPS_PER_BLOCK : 0;
 }
 
 }  // namespace
@@ -671,38 +704,38 @@ template <typename T, int S> int occ_one() {
 // The 2D kernel is warp-granular: `bx` must be 64 (columns a warp holds) and
 // `grid` counts warps.
 bool launch_step2d(int prec, int scheme, int bx, int grid, cudaStream_t st, const WorkItem* work, int n_work,
-                   const InstRec* recs, int lp) {
+                   const InstRec* recs, int lp, StepClock clk, bool ds) {
     if (bx != WARP_COLS) return false;
     if (prec == 0) {
         switch (scheme) {
-            case S10: return launch_one<float, S10>(grid, st, work, n_work, recs, lp);
-            case S21: return launch_one<float, S21>(grid, st, work, n_work, recs, lp);
-            case SBAR21: return launch_one<float, SBAR21>(grid, st, work, n_work, recs, lp);
+            case S10: return launch_one<float, S10>(grid, st, work, n_work, recs, lp, clk, ds);
+            case S21: return launch_one<float, S21>(grid, st, work, n_work, recs, lp, clk, ds);
+            case SBAR21: return launch_one<float, SBAR21>(grid, st, work, n_work, recs, lp, clk, ds);
         }
     } else {
         switch (scheme) {
-            case S10: return launch_one<double, S10>(grid, st, work, n_work, recs, lp);
-            case S21: return launch_one<double, S21>(grid, st, work, n_work, recs, lp);
-            case SBAR21: return launch_one<double, SBAR21>(grid, st, work, n_work, recs, lp);
+            case S10: return launch_one<double, S10>(grid, st, work, n_work, recs, lp, clk, ds);
+            case S21: return launch_one<double, S21>(grid, st, work, n_work, recs, lp, clk, ds);
+            case SBAR21: return launch_one<double, SBAR21>(grid, st, work, n_work, recs, lp, clk, ds);
         }
     }
     return false;
 }
 
 // Warps of the fused kernel resident on one SM (0 if not compiled).
-int occupancy_step2d(int prec, int scheme, int bx) {
+int occupancy_step2d(int prec, int scheme, int bx, bool ds) {
     if (bx != WARP_COLS) return 0;
     if (prec == 0) {
         switch (scheme) {
-            case S10: return occ_one<float, S10>();
-            case S21: return occ_one<float, S21>();
-            case SBAR21: return occ_one<float, SBAR21>();
+            case S10: return occ_one<float, S10>(ds);
+            case S21: return occ_one<float, S21>(ds);
+            case SBAR21: return occ_one<float, SBAR21>(ds);
         }
     } else {
         switch (scheme) {
-            case S10: return occ_one<double, S10>();
-            case S21: return occ_one<double, S21>();
-            case SBAR21: return occ_one<double, SBAR21>();
+            case S10: return occ_one<double, S10>(ds);
+            case S21: return occ_one<double, S21>(ds);
+            case SBAR21: return occ_one<double, SBAR21>(ds);
         }
     }
     return 0;

@@ -86,6 +86,14 @@ class Workload:
     centres: np.ndarray      # (n_grains, 3) reference point of each grain
     steps: int = 1
     name: str = ""
+    # directional solidification (frozen temperature along +y) and x walls
+    bc_x: int = 0            # 0 mirror, 1 periodic
+    thermal: int = 0         # 0 isothermal, 1 frozen gradient
+    Vp: float = 0.0          # pulling speed (W / tau0)
+    lT: float = 1.0          # thermal length (W)
+    yT: float = 0.0          # isotherm T0 at t = 0 (W)
+    psi_init: Optional[np.ndarray] = None  # explicit initial fields (else from the seeds)
+    U_init: Optional[np.ndarray] = None
 
     @property
     def n_cells(self) -> int:
@@ -133,6 +141,35 @@ def free_dendrite_3d(n: int = 256, scheme: str = "SBAR120", steps: int = 10000, 
     seeds = np.array([[c[0], c[1], c[2], 8 * p["h"]]])
     return Workload(3, n, n, n, p["h"], p["dt"], p["k"], p["eps4"], p["lam"], p["D"], p["U0"], scheme, seeds,
                     np.zeros(1, np.int16), R.reshape(1, 9), np.array([c]), steps, f"free_dendrite_3d_{n}^3_{scheme}")
+
+
+def directional_2d(nx: int = 256, ny: int = 512, theta_deg: float = 0.0, scheme: str = "SBAR21",
+                   Vp: float = 0.1, lT: float = 500.0, steps: int = 5000, seed: int = SEED_BASE + 5,
+                   modes: int = 6, amp: float = 0.5, **phys) -> Workload:
+    """Directional solidification of one grain (crystal turned by theta from the
+    pulling axis +y) in a frozen temperature field, periodic in x (Sec. 4.2):
+    a planar front on the isotherm T0 at y = yT = ny h / 8, perturbed by a few
+    seeded sine modes of amplitude `amp` (W); U = 0 in the solid and the steady
+    diffusion profile -1 + exp(-Vp (y - y_front) / D) ahead of it (U = -1 far
+    away: c_l0 = c_inf / k at T0)."""
+    p = _physics_2d(U0=-1.0, **phys)
+    rng = np.random.default_rng(seed)
+    h = p["h"]
+    yT = ny * h / 8.0
+    x = np.arange(nx) * h
+    y = np.arange(ny) * h
+    front = np.full(nx, yT)
+    Lx = nx * h
+    for m in range(1, modes + 1):
+        front += amp / math.sqrt(modes) * np.sin(2 * math.pi * m * x / Lx + rng.uniform(0, 2 * math.pi))
+    eta = y[:, None] - front[None, :]
+    psi = -eta
+    U = np.where(eta < 0, 0.0, -1.0 + np.exp(-Vp * np.maximum(eta, 0.0) / p["D"]))
+    c = (Lx / 2, 0.0, 0.0)
+    return Workload(2, nx, ny, 1, h, p["dt"], p["k"], p["eps4"], p["lam"], p["D"], p["U0"], scheme,
+                    np.array([[c[0], -100.0 * h, 0.0, h]]), np.zeros(1, np.int16), rot2d(theta_deg).reshape(1, 9),
+                    np.array([c]), steps, f"directional_2d_{nx}x{ny}_{theta_deg:g}deg_{scheme}",
+                    bc_x=1, thermal=1, Vp=Vp, lT=lT, yT=yT, psi_init=psi, U_init=U)
 
 
 def place_seeds(rng: np.random.Generator, dim: int, extent, n_seeds: int, r: float, tries: int = 1000):

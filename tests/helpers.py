@@ -6,9 +6,15 @@ from oracle import oracle as O
 from paper_2110_12448_gb300 import synth
 
 
-def oracle_params(w, scheme=None, bc=None, **over):
+def oracle_params(w, scheme=None, bc=None, step=0, **over):
+    """Oracle parameters of workload w (walls, frozen temperature) for a call
+    that starts at time step `step` of the simulation."""
+    if bc is None:
+        bc = O.BC_PERIODIC_X if getattr(w, "bc_x", 0) else O.BC_MIRROR
     d = dict(dim=w.dim, nx=w.nx, ny=w.ny, nz=w.nz, scheme=synth.SCHEMES[scheme or w.scheme],
-             bc=O.BC_MIRROR if bc is None else bc, h=w.h, dt=w.dt, k=w.k, eps4=w.eps4, lam=w.lam, D=w.D)
+             bc=bc, h=w.h, dt=w.dt, k=w.k, eps4=w.eps4, lam=w.lam, D=w.D,
+             thermal=getattr(w, "thermal", 0), Vp=getattr(w, "Vp", 0.0), lT=getattr(w, "lT", 1.0),
+             yT=getattr(w, "yT", 0.0), t0=step * w.dt)
     d.update(over)
     return O.params(**d)
 

@@ -66,3 +66,29 @@ def test_stability_bound_boundary():
     assert native.required_bytes(_p(dt=ok)) > 0
     # S10 has the larger Laplacian symbol (8) and so the tighter bound
     assert native.required_bytes(_p(scheme="S10", dt=ok)) == 0
+
+
+DS = dict(thermal=1, bc_x=1, Vp=0.1, lT=100.0, yT=5.0)  # frozen gradient, periodic x
+
+
+@pytest.mark.parametrize("bad", [
+    dict(bc_x=2), dict(thermal=2),
+    dict(dim=3, nz=8, scheme="SBAR120", bc_x=1, dt=0.01),        # periodic x is 2D only
+    dict(dim=3, nz=8, scheme="SBAR120", thermal=1, lT=100.0, dt=0.01),  # frozen gradient is 2D only
+    dict(DS, lT=0.0), dict(DS, lT=float("inf")), dict(DS, Vp=-0.1), dict(DS, yT=float("nan")),
+    # F1 = 1 - (1-k) ((ny-1) h - yT) / lT at the top row: 1 - 0.85 * (47 * 0.8 - 5) / 30 < 0.05
+    dict(DS, lT=30.0),
+])
+def test_invalid_directional_parameters_rejected(bad):
+    assert native.required_bytes(_p(**bad)) == 0
+
+
+def test_directional_parameters_accepted_and_bound():
+    assert native.required_bytes(_p(**DS)) > 0
+    # with F1min = 1 - 0.85 * (47 * 0.8 - 5) / 36 = 0.230 the psi mobility 1/F1min = 4.35 < D,
+    # so the D bound still applies; with a small D the 1/F1min term takes over
+    F1min = 1 - 0.85 * (47 * 0.8 - 5) / 36.0
+    d_small = dict(DS, lT=36.0, D=1.0, lam=10.0)
+    bound = 2 * 0.64 / (16 / 3 * (1 / F1min))
+    assert native.required_bytes(_p(**dict(d_small, dt=bound * 0.99))) > 0
+    assert native.required_bytes(_p(**dict(d_small, dt=bound * 1.01))) == 0

@@ -1,0 +1,151 @@
+"""GPU parity of directional solidification (frozen temperature along +y,
+Eqs. Thermal_F1/_F2 in Eq. PF_a; periodic x, Sec. 4.2) through the C-ABI
+against the FP64 oracle: one and many steps for the three 2D schemes on ragged
+and odd widths, the time origin of later steps, batched groups replayed from
+CUDA graphs (the device step clock), mixed thermal / isothermal members, FP32
+within the one-step tolerances, and the pulled planar front's steady state."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2110_12448_gb300 import synth
+from tests.helpers import max_abs, oracle_params, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def native():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_12448_gb300 import native as N
+    N.lib()
+    return N
+
+
+def ds_state(seed, nx, ny, scheme="SBAR21", n_grains=3, lT=60.0, Vp=0.3):
+    rng = np.random.default_rng(seed)
+    w = synth.directional_2d(nx, ny, 20.0, scheme, Vp=Vp, lT=lT)
+    w.yT = ny * w.h * 0.4
+    psi, U = synth.random_state(rng, w)
+    g, rots = synth.random_grains(rng, w, n_grains)
+    w.rots = rots
+    return w, psi, U, g, rots
+
+
+def gpu_sim(N, w, prec, g, rots, psi, U, step=0, stream=None):
+    p = N.make_params(2, w.nx, w.ny, 1, w.h, w.dt, w.k, w.eps4, w.lam, w.D, w.U0, w.scheme, prec,
+                      max_grains=rots.shape[0], bc_x=w.bc_x, thermal=w.thermal, Vp=w.Vp, lT=w.lT, yT=w.yT)
+    s = N.Sim(p, stream=stream)
+    s.set_grains(rots)
+    s.set_grain_index(g)
+    s.set_fields(psi, U)
+    s.set_step(step)
+    return s
+
+
+@pytest.mark.parametrize("nx", [64, 131, 190])
+@pytest.mark.parametrize("scheme", ["SBAR21", "S21", "S10"])
+def test_fp64_one_step_matches_oracle(native, scheme, nx):
+    w, psi, U, g, rots = ds_state(1, nx, 47, scheme)
+    s = gpu_sim(native, w, "f64", g, rots, psi, U, step=37)
+    s.step(1)
+    gp, gu = s.get_fields()
+    op, ou = O.step(oracle_params(w, step=37), rots, g, psi, U, 1)
+    assert rel_err(gp, op) < 1e-12 and rel_err(gu, ou) < 1e-12
+
+
+@pytest.mark.parametrize("scheme", ["SBAR21", "S10"])
+def test_fp64_many_steps(native, scheme):
+    w, psi, U, g, rots = ds_state(2, 97, 41, scheme)
+    s = gpu_sim(native, w, "f64", g, rots, psi, U, step=5)
+    s.step(7)
+    s.step(5)
+    gp, gu = s.get_fields()
+    op, ou = O.step(oracle_params(w, step=5), rots, g, psi, U, 12)
+    assert rel_err(gp, op) < 12e-12 and rel_err(gu, ou) < 12e-12
+
+
+def test_group_graph_clock(native):
+    # two frozen-gradient members at different steps and one isothermal member,
+    # 40 steps in a group (two graph replays of 16 plus single launches)
+    cases = []
+    for i, (nx, step) in enumerate([(70, 0), (64, 123)]):
+        w, psi, U, g, rots = ds_state(10 + i, nx, 33)
+        cases.append((w, psi, U, g, rots, step))
+    wi = synth.free_dendrite_2d(48, 10.0)
+    rng = np.random.default_rng(7)
+    psi_i, U_i = synth.random_state(rng, wi)
+    import torch
+    st = torch.cuda.Stream()
+    sims = [gpu_sim(native, w, "f64", g, rots, psi, U, step, stream=st) for w, psi, U, g, rots, step in cases]
+    si = native.Sim.from_workload(wi, "f64", stream=st)
+    si.set_fields(psi_i, U_i)
+    grp = native.Group(3, sum(native.Group.work_items(s) for s in sims + [si]), stream=st)
+    for s in sims + [si]:
+        grp.add(s)
+    grp.step(3, use_graph=False)
+    grp.step(37, use_graph=True)
+    grp.close()
+    for s, (w, psi, U, g, rots, step) in zip(sims, cases):
+        gp, gu = s.get_fields()
+        op, ou = O.step(oracle_params(w, step=step), rots, g, psi, U, 40)
+        assert rel_err(gp, op) < 40e-12 and rel_err(gu, ou) < 40e-12
+        assert s.steps_done == step + 40
+    gp, gu = si.get_fields()
+    op, ou = O.step(oracle_params(wi), wi.rots, np.zeros(wi.shape, np.int16), psi_i, U_i, 40)
+    assert rel_err(gp, op) < 40e-12 and rel_err(gu, ou) < 40e-12
+
+
+@pytest.mark.parametrize("scheme", ["SBAR21", "S21", "S10"])
+def test_fp32_one_step(native, scheme):
+    w, psi, U, g, rots = ds_state(3, 131, 40, scheme)
+    psi32, U32 = psi.astype(np.float32), U.astype(np.float32)
+    s = gpu_sim(native, w, "f32", g, rots, psi32, U32, step=11)
+    s.step(1)
+    gp, gu = s.get_fields()
+    op, ou = O.step(oracle_params(w, step=11), rots, g, psi32.astype(np.float64), U32.astype(np.float64), 1)
+    assert max_abs(np.tanh(gp.astype(np.float64) / math.sqrt(2)), np.tanh(op / math.sqrt(2))) < 2e-6
+    assert max_abs(gu, ou) < 5e-6
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_pulled_planar_front_tracks_the_isotherm(native, prec):
+    # same setting as the oracle pin: V W / D = 0.016, the front must move at Vp
+    # on the isotherm with U = 0 in the new solid
+    nx, ny = 64, 220
+    w = synth.directional_2d(nx, ny, 0.0, "SBAR21", Vp=0.1, lT=150.0, amp=0.0)
+    w.eps4 = 0.0
+    s = native.Sim.from_workload(w, prec)
+
+    def front():
+        psi, U = s.get_fields()
+        col = psi[:, 5].astype(np.float64)
+        j = int(np.nonzero((col[:-1] >= 0) & (col[1:] < 0))[0][0])
+        return (j + col[j] / (col[j] - col[j + 1])) * w.h, j, U
+
+    s.step(5000)
+    y1, _, _ = front()
+    s.step(5000)
+    y2, j2, U = front()
+    t = 10000 * w.dt
+    assert abs((y2 - y1) / (5000 * w.dt) - w.Vp) <= 0.01 * w.Vp
+    assert abs(y2 - (w.yT + w.Vp * t)) < 0.25
+    assert np.max(np.abs(U[j2 - 12])) < 0.01
+
+
+def test_group_on_legacy_stream_launches_directly(native):
+    # graphs need a capturable stream: on the legacy default stream the group
+    # falls back to direct launches and stays exact
+    w, psi, U, g, rots = ds_state(21, 64, 33)
+    s = gpu_sim(native, w, "f64", g, rots, psi, U, 9)
+    grp = native.Group(1, native.Group.work_items(s))
+    grp.add(s)
+    grp.step(20, use_graph=True)
+    grp.close()
+    gp, gu = s.get_fields()
+    op, ou = O.step(oracle_params(w, step=9), rots, g, psi, U, 20)
+    assert rel_err(gp, op) < 20e-12 and rel_err(gu, ou) < 20e-12
