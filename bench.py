@@ -34,6 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS & %HBM peak, batched FP32 vs plain FP64 at stated error; p50/p99 latency"
 THETAS = tuple(range(0, 50, 5))
+DS_THETAS = (0, 10, 20, 30, 40)
+DS_VP, DS_LT = 0.1, 2000.0
 OBS_EVERY = 100
 B_PER_CELL = {"f32": 18, "f64": 34}  # read psi, U, grain; write psi', U'
 
@@ -63,7 +65,8 @@ TRAFFIC = {
 # and the FP32 peak from the unit counts and the maximum clock: 152 SMs x 128
 # FP32 lanes x 2 (FMA) x 2.07 GHz.
 # (3D: executed per output cell, including the ring-1 recompute of the 30 x 14 tile)
-FLOP_PER_CELL = {("sweep2d", "SBAR21"): 315, ("poly2d", "SBAR21"): 315, ("dendrite3d", "SBAR120"): 1001}
+FLOP_PER_CELL = {("sweep2d", "SBAR21"): 315, ("poly2d", "SBAR21"): 315, ("directional2d", "SBAR21"): 315,
+                 ("dendrite3d", "SBAR120"): 1001}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
@@ -148,6 +151,8 @@ def workloads(n, scheme, mode="sweep2d"):
         return [synth.free_dendrite_3d(n, scheme=scheme)]
     if mode == "poly2d":
         return [w for w in synth.polycrystal_batch_2d(64)]
+    if mode == "directional2d":
+        return [synth.directional_2d(n, 2 * n, float(t), scheme, Vp=DS_VP, lT=DS_LT, steps=20000) for t in DS_THETAS]
     return [synth.free_dendrite_2d(n, float(t), scheme, steps=20000) for t in THETAS]
 
 
@@ -155,6 +160,8 @@ WORKLOAD_TEXT = {
     "sweep2d": "orientation sweep 2D, 10 x {n}^2 instances (alpha0 = 0..45 deg), {scheme}",
     "dendrite3d": "3D free dendrite {n}^3, random ZXZ orientation, {scheme}",
     "poly2d": "batched 2D polycrystal, 64 instances 256^2..1536^2, 3-12 grains each, {scheme}",
+    "directional2d": "directional solidification 2D, 5 x {n}x{n2} instances (alpha0 = 0..40 deg), frozen gradient "
+                     "Vp = 0.1 W/tau0, lT = 2000 W, periodic x, {scheme}",
 }
 
 
@@ -362,6 +369,18 @@ def run_native(args):
         sweep["at_step"] = sims[0].steps_done
         sweep["tip_radius_call_ms_p50"] = statistics.median(tr_s) * 1e3
 
+    # directional solidification: most advanced tip of each misorientation relative to
+    # the isotherm T0 and the distance to the well-oriented grain's tip (Sec. 4.2)
+    if args.workload == "directional2d" and rank == 0:
+        tips = []
+        for s in sims:
+            ob = s.observe(0)
+            tips.append(ob["tip"][1] if ob["found"] else float("nan"))
+        t_now = sims[0].steps_done * ws[0].dt
+        sweep = {"theta_deg": list(DS_THETAS), "tip_y": [round(v, 4) for v in tips],
+                 "isotherm_y": round(ws[0].yT + DS_VP * t_now, 4),
+                 "delta": [round(tips[0] - v, 4) for v in tips], "at_step": sims[0].steps_done}
+
     # roofline of the fused step kernel: algorithmic bytes per launch / mean launch time
     peak, peak_kind = peaks()
     bpc = B_PER_CELL[args.precision]
@@ -411,7 +430,7 @@ def run_native(args):
         line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-                "config": {"workload": WORKLOAD_TEXT[args.workload].format(n=args.n, scheme=args.scheme) +
+                "config": {"workload": WORKLOAD_TEXT[args.workload].format(n=args.n, n2=2 * args.n, scheme=args.scheme) +
                                        f", FP32 fields, batched persistent launch + CUDA graph, observe every "
                                        f"{OBS_EVERY} steps",
                            "cells_per_gpu": cells, "l2": f"state {cells * 16 / 1e6:.0f} MB per step > 129 MB L2"},
@@ -422,7 +441,7 @@ def run_native(args):
                 "tile": list(tile) if tile else None,
                 "gpu_launches": n_launch + 2 * len(sims) * (args.steps // OBS_EVERY)}
         if sweep:
-            line["orientation_sweep"] = sweep
+            line["directional" if args.workload == "directional2d" else "orientation_sweep"] = sweep
         if world == 1 and not args.no_fp64:
             line["fp64_plain"] = fp64_plain(stream)
         if world == 1 and not args.no_cpu and args.workload == "sweep2d":
@@ -443,7 +462,7 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--scheme", default="SBAR21", choices=["SBAR21", "S21", "S10", "SBAR120", "S100"])
     ap.add_argument("--n", type=int, default=None, help="grid side (default 1024 in 2D, 256 in 3D)")
-    ap.add_argument("--workload", default="sweep2d", choices=["sweep2d", "dendrite3d", "poly2d", "serve"])
+    ap.add_argument("--workload", default="sweep2d", choices=["sweep2d", "dendrite3d", "poly2d", "directional2d", "serve"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
     ap.add_argument("--window", type=float, default=20.0, help="serve: arrival window in seconds")
     ap.add_argument("--serve-scale", type=float, default=0.25, help="serve: scale of sides and step counts")

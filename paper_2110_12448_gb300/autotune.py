@@ -51,7 +51,8 @@ def wave_aligned(workloads, bx, by, resident, max_waves=8, min_sweep=8):
 
 
 def _key(device_name, w, precision, count):
-    return f"{device_name}|{w.dim}|{w.scheme}|{precision}|{w.nx}x{w.ny}x{w.nz}|n{count}"
+    ds = "|ds" if getattr(w, "thermal", 0) or getattr(w, "bc_x", 0) else ""  # the directional kernel variant
+    return f"{device_name}|{w.dim}|{w.scheme}|{precision}|{w.nx}x{w.ny}x{w.nz}|n{count}{ds}"
 
 
 def _load():
