@@ -251,12 +251,19 @@ template <> struct Vec2<double> { using t = double2; };
 __device__ __forceinline__ int col_idx(int c, int nx, bool per) {
     return per ? ((c % nx) + nx) % nx : mirror_idx(c, nx);
 }
+// One periodic period applied to a strip column (c in [-2, nx + 62)): the
+// wrapped pair stays contiguous, so it keeps the vector load; columns still
+// outside [0, nx) (grids narrower than a strip) take the scalar path.
+__device__ __forceinline__ int wrap_once(int c, int nx, bool per) {
+    return !per ? c : (c < 0 ? c + nx : (c >= nx ? c - nx : c));
+}
 
 // Load the pair (c, c+1) of a row; c is even.  Vector load when both columns
 // are inside and the row is 2-element aligned, wrapped or mirrored scalar
 // loads otherwise.
 template <typename T>
 __device__ __forceinline__ void load_pair(const T* __restrict__ row, int c, int nx, bool vec, bool per, T& a, T& b) {
+    c = wrap_once(c, nx, per);
     if (vec && c >= 0 && c + 1 < nx) {
         const typename Vec2<T>::t v = __ldg(reinterpret_cast<const typename Vec2<T>::t*>(row + c));
         a = v.x;
@@ -268,6 +275,7 @@ __device__ __forceinline__ void load_pair(const T* __restrict__ row, int c, int 
 }
 __device__ __forceinline__ void load_grain_pair(const int16_t* __restrict__ row, int c, int nx, bool vec, bool per,
                                                 int& a, int& b) {
+    c = wrap_once(c, nx, per);
     if (vec && c >= 0 && c + 1 < nx) {
         const int v = __ldg(reinterpret_cast<const int*>(row + c));
         a = (int)(int16_t)(v & 0xffff);
@@ -334,10 +342,10 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         const T isq2dt = cst[C_ISQ2DT];
         const bool vec = (nx & 1) == 0;
         const bool per = DS && rec.bcx != 0;
-        // frozen temperature: zeta at row p = zeta_y0 + (p - y0) zA (Eqs. Thermal_F1/_F2)
-        const bool thermal = DS && rec.thermal != 0;
+        // frozen temperature: zeta at row p = zeta_y0 + (p - y0) zA (Eqs. Thermal_F1/_F2);
+        // the DS variant applies it branch-free (zA = zB = zC = 0 gives zeta = 0, F1 = 1)
         T zeta_y0 = T(0), zA = T(0);
-        if (thermal) {
+        if (DS) {
             const long long n = clk.clock ? clk.base[wi.inst] + *clk.clock : clk.step;
             zeta_y0 = (T)((double)wi.y0 * rec.zA - rec.zB - (double)n * rec.zC);
             zA = (T)rec.zA;
@@ -472,14 +480,14 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             const V<T> ph = ph0.C();
             V<T> u = u0.C();  // F2 of Eq. PF_a
             T iF1 = T(1);     // 1 / F1
-            if (thermal) {
+            if (DS) {
                 const T z = zeta_y0 + T(p - y0) * zA;
                 u = u + bc<T>(z);
                 iF1 = M<T>::rcp(T(1) - omk * z);
             }
             const V<T> src = bc<T>(SQ2) * (ph - bc<T>(lam) * (bc<T>(T(1)) - ph * ph) * u);
             V<T> rate = (L + N + src) * rcp2(ac * ac) - bc<T>(SQ2) * ph * G;
-            if (thermal) rate = rate * bc<T>(iF1);
+            if (DS) rate = rate * bc<T>(iF1);
             psin = fma(bc<T>(dt), rate, C0);
             phin = mk(M<T>::tanh_isq2(psin.x()), M<T>::tanh_isq2(psin.y()));
             dph = phin - ph;
