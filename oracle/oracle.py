@@ -22,6 +22,7 @@ _lock = threading.Lock()
 _lib = None
 
 S10, S21, SBAR21, S100, SBAR120 = 0, 1, 2, 3, 4
+T1, T0 = 0, 1
 BC_MIRROR, BC_PERIODIC, BC_PERIODIC_X = 0, 1, 2
 
 OPS = {
@@ -39,7 +40,7 @@ class Params(C.Structure):
                 ("scheme", C.c_int), ("bc", C.c_int),
                 ("h", C.c_double), ("dt", C.c_double), ("k", C.c_double), ("eps4", C.c_double),
                 ("lam", C.c_double), ("D", C.c_double),
-                ("thermal", C.c_int), ("pad", C.c_int),
+                ("thermal", C.c_int), ("time_level", C.c_int),
                 ("Vp", C.c_double), ("lT", C.c_double), ("yT", C.c_double), ("t0", C.c_double)]
 
 
@@ -89,13 +90,14 @@ def _i16(a):
 
 
 def params(dim=2, nx=16, ny=16, nz=1, scheme=SBAR21, bc=BC_MIRROR, h=0.8, dt=0.02, k=0.15, eps4=0.02,
-           lam=10.0, D=None, thermal=0, Vp=0.0, lT=1.0, yT=0.0, t0=0.0) -> Params:
+           lam=10.0, D=None, thermal=0, Vp=0.0, lT=1.0, yT=0.0, t0=0.0, time_level=0) -> Params:
     """Oracle parameters; thermal=1 selects the frozen temperature along +y
-    (zeta = (y - yT - Vp t) / lT, t = t0 + step * dt)."""
+    (zeta = (y - yT - Vp t) / lT, t = t0 + step * dt); time_level=1 selects
+    T0 (pure forward Euler of Eq. PF_b) instead of T1."""
     if D is None:
         D = 0.6267 * lam
-    return Params(dim, nx, ny, nz if dim == 3 else 1, scheme, bc, h, dt, k, eps4, lam, D, int(thermal), 0,
-                  Vp, lT, yT, t0)
+    return Params(dim, nx, ny, nz if dim == 3 else 1, scheme, bc, h, dt, k, eps4, lam, D, int(thermal),
+                  int(time_level), Vp, lT, yT, t0)
 
 
 def _shape(p: Params):

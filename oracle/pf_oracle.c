@@ -67,9 +67,16 @@ typedef struct {
     int dim, nx, ny, nz;
     int scheme, bc;
     double h, dt, k, eps4, lambda, D;
-    int thermal, pad;
+    int thermal, time_level;
     double Vp, lT, yT, t0;
 } or_params;
+
+/* time_level 0 = T1 (default): U' uses phi' and delta phi = phi' - phi;
+ * time_level 1 = T0: pure forward Euler of Eq. PF_b as printed, d phi/dt =
+ * (1 - phi^2) / sqrt2 d psi/dt (chain rule) in the source and the
+ * anti-trapping term, phi^n on the left-hand side. */
+#define OR_T1 0
+#define OR_T0 1
 
 static const double SQ2 = 1.41421356237309504880;
 static const double SQ3 = 1.73205080756887729353;
@@ -611,6 +618,7 @@ static int check_params(const or_params* q) {
     if (q->dim == 3 && q->scheme != OR_S100 && q->scheme != OR_SBAR120) return -1;
     if (!(q->h > 0) || !(q->dt > 0)) return -1;
     if (q->thermal && (q->dim != 2 || !(q->lT > 0))) return -1;
+    if (q->time_level != OR_T1 && q->time_level != OR_T0) return -1;
     return 0;
 }
 
@@ -656,12 +664,23 @@ int or_step(const or_params* q, int n_grains, const double* rot, const int16_t* 
                     dpsi[c] = r;
                     psin[c] = psi[c] + dt * r;
                 }
-        /* pass 3: phi', delta phi with ghosts from psi' */
-        pad_fill(&Pnew, psin, q->bc);
-        for (size_t c = 0; c < padN; ++c) {
-            double phn = tanh(Pnew.v[c] / SQ2);
-            Pdphi.v[c] = phn - Pphi.v[c];
-            Pnew.v[c] = phn; /* Pnew now holds phi' */
+        /* pass 3: phi', delta phi with ghosts from psi' (T1), or the chain-rule
+         * increment dt (1 - phi^2)/sqrt2 dpsi/dt with ghosts from dpsi/dt and
+         * phi^n in place of phi' (T0) */
+        if (q->time_level == OR_T0) {
+            pad_fill(&Pnew, dpsi, q->bc);
+            for (size_t c = 0; c < padN; ++c) {
+                double ph = Pphi.v[c];
+                Pdphi.v[c] = dt * (1.0 - ph * ph) / SQ2 * Pnew.v[c];
+                Pnew.v[c] = ph; /* phi^n on the left-hand side */
+            }
+        } else {
+            pad_fill(&Pnew, psin, q->bc);
+            for (size_t c = 0; c < padN; ++c) {
+                double phn = tanh(Pnew.v[c] / SQ2);
+                Pdphi.v[c] = phn - Pphi.v[c];
+                Pnew.v[c] = phn; /* Pnew now holds phi' */
+            }
         }
         /* alpha of the U equation: 1 - phi (D term) in Pomp, and
          * (1 + (1-k) U) d phi/dt / sqrt 2 (anti-trapping) in Palpha */

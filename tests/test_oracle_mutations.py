@@ -3,7 +3,7 @@
 Each case plants one mistake in a temporary copy of oracle/pf_oracle.c
 (never in the committed file), builds it, and runs the pin suites
 (test_oracle_symbols.py, test_oracle_step.py, test_oracle_tip_radius.py,
-test_oracle_directional.py) against that build through the ORACLE_LIB override: at least one pin must
+test_oracle_directional.py, test_oracle_time_level.py) against that build through the ORACLE_LIB override: at least one pin must
 fail."""
 import os
 import subprocess
@@ -74,6 +74,12 @@ MUTATIONS = [
      "double zeta = ((j + 1) * h - q->yT - q->Vp * t) / q->lT;"),
     ("thermal_clock_frozen", "dpsi_dt_2d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, q->t0 + (double)s * dt)",
      "dpsi_dt_2d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, q->t0)"),
+    ("t0_chain_rule_factor", "Pdphi.v[c] = dt * (1.0 - ph * ph) / SQ2 * Pnew.v[c];",
+     "Pdphi.v[c] = dt * (1.0 - ph * ph) * Pnew.v[c];"),
+    ("t0_without_1_minus_phi2", "Pdphi.v[c] = dt * (1.0 - ph * ph) / SQ2 * Pnew.v[c];",
+     "Pdphi.v[c] = dt / SQ2 * Pnew.v[c];"),
+    ("t0_uses_new_phi", "                Pnew.v[c] = ph; /* phi^n on the left-hand side */",
+     "                Pnew.v[c] = tanh((Ppsi.v[c] + dt * Pnew.v[c]) / SQ2);"),
     ("periodic_x_as_mirror", "if (bc == OR_BC_PERIODIC_X) return axis == 0 ? OR_BC_PERIODIC : OR_BC_MIRROR;",
      "if (bc == OR_BC_PERIODIC_X) return OR_BC_MIRROR;"),
 ]
@@ -99,6 +105,7 @@ def test_pins_catch_mutation(source, name, old, new):
                             os.path.join(ROOT, "tests", "test_oracle_symbols.py"),
                             os.path.join(ROOT, "tests", "test_oracle_step.py"),
                             os.path.join(ROOT, "tests", "test_oracle_tip_radius.py"),
-                            os.path.join(ROOT, "tests", "test_oracle_directional.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_directional.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_time_level.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"mutation {name} survived every pin:\n{r.stdout[-2000:]}"
