@@ -66,6 +66,14 @@ enum {
 enum { PF_BC_MIRROR = 0, PF_BC_PERIODIC = 1 };
 /* Thermal condition (Sec. 2.1). */
 enum { PF_ISOTHERMAL = 0, PF_FROZEN_GRADIENT = 1 };
+/* Time levels of the U update (Sec. 3.3.1 leaves them open):
+ * PF_T1: U' = U + [dt (D~ D + A) + (1+(1-k)U) dphi] / (1+k-(1-k)phi'),
+ *        dphi = phi' - phi, anti-trapping alpha from dphi / dt (conserves the
+ *        solute exactly with mirror walls);
+ * PF_T0: pure forward Euler of Eq. PF_b as printed: dphi replaced by
+ *        dt (1-phi^2)/sqrt2 dpsi/dt (chain rule), phi^n instead of phi'
+ *        (conserves the solute to O(dt) over a fixed time). */
+enum { PF_T1 = 0, PF_T0 = 1 };
 
 /* Problem statement (Sec. 2.1): grid, lattice spacing h (units of W), time
  * step dt (units of tau0), partition coefficient k, anisotropy strength
@@ -97,6 +105,8 @@ typedef struct {
     int32_t bc_x;       /* PF_BC_MIRROR or PF_BC_PERIODIC (2D) */
     int32_t thermal;    /* PF_ISOTHERMAL or PF_FROZEN_GRADIENT (2D) */
     double Vp, lT, yT;  /* frozen gradient: pulling speed, thermal length, isotherm T0 at t = 0 */
+    int32_t time_level; /* PF_T1 (default) or PF_T0 */
+    int32_t reserved;   /* 0 */
 } pf_params;
 
 /* A spherical (circular in 2D) seed: centre (x, y, z) and radius r in units

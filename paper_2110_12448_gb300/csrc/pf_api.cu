@@ -48,6 +48,7 @@ bool valid_params(const pf_params* p) {
     if (p->bc_x != PF_BC_MIRROR && p->bc_x != PF_BC_PERIODIC) return false;
     if (p->bc_x == PF_BC_PERIODIC && p->dim != 2) return false;
     if (p->thermal != PF_ISOTHERMAL && p->thermal != PF_FROZEN_GRADIENT) return false;
+    if (p->time_level != PF_T1 && p->time_level != PF_T0) return false;
     double F1min = 1.0;
     if (p->thermal == PF_FROZEN_GRADIENT) {
         if (p->dim != 2 || !(p->lT > 0) || !std::isfinite(p->lT) || !(p->Vp >= 0) || !std::isfinite(p->Vp) ||
@@ -176,8 +177,10 @@ void build_work(const pf_sim* s, int inst, std::vector<WorkItem>& out) {
     }
 }
 
-// the 2D kernel variant with frozen temperature / periodic x
-bool ds_of(const pf_params& p) { return p.thermal == PF_FROZEN_GRADIENT || p.bc_x == PF_BC_PERIODIC; }
+// the 2D kernel variant with frozen temperature / periodic x / T0 time level
+bool ds_of(const pf_params& p) {
+    return p.thermal == PF_FROZEN_GRADIENT || p.bc_x == PF_BC_PERIODIC || p.time_level == PF_T0;
+}
 
 int occupancy(const pf_sim* s) {
     const int prec = s->p.precision == PF_F64 ? 1 : 0;
@@ -199,6 +202,7 @@ InstRec make_rec(const pf_sim* s, int parity_offset) {
     r.parity_offset = parity_offset;
     r.thermal = s->p.thermal == PF_FROZEN_GRADIENT ? 1 : 0;
     r.bcx = s->p.bc_x == PF_BC_PERIODIC ? 1 : 0;
+    r.tlevel = s->p.time_level == PF_T0 ? 1 : 0;
     if (r.thermal) {
         r.zA = s->p.h / s->p.lT;
         r.zB = s->p.yT / s->p.lT;

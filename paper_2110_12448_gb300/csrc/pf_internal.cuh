@@ -42,6 +42,8 @@ struct InstRec {
     int32_t nx, ny, nz, parity_offset;
     int32_t thermal;  // 1: frozen temperature along +y (2D)
     int32_t bcx;      // 1: periodic x (2D)
+    int32_t tlevel;   // 1: T0 time level (pure forward Euler of Eq. PF_b)
+    int32_t pad_;
     double h, dt, k, eps4, lambda, D;
     // frozen temperature: zeta(row j, step n) = j zA - zB - n zC
     // (zA = h / lT, zB = yT / lT, zC = Vp dt / lT)

@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         const T isq2dt = cst[C_ISQ2DT];
         const bool vec = (nx & 1) == 0;
         const bool per = DS && rec.bcx != 0;
+        const bool t0 = DS && rec.tlevel != 0;  // T0 time level
         // frozen temperature: zeta at row p = zeta_y0 + (p - y0) zA (Eqs. Thermal_F1/_F2);
         // the DS variant applies it branch-free (zA = zB = zC = 0 gives zeta = 0, F1 = 1)
         T zeta_y0 = T(0), zA = T(0);
@@ -491,6 +492,12 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             psin = fma(bc<T>(dt), rate, C0);
             phin = mk(M<T>::tanh_isq2(psin.x()), M<T>::tanh_isq2(psin.y()));
             dph = phin - ph;
+            if (DS) {
+                // T0: chain-rule increment dt (1 - phi^2)/sqrt2 dpsi/dt and phi^n on the left-hand side
+                const V<T> d0 = bc<T>(dt * T(0.70710678118654752440)) * (bc<T>(T(1)) - ph * ph) * rate;
+                dph = mk(t0 ? d0.x() : dph.x(), t0 ? d0.y() : dph.y());
+                phin = mk(t0 ? ph.x() : phin.x(), t0 ? ph.y() : phin.y());
+            }
         };
 
         // phase-2 carries: fluxes of row q-1 that row q uses (subtracted)

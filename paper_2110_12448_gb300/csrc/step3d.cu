@@ -141,6 +141,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
         const T ih2 = cst[C_IH2];
         const T isq2dt = cst[C_ISQ2DT];
         const int x0 = wi.x0, y0 = wi.y0, z0 = wi.z0;
+        const bool t0 = rec.tlevel != 0;  // T0 time level
         const int z1 = min(z0 + wi.ext, nz);
 
         // this thread's ring-region cell and the cell it computes in phase 1
@@ -266,11 +267,12 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             const T rate = (L + N + SQ2 * (ph - lam * (T(1) - ph * ph) * u)) * M3<T>::rcp(ac * ac) - SQ2 * ph * G;
             psin = pc + dt * rate;
             const T phn = M3<T>::tanh_(psin * ISQ2);
-            const T dph = phn - ph;
+            // T1: delta phi = phi' - phi; T0: chain-rule increment, phi^n on the left-hand side
+            const T dph = t0 ? dt * (T(1) - ph * ph) * ISQ2 * rate : phn - ph;
             RG(s_dphi, 4, p, ty, tx) = dph;
             RG(s_aD, 4, p, ty, tx) = T(1) - ph;
             RG(s_aA, 4, p, ty, tx) = (T(1) + omk * u) * dph * isq2dt;
-            return phn;
+            return t0 ? ph : phn;
         };
         // ghost plane vz takes the slot values of plane mz
         auto copy_plane = [&](int vz, int mz) {

@@ -39,11 +39,13 @@ class Params(C.Structure):
                 ("lam", C.c_double), ("D", C.c_double), ("U0", C.c_double),
                 ("scheme", C.c_int32), ("precision", C.c_int32), ("max_grains", C.c_int32),
                 ("max_seeds", C.c_int32), ("bc_x", C.c_int32), ("thermal", C.c_int32),
-                ("Vp", C.c_double), ("lT", C.c_double), ("yT", C.c_double)]
+                ("Vp", C.c_double), ("lT", C.c_double), ("yT", C.c_double),
+                ("time_level", C.c_int32), ("reserved", C.c_int32)]
 
 
 PF_BC_MIRROR, PF_BC_PERIODIC = 0, 1
 PF_ISOTHERMAL, PF_FROZEN_GRADIENT = 0, 1
+PF_T1, PF_T0 = 0, 1
 
 
 class Seed(C.Structure):
@@ -130,13 +132,13 @@ def _check(rc: int, what: str):
 
 def make_params(dim, nx, ny, nz=1, h=0.8, dt=0.02, k=0.15, eps4=0.02, lam=10.0, D=None, U0=-0.55,
                 scheme="SBAR21", precision="f32", max_grains=1, max_seeds=0, bc_x=PF_BC_MIRROR,
-                thermal=PF_ISOTHERMAL, Vp=0.0, lT=1.0, yT=0.0) -> Params:
+                thermal=PF_ISOTHERMAL, Vp=0.0, lT=1.0, yT=0.0, time_level=PF_T1) -> Params:
     if D is None:
         D = 0.6267 * lam
     return Params(int(dim), int(nx), int(ny), int(nz if dim == 3 else 1), float(h), float(dt), float(k), float(eps4),
                   float(lam), float(D), float(U0), SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
                   PRECISIONS[precision] if isinstance(precision, str) else int(precision), int(max_grains),
-                  int(max_seeds), int(bc_x), int(thermal), float(Vp), float(lT), float(yT))
+                  int(max_seeds), int(bc_x), int(thermal), float(Vp), float(lT), float(yT), int(time_level), 0)
 
 
 def required_bytes(p: Params) -> int:
@@ -175,7 +177,7 @@ class Sim:
         p = make_params(w.dim, w.nx, w.ny, w.nz, w.h, w.dt, w.k, w.eps4, w.lam, w.D, w.U0, scheme or w.scheme,
                         precision, max_grains=max(1, w.n_grains), max_seeds=max(1, len(w.seeds)),
                         bc_x=getattr(w, "bc_x", 0), thermal=getattr(w, "thermal", 0), Vp=getattr(w, "Vp", 0.0),
-                        lT=getattr(w, "lT", 1.0), yT=getattr(w, "yT", 0.0))
+                        lT=getattr(w, "lT", 1.0), yT=getattr(w, "yT", 0.0), time_level=getattr(w, "time_level", 0))
         s = cls(p, stream=stream)
         s.set_grains(w.rots, w.centres)
         if init:
