@@ -53,10 +53,10 @@ def dist_env():
 TRAFFIC = {
     # profiles/k_step2d_sbar21_f32_orientation_sweep_10x1024sq.md
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
-                "sha256": "e85d6dedd34223d3c74913e45dac409503649da64cf449032f7bad6161f5ef8a", "bytes": 155041024},
+                "sha256": "9854506c6ca4a8a58d75ec80f866bf6ed480ba5f78525c2ca32329f5e4693873", "bytes": 154593536},
     # profiles/k_step3d_sbar120_f32_dendrite_256cube.md
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
-                   "sha256": "69f72bf81f30839c68f5021cea106e0e603e5d414f51d8652ad56d2adbbc1096", "bytes": 263041024},
+                   "sha256": "19935abcc464729f045d148f0c9d5df216a7ec0229da75f2c0ddb505b2daa1b0", "bytes": 262713856},
 }
 
 
