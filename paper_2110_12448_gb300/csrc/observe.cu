@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(OBS_THREADS) k_observe_finish(const ObsPartial
 // multilinearly between cell centres and the first sample with psi >= 0 gives
 // the crossing by linear interpolation.  Fit: c = sum t s^2 / sum s^4 over the
 // crossings with t <= w, rho = 1 / (2c); w = 40 h, then the previous rho; four
-// rounds.  Thread l of each 64-thread half marches line l; one thread per half
-// fits in line order.  All FP64 operations are explicitly rounded (no
-// contraction), so the crossings are reproducible.
+// rounds.  One warp per line (its lanes take 32 samples at a time), then one
+// thread per transverse axis fits in line order.  All FP64 operations are
+// explicitly rounded (no contraction), so the crossings are reproducible.
 constexpr int TIP_J = 32, TIP_M = 160, TIP_ROUNDS = 4;
 
 template <typename T>
@@ -175,71 +175,94 @@ __device__ double tip_interp(const TipArgs& a, const T* __restrict__ psi, const 
     return __dadd_rn(__dmul_rn(__dsub_rn(1.0, f[2]), v0), __dmul_rn(f[2], plane(1)));
 }
 
-template <typename T> __global__ void __launch_bounds__(TIP_THREADS) k_tip_radius(TipArgs a, double* __restrict__ out) {
-    __shared__ double ts[2][2 * TIP_J];
-    __shared__ double frame[3][3];  // e_par, e_x, e_z
-    const T* __restrict__ psi = static_cast<const T*>(a.psi);
-    if (threadIdx.x == 0) {
-        double ep[3] = {a.axis[0], a.axis[1], a.dim == 3 ? a.axis[2] : 0.0};
-        const double na =
-            __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ep[0], ep[0]), __dmul_rn(ep[1], ep[1])), __dmul_rn(ep[2], ep[2])));
-        for (int q = 0; q < 3; ++q) ep[q] = __ddiv_rn(ep[q], na);
-        double ex[3], ez[3] = {0.0, 0.0, 0.0};
-        if (a.dim == 2) {
-            ex[0] = ep[1];
-            ex[1] = -ep[0];
-            ex[2] = 0.0;
-        } else {
-            double ref[3] = {0.0, 0.0, 1.0};
-            if (fabs(ep[2]) > 1.0 - 1e-6) {
-                ref[0] = 1.0;
-                ref[2] = 0.0;
-            }
-            const double pr =
-                __dadd_rn(__dadd_rn(__dmul_rn(ref[0], ep[0]), __dmul_rn(ref[1], ep[1])), __dmul_rn(ref[2], ep[2]));
-            for (int q = 0; q < 3; ++q) ez[q] = __dsub_rn(ref[q], __dmul_rn(pr, ep[q]));
-            const double nz = __dsqrt_rn(
-                __dadd_rn(__dadd_rn(__dmul_rn(ez[0], ez[0]), __dmul_rn(ez[1], ez[1])), __dmul_rn(ez[2], ez[2])));
-            for (int q = 0; q < 3; ++q) ez[q] = __ddiv_rn(ez[q], nz);
-            ex[0] = __dsub_rn(__dmul_rn(ez[1], ep[2]), __dmul_rn(ez[2], ep[1]));
-            ex[1] = __dsub_rn(__dmul_rn(ez[2], ep[0]), __dmul_rn(ez[0], ep[2]));
-            ex[2] = __dsub_rn(__dmul_rn(ez[0], ep[1]), __dmul_rn(ez[1], ep[0]));
+// growth axis e_par and transverse axes e_x, e_z of the fit (explicitly rounded)
+__device__ void tip_frame(const TipArgs& a, double frame[3][3]) {
+    double ep[3] = {a.axis[0], a.axis[1], a.dim == 3 ? a.axis[2] : 0.0};
+    const double na =
+        __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ep[0], ep[0]), __dmul_rn(ep[1], ep[1])), __dmul_rn(ep[2], ep[2])));
+    for (int q = 0; q < 3; ++q) ep[q] = __ddiv_rn(ep[q], na);
+    double ex[3], ez[3] = {0.0, 0.0, 0.0};
+    if (a.dim == 2) {
+        ex[0] = ep[1];
+        ex[1] = -ep[0];
+        ex[2] = 0.0;
+    } else {
+        double ref[3] = {0.0, 0.0, 1.0};
+        if (fabs(ep[2]) > 1.0 - 1e-6) {
+            ref[0] = 1.0;
+            ref[2] = 0.0;
         }
-        for (int q = 0; q < 3; ++q) {
-            frame[0][q] = ep[q];
-            frame[1][q] = ex[q];
-            frame[2][q] = ez[q];
-        }
+        const double pr =
+            __dadd_rn(__dadd_rn(__dmul_rn(ref[0], ep[0]), __dmul_rn(ref[1], ep[1])), __dmul_rn(ref[2], ep[2]));
+        for (int q = 0; q < 3; ++q) ez[q] = __dsub_rn(ref[q], __dmul_rn(pr, ep[q]));
+        const double nz =
+            __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ez[0], ez[0]), __dmul_rn(ez[1], ez[1])), __dmul_rn(ez[2], ez[2])));
+        for (int q = 0; q < 3; ++q) ez[q] = __ddiv_rn(ez[q], nz);
+        ex[0] = __dsub_rn(__dmul_rn(ez[1], ep[2]), __dmul_rn(ez[2], ep[1]));
+        ex[1] = __dsub_rn(__dmul_rn(ez[2], ep[0]), __dmul_rn(ez[0], ep[2]));
+        ex[2] = __dsub_rn(__dmul_rn(ez[0], ep[1]), __dmul_rn(ez[1], ep[0]));
     }
+    for (int q = 0; q < 3; ++q) {
+        frame[0][q] = ep[q];
+        frame[1][q] = ex[q];
+        frame[2][q] = ez[q];
+    }
+}
+
+// One warp per contour line (64 per transverse axis); the lanes evaluate 32
+// consecutive samples at once and the first sample that is outside the grid
+// or has psi >= 0 ends the line, as in a sequential march.  t[line] = the
+// crossing or NaN.
+template <typename T> __global__ void __launch_bounds__(TIP_THREADS) k_tip_lines(TipArgs a, double* __restrict__ t) {
+    __shared__ double frame[3][3];
+    if (threadIdx.x == 0) tip_frame(a, frame);
     __syncthreads();
-    const int l = threadIdx.x & 63, half = threadIdx.x >> 6;  // half 0: e_x lines, 1: e_z lines
-    const bool active = half == 0 || a.dim == 3;
+    const T* __restrict__ psi = static_cast<const T*>(a.psi);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (TIP_THREADS / 32) + (threadIdx.x >> 5);
+    const int half = gw / (2 * TIP_J), l = gw % (2 * TIP_J);  // half 0: e_x lines, 1: e_z lines
+    if (half >= (a.dim == 3 ? 2 : 1)) return;                 // whole warps only
+    const double* e = frame[1 + half];
+    const int j = l < TIP_J ? l - TIP_J : l - TIP_J + 1;
+    const double s = __dmul_rn((double)j, a.h);
     const double dt = __dmul_rn(a.h, 0.25);
-    if (active) {
-        const double* e = frame[1 + half];
-        const int j = l < TIP_J ? l - TIP_J : l - TIP_J + 1;
-        const double s = __dmul_rn((double)j, a.h);
-        double base[3];
-        for (int q = 0; q < 3; ++q) base[q] = __dadd_rn(a.tip[q], __dmul_rn(s, e[q]));
-        double tc = CUDART_NAN, prev = 0.0;
-        for (int m = 0; m <= TIP_M; ++m) {
+    double base[3];
+    for (int q = 0; q < 3; ++q) base[q] = __dadd_rn(a.tip[q], __dmul_rn(s, e[q]));
+    double tc = CUDART_NAN, carry = 0.0;
+    for (int m0 = 0; m0 <= TIP_M; m0 += 32) {
+        const int m = m0 + lane;
+        double v = 0.0;
+        bool inside = false;
+        if (m <= TIP_M) {
             const double tm = __dmul_rn((double)m, dt);
             double r[3];
             for (int q = 0; q < 3; ++q) r[q] = __dsub_rn(base[q], __dmul_rn(tm, frame[0][q]));
-            bool inside;
-            const double v = tip_interp<T>(a, psi, r, inside);
-            if (!inside) break;
-            if (v >= 0.0) {
-                if (m >= 1)
-                    tc = __dadd_rn(__dmul_rn((double)(m - 1), dt), __dmul_rn(dt, __ddiv_rn(prev, __dsub_rn(prev, v))));
-                break;
-            }
-            prev = v;
+            v = tip_interp<T>(a, psi, r, inside);
         }
-        ts[half][l] = tc;
+        const bool ev = m <= TIP_M && (!inside || v >= 0.0);
+        const unsigned b = __ballot_sync(FULL, ev);
+        const double vup = __shfl_up_sync(FULL, v, 1);
+        const double prev = lane == 0 ? carry : vup;  // psi at sample m - 1
+        if (b) {
+            const int f = __ffs(b) - 1;
+            double tl = CUDART_NAN;
+            if (lane == f && inside && v >= 0.0 && m >= 1)
+                tl = __dadd_rn(__dmul_rn((double)(m - 1), dt), __dmul_rn(dt, __ddiv_rn(prev, __dsub_rn(prev, v))));
+            tc = __shfl_sync(FULL, tl, f);
+            break;
+        }
+        carry = __shfl_sync(FULL, v, 31);
     }
-    __syncthreads();
-    if (active && l == 0) {
+    if (lane == 0) t[half * 2 * TIP_J + l] = tc;
+}
+
+// Parabola fits of the crossings in line order (one thread per transverse
+// axis), then rho (3D: 2 / (1/rho_x + 1/rho_z)).
+__global__ void k_tip_fit(TipArgs a, const double* __restrict__ t, double* __restrict__ out) {
+    const int half = threadIdx.x;
+    const double dt = __dmul_rn(a.h, 0.25);
+    if (half < (a.dim == 3 ? 2 : 1)) {
         double w = __dmul_rn((double)TIP_M, dt), rho = CUDART_NAN;
         int used = 0;
         for (int round = 0; round < TIP_ROUNDS; ++round) {
@@ -248,10 +271,10 @@ template <typename T> __global__ void __launch_bounds__(TIP_THREADS) k_tip_radiu
             for (int k = 0; k < 2 * TIP_J; ++k) {
                 const int j = k < TIP_J ? k - TIP_J : k - TIP_J + 1;
                 const double s = __dmul_rn((double)j, a.h);
-                const double t = ts[half][k];
-                if (!(t <= w)) continue;
+                const double tk = t[half * 2 * TIP_J + k];
+                if (!(tk <= w)) continue;
                 const double s2 = __dmul_rn(s, s);
-                st = __dadd_rn(st, __dmul_rn(t, s2));
+                st = __dadd_rn(st, __dmul_rn(tk, s2));
                 s4 = __dadd_rn(s4, __dmul_rn(s2, s2));
                 ++n;
             }
@@ -355,10 +378,13 @@ cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* r
 }
 
 cudaError_t launch_tip_radius(const TipArgs& a, double* out, cudaStream_t st) {
+    double* t = out + 8;  // 2 x 64 crossings after the five results
+    const int blocks = (a.dim == 3 ? 2 : 1) * 2 * TIP_J / (TIP_THREADS / 32);
     if (a.prec == 0)
-        k_tip_radius<float><<<1, TIP_THREADS, 0, st>>>(a, out);
+        k_tip_lines<float><<<blocks, TIP_THREADS, 0, st>>>(a, t);
     else
-        k_tip_radius<double><<<1, TIP_THREADS, 0, st>>>(a, out);
+        k_tip_lines<double><<<blocks, TIP_THREADS, 0, st>>>(a, t);
+    k_tip_fit<<<1, 32, 0, st>>>(a, t, out);
     return cudaGetLastError();
 }
 

@@ -120,14 +120,15 @@ cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* r
 cudaError_t noalloc_scratch(ObsPartial** partials, ObsPartial** result);
 
 // Tip radius (Sec. 3.3.2, Sec. 6.2.2): contour lines and parabola fits on the
-// device.  out[0..4] = rho, rho_x, rho_z, samples in the x fit, in the z fit.
+// device.  out[0..4] = rho, rho_x, rho_z, samples in the x fit, in the z fit;
+// out[8..135] receive the contour crossings.
 struct TipArgs {
     const void* psi;
     int prec, dim, nx, ny, nz;
     double h;
     double tip[3], axis[3];  // tip position and (unnormalised) growth axis
 };
-constexpr int TIP_THREADS = 128;  // 2 x 64 contour lines
+constexpr int TIP_THREADS = 128;  // 4 warps per block, one warp per contour line
 cudaError_t launch_tip_radius(const TipArgs& a, double* out, cudaStream_t st);
 
 struct SeedDev {
