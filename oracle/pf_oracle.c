@@ -587,7 +587,7 @@ static double dpsi_dt_2d(const or_params* q, const pad_t* psi, const pad_t* phi,
 }
 
 static double dpsi_dt_3d(const or_params* q, const pad_t* psi, const pad_t* phi, const pad_t* U, const pad_t* gr,
-                         const double* rot, int i, int j, int k) {
+                         const double* rot, int i, int j, int k, double t) {
     double h = q->h;
     const double* R = rot + 9 * (int)V3(gr, i, j, k);
     double L = is_iso(q->scheme) ? lap_120(psi, i, j, k, h) : lap_100(psi, i, j, k, h);
@@ -608,6 +608,12 @@ static double dpsi_dt_3d(const or_params* q, const pad_t* psi, const pad_t* phi,
         }
     N /= h;
     double ph = F3(phi, 0, 0, 0), u = F3(U, 0, 0, 0);
+    if (q->thermal) {
+        /* Eq. PF_a with the frozen-temperature functions F1, F2 (pulling along +y) */
+        double zeta = (j * h - q->yT - q->Vp * t) / q->lT;
+        double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u + zeta;
+        return ((L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * F2)) / (ac * ac) - SQ2 * ph * G) / F1;
+    }
     return (L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * u)) / (ac * ac) - SQ2 * ph * G;
 }
 
@@ -617,7 +623,7 @@ static int check_params(const or_params* q) {
     if (q->dim == 2 && q->scheme > OR_SBAR21) return -1;
     if (q->dim == 3 && q->scheme != OR_S100 && q->scheme != OR_SBAR120) return -1;
     if (!(q->h > 0) || !(q->dt > 0)) return -1;
-    if (q->thermal && (q->dim != 2 || !(q->lT > 0))) return -1;
+    if (q->thermal && !(q->lT > 0)) return -1;
     if (q->time_level != OR_T1 && q->time_level != OR_T0) return -1;
     return 0;
 }
@@ -660,7 +666,7 @@ int or_step(const or_params* q, int n_grains, const double* rot, const int16_t* 
                 for (int i = 0; i < q->nx; ++i) {
                     size_t c = ((size_t)kk * q->ny + j) * q->nx + i;
                     double r = q->dim == 2 ? dpsi_dt_2d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, q->t0 + (double)s * dt)
-                                           : dpsi_dt_3d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, kk);
+                                           : dpsi_dt_3d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, kk, q->t0 + (double)s * dt);
                     dpsi[c] = r;
                     psin[c] = psi[c] + dt * r;
                 }

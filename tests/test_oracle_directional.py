@@ -110,3 +110,59 @@ def test_pulled_planar_front_tracks_the_isotherm():
     for d in (5.0, 20.0, 50.0):
         jj = int(round((y2 + d) / h))
         assert abs(U[jj, 0] - (-1.0 + math.exp(-Vp * (jj * h - y2) / D))) < 0.01
+
+
+# ---- 3D: the same terms in Eq. PF_a (pulling along +y), periodic x, mirror y and z ----
+
+def rand_state3(rng, nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    psi = 2.0 * np.sin(2 * np.pi * x / nx) + np.cos(2 * np.pi * z / nz) + 0.4 * (ny / 2 - y) + \
+        rng.normal(0, 0.3, (nz, ny, nx))
+    U = -0.5 + 0.2 * rng.random((nz, ny, nx))
+    return psi, U
+
+
+def test_infinite_thermal_length_is_isothermal_3d():
+    rng = np.random.default_rng(11)
+    psi, U = rand_state3(rng, 10, 9, 8)
+    g = np.zeros((8, 9, 10), np.int16)
+    rot = np.eye(3).reshape(1, 9)
+    base = dict(dim=3, nx=10, ny=9, nz=8, scheme=O.SBAR120, dt=0.01, eps4=0.03)
+    a = O.step(O.params(**base), rot, g, psi, U, 2)
+    b = O.step(O.params(thermal=1, Vp=0.0, lT=1e30, yT=3.0, **base), rot, g, psi, U, 2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("scheme", [O.SBAR120, O.S100])
+def test_linear_psi_closed_form_rate_3d(scheme):
+    nx, ny, nz, h = 6, 24, 5, 0.8
+    rng = np.random.default_rng(12)
+    y = (np.arange(ny) * h)[None, :, None] * np.ones((nz, 1, nx))
+    gy = 0.8
+    psi = 1.0 + gy * (y - 9.0)
+    U = -0.6 + 0.3 * rng.random((nz, ny, nx))
+    k, lam, Vp, lT, yT, t0 = 0.15, 10.0, 0.3, 41.0, 7.0, 2.3
+    p = O.params(dim=3, nx=nx, ny=ny, nz=nz, h=h, dt=0.01, scheme=scheme, eps4=0.0, k=k, lam=lam, thermal=1,
+                 Vp=Vp, lT=lT, yT=yT, t0=t0, bc=O.BC_PERIODIC_X)
+    _, _, rate = O.step(p, np.eye(3).reshape(1, 9), np.zeros((nz, ny, nx), np.int16), psi, U, 1, want_rate=True)
+    phi = np.tanh(psi / SQ2)
+    zeta = (y - yT - Vp * t0) / lT
+    expect = (SQ2 * phi * (1.0 - gy * gy) - SQ2 * lam * (1.0 - phi ** 2) * (U + zeta)) / (1.0 - (1.0 - k) * zeta)
+    inner = (slice(None), slice(2, ny - 2), slice(None))
+    assert np.max(np.abs(rate[inner] - expect[inner])) <= 1e-12 * np.max(np.abs(expect[inner])) + 1e-13
+
+
+@pytest.mark.parametrize("scheme", [O.SBAR120, O.S100])
+def test_periodic_x_commutes_with_shifts_3d(scheme):
+    rng = np.random.default_rng(13)
+    nx, ny, nz = 11, 9, 8
+    psi, U = rand_state3(rng, nx, ny, nz)
+    g = (rng.random((nz, ny, nx)) < 0.3).astype(np.int16)
+    c, s_ = math.cos(0.4), math.sin(0.4)
+    rot = np.stack([np.eye(3).ravel(), np.array([[c, -s_, 0], [s_, c, 0], [0, 0, 1]]).ravel()])
+    p = O.params(dim=3, nx=nx, ny=ny, nz=nz, scheme=scheme, dt=0.01, bc=O.BC_PERIODIC_X, eps4=0.04, thermal=1,
+                 Vp=0.3, lT=50.0, yT=2.0)
+    a = O.step(p, rot, g, psi, U, 2)
+    for m in (1, 6):
+        b = O.step(p, rot, np.roll(g, m, 2), np.roll(psi, m, 2), np.roll(U, m, 2), 2)
+        assert np.array_equal(np.roll(a[0], m, 2), b[0]) and np.array_equal(np.roll(a[1], m, 2), b[1])
