@@ -82,7 +82,7 @@ enum { PF_T1 = 0, PF_T0 = 1 };
  * of the grain table (>= 1) and of the seed list used by pf_init_seeds
  * (0 = 64).  Every axis needs at least 4 cells.
  *
- * Thermal condition: PF_ISOTHERMAL (F1 = 1, F2 = U) or, in 2D,
+ * Thermal condition: PF_ISOTHERMAL (F1 = 1, F2 = U) or
  * PF_FROZEN_GRADIENT: directional solidification in a frozen temperature
  * field pulled along +y (Eqs. Thermal_F1, Thermal_F2): with
  * zeta = (y - yT - Vp t) / lT, y = j h and t = step * dt,
@@ -90,7 +90,8 @@ enum { PF_T1 = 0, PF_T0 = 1 };
  *   F2 = U + zeta replaces U in its coupling term;
  * Vp >= 0 (pulling speed, W / tau0), lT > 0 (thermal length, W), yT the
  * position of the reference isotherm T0 at t = 0.  F1 must stay above 0.05
- * over the grid at t = 0.  bc_x = PF_BC_PERIODIC makes x periodic (2D).
+ * over the grid at t = 0.  bc_x = PF_BC_PERIODIC makes x periodic; y (and
+ * z) keep the mirror (no-flux) walls, which meet an interface at 90 deg.
  *
  * dt must not exceed the explicit-Euler bound 2 h^2 / (Lambda max(D, 1/F1min)),
  * Lambda = 16/3 for the isotropic Laplacians, 8 for L_{1,0}, 12 for L_{1,0,0};
@@ -102,8 +103,8 @@ typedef struct {
     int32_t precision;  /* pf_precision */
     int32_t max_grains;
     int32_t max_seeds;
-    int32_t bc_x;       /* PF_BC_MIRROR or PF_BC_PERIODIC (2D) */
-    int32_t thermal;    /* PF_ISOTHERMAL or PF_FROZEN_GRADIENT (2D) */
+    int32_t bc_x;       /* PF_BC_MIRROR or PF_BC_PERIODIC */
+    int32_t thermal;    /* PF_ISOTHERMAL or PF_FROZEN_GRADIENT */
     double Vp, lT, yT;  /* frozen gradient: pulling speed, thermal length, isotherm T0 at t = 0 */
     int32_t time_level; /* PF_T1 (default) or PF_T0 */
     int32_t reserved;   /* 0 */

@@ -46,12 +46,11 @@ bool valid_params(const pf_params* p) {
     if (!(p->D > 0) || !(p->lambda >= 0) || !std::isfinite(p->U0)) return false;
     if (p->max_grains < 1 || p->max_grains > 32767 || p->max_seeds < 0 || p->max_seeds > (1 << 20)) return false;
     if (p->bc_x != PF_BC_MIRROR && p->bc_x != PF_BC_PERIODIC) return false;
-    if (p->bc_x == PF_BC_PERIODIC && p->dim != 2) return false;
     if (p->thermal != PF_ISOTHERMAL && p->thermal != PF_FROZEN_GRADIENT) return false;
     if (p->time_level != PF_T1 && p->time_level != PF_T0) return false;
     double F1min = 1.0;
     if (p->thermal == PF_FROZEN_GRADIENT) {
-        if (p->dim != 2 || !(p->lT > 0) || !std::isfinite(p->lT) || !(p->Vp >= 0) || !std::isfinite(p->Vp) ||
+        if (!(p->lT > 0) || !std::isfinite(p->lT) || !(p->Vp >= 0) || !std::isfinite(p->Vp) ||
             !std::isfinite(p->yT))
             return false;
         // F1 = 1 - (1-k) zeta is smallest at the top row at t = 0 (the isotherm only moves up)
@@ -275,7 +274,8 @@ bool launch_sim_step(const pf_sim* s, int64_t step) {
     if (s->p.dim == 2)
         return launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp,
                              StepClock{nullptr, nullptr, (long long)step}, ds_of(s->p));
-    return launch_step3d(prec, s->p.scheme, s->bx, s->by, s->grid, s->st, s->work, s->n_work, s->rec, lp);
+    return launch_step3d(prec, s->p.scheme, s->bx, s->by, s->grid, s->st, s->work, s->n_work, s->rec, lp,
+                         StepClock{nullptr, nullptr, (long long)step});
 }
 
 }  // namespace
@@ -793,7 +793,7 @@ bool group_launch_once(pf_group* g, int launch_parity) {
         bool ok = c.dim == 2 ? launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs,
                                              launch_parity, clk, c.ds)
                              : launch_step3d(c.prec, c.scheme, c.bx, c.by, c.grid, g->st, g->work + c.w0, c.n, g->recs,
-                                             launch_parity);
+                                             launch_parity, clk);
         if (!ok) return false;
     }
     if (g->thermal_any && launch_tick(g->clock, g->st) != cudaSuccess) return false;

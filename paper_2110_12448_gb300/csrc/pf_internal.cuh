@@ -88,7 +88,7 @@ struct StepClock {
 bool launch_step2d(int prec, int scheme, int bx, int grid, cudaStream_t st, const WorkItem* work, int n_work,
                    const InstRec* recs, int launch_parity, StepClock clk, bool ds);
 bool launch_step3d(int prec, int scheme, int bx, int by, int grid, cudaStream_t st, const WorkItem* work,
-                   int n_work, const InstRec* recs, int launch_parity);
+                   int n_work, const InstRec* recs, int launch_parity, StepClock clk);
 // clock += 1 (one thread)
 cudaError_t launch_tick(long long* clock, cudaStream_t st);
 // Blocks of the fused kernel that fit on one SM (0 if not compiled).

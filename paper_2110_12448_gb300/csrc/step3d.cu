@@ -103,7 +103,8 @@ template <typename T, int S, int TX, int TY> struct Tile3 {
 
 template <typename T, int S, int TX, int TY>
 __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* __restrict__ work, int n_work,
-                                                              const InstRec* __restrict__ recs, int launch_parity) {
+                                                              const InstRec* __restrict__ recs, int launch_parity,
+                                                              StepClock clk) {
     using TL = Tile3<T, S, TX, TY>;
     constexpr int AX = TL::AX, AY = TL::AY, PX = TL::PX, PY = TL::PY, NT = TL::NT;
     constexpr int NFI = TL::NFI, NFZ = TL::NFZ;
@@ -146,10 +147,24 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
 
         // this thread's ring-region cell and the cell it computes in phase 1
         const int vx = x0 - 1 + tx, vy = y0 - 1 + ty;
-        const int mx = mirror_idx(vx, nx), my = mirror_idx(vy, ny);
+        // x walls: mirror, or periodic (rec.bcx); y and z walls: mirror
+        const bool per = rec.bcx != 0;
+        auto xidx = [&](int c) -> int { return per ? ((c % nx) + nx) % nx : mirror_idx(c, nx); };
+        const int mx = xidx(vx), my = mirror_idx(vy, ny);
         const bool do_p1 = vx >= -1 && vx <= nx && vy >= -1 && vy <= ny;
         const bool do_p2 = tx >= 1 && tx <= AX - 2 && ty >= 1 && ty <= AY - 2 && vx < nx && vy < ny;
-        const int jx = mx - x0 + 2, jy = my - y0 + 2;  // psi-region index of the phase-1 cell
+        // psi-region index of the phase-1 cell: a mirror ghost evaluates its mirror
+        // cell; a periodic ghost evaluates in place (its tile neighbourhood is
+        // the wrapped cell's)
+        const int jx = per ? vx - x0 + 2 : mx - x0 + 2, jy = my - y0 + 2;
+        // frozen temperature along +y (Eqs. Thermal_F1/_F2): zeta of the phase-1
+        // cell at this launch's step; F2 = U + zeta, the rate divided by F1
+        T zc = T(0), iF1 = T(1);
+        if (rec.thermal) {
+            const long long n = clk.clock ? clk.base[wi.inst] + *clk.clock : clk.step;
+            zc = (T)((double)my * rec.zA - rec.zB - (double)n * rec.zC);
+            iF1 = T(1) / (T(1) - omk * zc);
+        }
 
         auto PS = [&](int z, int y, int x) -> T& { return s_psi[((z & 7) * PY + y) * PX + x]; };
         auto RG = [&](T* base, int slots, int z, int y, int x) -> T& {
@@ -168,7 +183,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                 const int i = tid + k * NT;
                 if (i < PX * PY) {
                     const int px = i % PX, py = i / PX;
-                    const int gx = mirror_idx(x0 - 2 + px, nx), gy = mirror_idx(y0 - 2 + py, ny);
+                    const int gx = xidx(x0 - 2 + px), gy = mirror_idx(y0 - 2 + py, ny);
                     pv[k] = __ldg(psi + rz * sxy + (long long)gy * nx + gx);
                 }
             }
@@ -264,7 +279,8 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             const T ac = aniso_a3<T>(gc, R, eps, hh);
             const T ph = RG(s_phi, 8, p, jy - 1, jx - 1);
             const T u = RG(s_U, 4, p, jy - 1, jx - 1);
-            const T rate = (L + N + SQ2 * (ph - lam * (T(1) - ph * ph) * u)) * M3<T>::rcp(ac * ac) - SQ2 * ph * G;
+            const T rate =
+                ((L + N + SQ2 * (ph - lam * (T(1) - ph * ph) * (u + zc))) * M3<T>::rcp(ac * ac) - SQ2 * ph * G) * iF1;
             psin = pc + dt * rate;
             const T phn = M3<T>::tanh_(psin * ISQ2);
             // T1: delta phi = phi' - phi; T0: chain-rule increment, phi^n on the left-hand side
@@ -501,7 +517,8 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
 }
 
 template <typename T, int S, int TX, int TY>
-bool launch_t(int grid, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp) {
+bool launch_t(int grid, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp,
+              StepClock clk) {
     using TL = Tile3<T, S, TX, TY>;
     static bool attr = false;
     if (!attr) {
@@ -510,7 +527,7 @@ bool launch_t(int grid, cudaStream_t st, const WorkItem* work, int n_work, const
             return false;
         attr = true;
     }
-    k_step3d<T, S, TX, TY><<<grid, TL::NT, TL::smem, st>>>(work, n_work, recs, lp);
+    k_step3d<T, S, TX, TY><<<grid, TL::NT, TL::smem, st>>>(work, n_work, recs, lp, clk);
     return true;
 }
 template <typename T, int S, int TX, int TY> int occ_t() {
@@ -526,9 +543,10 @@ template <typename T, int S, int TX, int TY> int occ_t() {
 
 // Compiled tiles (block_x, block_y) = (TX + 4, TY + 4): (34, 18) and (34, 10).
 template <typename T, int S>
-bool launch_s(int bx, int by, int grid, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp) {
-    if (bx == 34 && by == 18) return launch_t<T, S, 30, 14>(grid, st, work, n_work, recs, lp);
-    if (bx == 34 && by == 10) return launch_t<T, S, 30, 6>(grid, st, work, n_work, recs, lp);
+bool launch_s(int bx, int by, int grid, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp,
+              StepClock clk) {
+    if (bx == 34 && by == 18) return launch_t<T, S, 30, 14>(grid, st, work, n_work, recs, lp, clk);
+    if (bx == 34 && by == 10) return launch_t<T, S, 30, 6>(grid, st, work, n_work, recs, lp, clk);
     return false;
 }
 template <typename T, int S> int occ_s(int bx, int by) {
@@ -540,13 +558,13 @@ template <typename T, int S> int occ_s(int bx, int by) {
 }  // namespace
 
 bool launch_step3d(int prec, int scheme, int bx, int by, int grid, cudaStream_t st, const WorkItem* work, int n_work,
-                   const InstRec* recs, int lp) {
+                   const InstRec* recs, int lp, StepClock clk) {
     if (prec == 0) {
-        if (scheme == S100) return launch_s<float, S100>(bx, by, grid, st, work, n_work, recs, lp);
-        if (scheme == SBAR120) return launch_s<float, SBAR120>(bx, by, grid, st, work, n_work, recs, lp);
+        if (scheme == S100) return launch_s<float, S100>(bx, by, grid, st, work, n_work, recs, lp, clk);
+        if (scheme == SBAR120) return launch_s<float, SBAR120>(bx, by, grid, st, work, n_work, recs, lp, clk);
     } else {
-        if (scheme == S100) return launch_s<double, S100>(bx, by, grid, st, work, n_work, recs, lp);
-        if (scheme == SBAR120) return launch_s<double, SBAR120>(bx, by, grid, st, work, n_work, recs, lp);
+        if (scheme == S100) return launch_s<double, S100>(bx, by, grid, st, work, n_work, recs, lp, clk);
+        if (scheme == SBAR120) return launch_s<double, SBAR120>(bx, by, grid, st, work, n_work, recs, lp, clk);
     }
     return false;
 }

@@ -73,8 +73,6 @@ DS = dict(thermal=1, bc_x=1, Vp=0.1, lT=100.0, yT=5.0)  # frozen gradient, perio
 
 @pytest.mark.parametrize("bad", [
     dict(bc_x=2), dict(thermal=2),
-    dict(dim=3, nz=8, scheme="SBAR120", bc_x=1, dt=0.01),        # periodic x is 2D only
-    dict(dim=3, nz=8, scheme="SBAR120", thermal=1, lT=100.0, dt=0.01),  # frozen gradient is 2D only
     dict(DS, lT=0.0), dict(DS, lT=float("inf")), dict(DS, Vp=-0.1), dict(DS, yT=float("nan")),
     # F1 = 1 - (1-k) ((ny-1) h - yT) / lT at the top row: 1 - 0.85 * (47 * 0.8 - 5) / 30 < 0.05
     dict(DS, lT=30.0),
@@ -85,6 +83,7 @@ def test_invalid_directional_parameters_rejected(bad):
 
 def test_directional_parameters_accepted_and_bound():
     assert native.required_bytes(_p(**DS)) > 0
+    assert native.required_bytes(_p(dim=3, nz=8, scheme="SBAR120", dt=0.01, **DS)) > 0
     # with F1min = 1 - 0.85 * (47 * 0.8 - 5) / 36 = 0.230 the psi mobility 1/F1min = 4.35 < D,
     # so the D bound still applies; with a small D the 1/F1min term takes over
     F1min = 1 - 0.85 * (47 * 0.8 - 5) / 36.0

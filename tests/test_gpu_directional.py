@@ -149,3 +149,68 @@ def test_group_on_legacy_stream_launches_directly(native):
     gp, gu = s.get_fields()
     op, ou = O.step(oracle_params(w, step=9), rots, g, psi, U, 20)
     assert rel_err(gp, op) < 20e-12 and rel_err(gu, ou) < 20e-12
+
+
+# ---- 3D: frozen gradient along +y, periodic x, mirror y and z ----
+
+def ds_state3(seed, nx, ny, nz, scheme, lT=60.0, Vp=0.3):
+    rng = np.random.default_rng(seed)
+    w = synth.free_dendrite_3d(nx, scheme=scheme)
+    w.ny, w.nz = ny, nz
+    w.bc_x, w.thermal, w.Vp, w.lT, w.yT = 1, 1, Vp, lT, ny * w.h * 0.4
+    psi, U = synth.random_state(rng, w)
+    g, rots = synth.random_grains(rng, w, 2)
+    w.rots = rots
+    return w, psi, U, g, rots
+
+
+def gpu_sim3(N, w, prec, g, rots, psi, U, step=0, stream=None):
+    p = N.make_params(3, w.nx, w.ny, w.nz, w.h, w.dt, w.k, w.eps4, w.lam, w.D, w.U0, w.scheme, prec,
+                      max_grains=rots.shape[0], bc_x=w.bc_x, thermal=w.thermal, Vp=w.Vp, lT=w.lT, yT=w.yT)
+    s = N.Sim(p, stream=stream)
+    s.set_grains(rots)
+    s.set_grain_index(g)
+    s.set_fields(psi, U)
+    s.set_step(step)
+    return s
+
+
+@pytest.mark.parametrize("shape", [(64, 21, 19), (37, 29, 17)])
+@pytest.mark.parametrize("scheme", ["SBAR120", "S100"])
+def test_fp64_3d_matches_oracle(native, scheme, shape):
+    w, psi, U, g, rots = ds_state3(31, *shape, scheme)
+    s = gpu_sim3(native, w, "f64", g, rots, psi, U, step=17)
+    s.step(1)
+    gp, gu = s.get_fields()
+    op, ou = O.step(oracle_params(w, step=17), rots, g, psi, U, 1)
+    assert rel_err(gp, op) < 1e-12 and rel_err(gu, ou) < 1e-12
+    s.step(4)
+    gp, gu = s.get_fields()
+    op, ou = O.step(oracle_params(w, step=17), rots, g, psi, U, 5)
+    assert rel_err(gp, op) < 5e-12 and rel_err(gu, ou) < 5e-12
+
+
+@pytest.mark.parametrize("scheme", ["SBAR120", "S100"])
+def test_fp32_3d_one_step(native, scheme):
+    w, psi, U, g, rots = ds_state3(32, 45, 23, 18, scheme)
+    psi32, U32 = psi.astype(np.float32), U.astype(np.float32)
+    s = gpu_sim3(native, w, "f32", g, rots, psi32, U32, step=3)
+    s.step(1)
+    gp, gu = s.get_fields()
+    op, ou = O.step(oracle_params(w, step=3), rots, g, psi32.astype(np.float64), U32.astype(np.float64), 1)
+    assert max_abs(np.tanh(gp.astype(np.float64) / math.sqrt(2)), np.tanh(op / math.sqrt(2))) < 2e-6
+    assert max_abs(gu, ou) < 5e-6
+
+
+def test_group_graph_clock_3d(native):
+    import torch
+    st = torch.cuda.Stream()
+    w, psi, U, g, rots = ds_state3(33, 40, 22, 16, "SBAR120")
+    s = gpu_sim3(native, w, "f64", g, rots, psi, U, step=50, stream=st)
+    grp = native.Group(1, native.Group.work_items(s), stream=st)
+    grp.add(s)
+    grp.step(35, use_graph=True)
+    grp.close()
+    gp, gu = s.get_fields()
+    op, ou = O.step(oracle_params(w, step=50), rots, g, psi, U, 35)
+    assert rel_err(gp, op) < 35e-12 and rel_err(gu, ou) < 35e-12
