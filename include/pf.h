@@ -228,6 +228,14 @@ int pf_get_tile(pf_sim* s, int* block_x, int* block_y, int* sweep);
  * or a negative PF_ERR_* code; needs a current CUDA device. */
 int pf_resident_units(pf_sim* s);
 
+/* Bounds-checked builds (compiled with -DPF_BOUNDS_CHECK): every global and
+ * shared-memory index formed by the kernels is checked; an index outside its
+ * array is counted, replaced by 0 (no access leaves the array) and the
+ * source line of the first one kept.  Returns PF_OK with the totals over all
+ * kernels since the library was loaded, or PF_ERR_STATE in a build without
+ * the checks (counts 0). */
+int pf_debug_bounds(unsigned long long* failures, int* first_line);
+
 int pf_destroy(pf_sim* s);
 const char* pf_status_string(int code);
 /* Text of the last CUDA error seen by any call (thread-local). */

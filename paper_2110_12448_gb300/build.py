@@ -1,6 +1,8 @@
 """Build step of the package: compiles the CUDA sources under ``csrc/`` for
 sm_103a with nvcc (one translation unit per file, compiled in parallel) and
-links them into ``_build/libpf.so`` in the package directory."""
+links them into ``_build/libpf.so`` in the package directory.  ``checked=True``
+builds the bounds-checked variant (-DPF_BOUNDS_CHECK) into
+``_build_checked/libpf.so`` instead (see pf_debug_bounds in include/pf.h)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -12,6 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpf.so")
+OUT_DIR_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(OUT_DIR_CHECKED, "libpf.so")
 SOURCES = ["step2d.cu", "step3d.cu", "observe.cu", "pf_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -31,15 +35,18 @@ def _newer(target: str, deps) -> bool:
     return all(os.path.getmtime(d) <= t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    out_dir, lib = (OUT_DIR_CHECKED, LIB_CHECKED) if checked else (OUT_DIR, LIB)
+    if checked:
+        extra_flags = (*extra_flags, "-DPF_BOUNDS_CHECK")
+    os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "pf.h"))
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or not _newer(o, [s] + headers):
             cmd = [nvcc(), *ARCH, *FLAGS, *extra_flags, "-c", s, "-o", o]
@@ -53,15 +60,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                     print(r.stdout, r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed: {' '.join(c)}\n{r.stderr}")
-    if force or jobs or not _newer(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or jobs or not _newer(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

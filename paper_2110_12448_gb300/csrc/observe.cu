@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(OBS_THREADS) k_observe(ObsArgs a, ObsPartial* 
         else if (a.ea == 1) jj += a.es;
         else kq += a.es;
         if (ii < 0 || jj < 0 || kq < 0 || ii >= nx || jj >= ny || kq >= nz) continue;
-        const double pn = (double)psi[(kq * ny + jj) * nx + ii];
+        const double pn = (double)psi[PF_CHK((kq * ny + jj) * nx + ii, N)];
         if (!(pn < 0.0)) continue;
         const double frac = __ddiv_rn(ps, __dsub_rn(ps, pn));
         double p[3] = {__dmul_rn((double)i, a.h), __dmul_rn((double)j, a.h),
@@ -162,7 +162,8 @@ __device__ double tip_interp(const TipArgs& a, const T* __restrict__ psi, const 
         f[q] = __dsub_rn(u, (double)i);
     }
     auto P = [&](int di, int dj, int dk) -> double {
-        return (double)psi[((long long)(i0[2] + dk) * a.ny + (i0[1] + dj)) * a.nx + (i0[0] + di)];
+        return (double)psi[PF_CHK(((long long)(i0[2] + dk) * a.ny + (i0[1] + dj)) * a.nx + (i0[0] + di),
+                                  (long long)a.nx * a.ny * (a.dim == 3 ? a.nz : 1))];
     };
     auto plane = [&](int dk) -> double {
         const double g0 = __dsub_rn(1.0, f[0]);
@@ -376,6 +377,8 @@ cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* r
     k_observe_finish<<<1, OBS_THREADS, 0, st>>>(partials, OBS_BLOCKS, result);
     return cudaGetLastError();
 }
+
+PF_BOUNDS_READER(bounds_observe)
 
 cudaError_t launch_tip_radius(const TipArgs& a, double* out, cudaStream_t st) {
     double* t = out + 8;  // 2 x 64 crossings after the five results

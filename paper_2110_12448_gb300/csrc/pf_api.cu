@@ -202,6 +202,7 @@ InstRec make_rec(const pf_sim* s, int parity_offset) {
     r.thermal = s->p.thermal == PF_FROZEN_GRADIENT ? 1 : 0;
     r.bcx = s->p.bc_x == PF_BC_PERIODIC ? 1 : 0;
     r.tlevel = s->p.time_level == PF_T0 ? 1 : 0;
+    r.n_grains = s->n_grains;
     if (r.thermal) {
         r.zA = s->p.h / s->p.lT;
         r.zB = s->p.yT / s->p.lT;
@@ -354,6 +355,7 @@ int pf_set_grains(pf_sim* s, int n_grains, const double* rot9, const double* cen
     }
     s->have_prev.assign(n_grains + 1, 0);
     s->prev.assign(4 * (n_grains + 1), 0.0);
+    s->work_dirty = true;  // the instance record carries the grain count
     return upload_rot(s);
 }
 
@@ -600,6 +602,19 @@ int pf_get_tile(pf_sim* s, int* block_x, int* block_y, int* sweep) {
     if (block_y) *block_y = s->by;
     if (sweep) *sweep = s->sweep;
     return PF_OK;
+}
+
+int pf_debug_bounds(unsigned long long* failures, int* first_line) {
+    if (!failures || !first_line) return PF_ERR_INVALID;
+    unsigned long long c[3] = {0, 0, 0};
+    int l[3] = {0, 0, 0};
+    const int r0 = bounds_step2d(&c[0], &l[0]);
+    const int r1 = bounds_step3d(&c[1], &l[1]);
+    const int r2 = bounds_observe(&c[2], &l[2]);
+    if (r0 < 0 || r1 < 0 || r2 < 0) return PF_ERR_CUDA;
+    *failures = c[0] + c[1] + c[2];
+    *first_line = l[0] ? l[0] : (l[1] ? l[1] : l[2]);
+    return (r0 == 1 && r1 == 1 && r2 == 1) ? PF_ERR_STATE : PF_OK;
 }
 
 int pf_resident_units(pf_sim* s) {

@@ -43,7 +43,7 @@ struct InstRec {
     int32_t thermal;  // 1: frozen temperature along +y (2D)
     int32_t bcx;      // 1: periodic x (2D)
     int32_t tlevel;   // 1: T0 time level (pure forward Euler of Eq. PF_b)
-    int32_t pad_;
+    int32_t n_grains; // rows of the rotation table
     double h, dt, k, eps4, lambda, D;
     // frozen temperature: zeta(row j, step n) = j zA - zB - n zC
     // (zA = h / lT, zB = yT / lT, zC = Vp dt / lT)
@@ -64,6 +64,40 @@ struct WorkItem {
 template <typename T> struct Guard;
 template <> struct Guard<float> { static constexpr float v = 1e-12f; };
 template <> struct Guard<double> { static constexpr double v = 1e-20; };
+
+// Bounds-checked build (compile with -DPF_BOUNDS_CHECK): every global and
+// shared-memory index the kernels form goes through PF_CHK(i, n).  An index
+// outside [0, n) is counted, its source line kept (first one), and replaced
+// by 0, so the access stays inside the array and nothing faults.  Each
+// translation unit keeps its own record and exports a host reader; pf_debug_bounds() sums them.  The default build compiles the
+// index unchanged.
+#ifdef PF_BOUNDS_CHECK
+static __device__ unsigned long long g_oob_count;
+static __device__ int g_oob_line;
+__device__ __forceinline__ long long pf_chk(long long i, long long n, int line) {
+    if (i >= 0 && i < n) return i;
+    atomicAdd(&g_oob_count, 1ull);
+    atomicCAS(&g_oob_line, 0, line);
+    return 0;
+}
+#define PF_CHK(i, n) ::pf::pf_chk((long long)(i), (long long)(n), __LINE__)
+#define PF_BOUNDS_READER(name)                                                     \
+    int name(unsigned long long* count, int* line) {                               \
+        if (cudaMemcpyFromSymbol(count, g_oob_count, sizeof(*count)) != cudaSuccess) \
+            return -1;                                                             \
+        if (cudaMemcpyFromSymbol(line, g_oob_line, sizeof(*line)) != cudaSuccess)  \
+            return -1;                                                             \
+        return 0;                                                                  \
+    }
+#else
+#define PF_CHK(i, n) (i)
+#define PF_BOUNDS_READER(name) \
+    int name(unsigned long long* count, int* line) { *count = 0; *line = 0; return 1; }
+#endif
+// host readers of the per-unit records (return 1 in an unchecked build)
+int bounds_step2d(unsigned long long* count, int* line);
+int bounds_step3d(unsigned long long* count, int* line);
+int bounds_observe(unsigned long long* count, int* line);
 
 // Cell-centred mirror of an index into [0, n): -1 -> 0, -2 -> 1, n -> n-1,
 // n+1 -> n-2.  Values further out (never consumed) are clamped in range.

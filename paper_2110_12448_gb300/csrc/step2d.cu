@@ -265,36 +265,36 @@ template <typename T>
 __device__ __forceinline__ void load_pair(const T* __restrict__ row, int c, int nx, bool vec, bool per, T& a, T& b) {
     c = wrap_once(c, nx, per);
     if (vec && c >= 0 && c + 1 < nx) {
-        const typename Vec2<T>::t v = __ldg(reinterpret_cast<const typename Vec2<T>::t*>(row + c));
+        const typename Vec2<T>::t v = __ldg(reinterpret_cast<const typename Vec2<T>::t*>(row + PF_CHK(c, nx - 1)));
         a = v.x;
         b = v.y;
     } else {
-        a = __ldg(row + col_idx(c, nx, per));
-        b = __ldg(row + col_idx(c + 1, nx, per));
+        a = __ldg(row + PF_CHK(col_idx(c, nx, per), nx));
+        b = __ldg(row + PF_CHK(col_idx(c + 1, nx, per), nx));
     }
 }
 __device__ __forceinline__ void load_grain_pair(const int16_t* __restrict__ row, int c, int nx, bool vec, bool per,
                                                 int& a, int& b) {
     c = wrap_once(c, nx, per);
     if (vec && c >= 0 && c + 1 < nx) {
-        const int v = __ldg(reinterpret_cast<const int*>(row + c));
+        const int v = __ldg(reinterpret_cast<const int*>(row + PF_CHK(c, nx - 1)));
         a = (int)(int16_t)(v & 0xffff);
         b = (int)(int16_t)((unsigned)v >> 16);
     } else {
-        a = __ldg(row + col_idx(c, nx, per));
-        b = __ldg(row + col_idx(c + 1, nx, per));
+        a = __ldg(row + PF_CHK(col_idx(c, nx, per), nx));
+        b = __ldg(row + PF_CHK(col_idx(c + 1, nx, per), nx));
     }
 }
 template <typename T>
-__device__ __forceinline__ void store_pair(T* __restrict__ row, int c, bool vec, bool okL, bool okR, V<T> v) {
+__device__ __forceinline__ void store_pair(T* __restrict__ row, int c, int nx, bool vec, bool okL, bool okR, V<T> v) {
     if (vec && okL && okR) {
         typename Vec2<T>::t o;
         o.x = v.x();
         o.y = v.y();
-        *reinterpret_cast<typename Vec2<T>::t*>(row + c) = o;
+        *reinterpret_cast<typename Vec2<T>::t*>(row + PF_CHK(c, nx - 1)) = o;
     } else {
-        if (okL) row[c] = v.x();
-        if (okR) row[c + 1] = v.y();
+        if (okL) row[PF_CHK(c, nx)] = v.x();
+        if (okR) row[PF_CHK(c + 1, nx)] = v.y();
     }
 }
 
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         const bool hiL = ((mL - (x0 - 2)) & 1) != 0, hiR = ((mR - (x0 - 2)) & 1) != 0;
 
         auto fetch_row = [&](const T* f, int vr, T& a, T& b) {
-            load_pair<T>(f + (size_t)mirror_idx(vr, ny) * nx, cL, nx, vec, per, a, b);
+            load_pair<T>(f + (size_t)PF_CHK(mirror_idx(vr, ny), ny) * nx, cL, nx, vec, per, a, b);
         };
         auto make_row = [&](T a, T b, bool wide) {
             Row<T> row;
@@ -398,6 +398,8 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             o.l = d.x();
             o.r = d.y();
             if (edge) {
+                // a far ghost column (beyond nx + 1) gets an out-of-range source lane,
+                // which the shuffle reduces modulo 32; its value reaches no output
                 const T aL = __shfl_sync(FULL, d.x(), srcL), bL = __shfl_sync(FULL, d.y(), srcL);
                 const T aR = __shfl_sync(FULL, d.x(), srcR), bR = __shfl_sync(FULL, d.y(), srcR);
                 o.l = realL ? o.l : (hiL ? bL : aL);
@@ -414,8 +416,8 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         int cgL = -1, cgR = -1;
         auto set_rot = [&](int gL, int gR) {
             if (gL != cgL || gR != cgR) {
-                const T* A = rot + 9 * gL;
-                const T* B = rot + 9 * gR;
+                const T* A = rot + 9 * PF_CHK(gL, rec.n_grains);
+                const T* B = rot + 9 * PF_CHK(gR, rec.n_grains);
                 RR.a = mk(__ldg(A + 0), __ldg(B + 0));
                 RR.b = mk(__ldg(A + 1), __ldg(B + 1));
                 RR.c = mk(__ldg(A + 3), __ldg(B + 3));
@@ -616,14 +618,14 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             V<T> psn, fn, dm = bc<T>(T(0)), d0;
             const bool ghost = (y0 - 1) < 0;
             if (!ghost) {
-                load_grain_pair(grain + (size_t)(y0 - 1) * nx, cL, nx, vec, per, gL, gR);
+                load_grain_pair(grain + (size_t)PF_CHK((y0 - 1), ny) * nx, cL, nx, vec, per, gL, gR);
                 phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, psn, fn, dm);
             }
-            load_grain_pair(grain + (size_t)y0 * nx, cL, nx, vec, per, gL, gR);
+            load_grain_pair(grain + (size_t)PF_CHK(y0, ny) * nx, cL, nx, vec, per, gL, gR);
             phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, psn, fn, d0);
             if (ghost) dm = d0;
             phin_cur = fn;
-            if (y0 < y1) store_pair<T>(psi_o + (size_t)y0 * nx, cL, vec, outL, outR, psn);
+            if (y0 < y1) store_pair<T>(psi_o + (size_t)PF_CHK(y0, ny) * nx, cL, nx, vec, outL, outR, psn);
             const Row<T> dmr = dphi_row(dm), d0r = dphi_row(d0);
             // phase-2 fluxes at row y0-1 (carries only); psi rows y0-3 .. y0+1
             const Row<T> aDm = alphaD(phm), aAm = alphaA(um, dmr);
@@ -644,7 +646,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         int nGa = 0, nGb = 0;
         fetch_row(psi, y0 + 2, nPa, nPb);
         fetch_row(Uf, y0 + 1, nUa, nUb);
-        if (y0 + 1 < ny) load_grain_pair(grain + (size_t)(y0 + 1) * nx, cL, nx, vec, per, nGa, nGb);
+        if (y0 + 1 < ny) load_grain_pair(grain + (size_t)PF_CHK((y0 + 1), ny) * nx, cL, nx, vec, per, nGa, nGb);
 
         // ---------------- sweep ----------------
         for (int r = y0; r < y1; ++r) {
@@ -654,7 +656,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             const int gL = nGa, gR = nGb;
             fetch_row(psi, r + 3, nPa, nPb);
             fetch_row(Uf, r + 2, nUa, nUb);
-            if (r + 2 < ny) load_grain_pair(grain + (size_t)(r + 2) * nx, cL, nx, vec, per, nGa, nGb);
+            if (r + 2 < ny) load_grain_pair(grain + (size_t)PF_CHK((r + 2), ny) * nx, cL, nx, vec, per, nGa, nGb);
 
             // phase 1 at row r+1
             V<T> phn = bc<T>(T(0));
@@ -662,7 +664,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             if (r + 1 < ny) {
                 V<T> psn, d;
                 phase1(r + 1, P[2], P[3], P[4], PH1, UU1, gL, gR, psn, phn, d);
-                if (r + 1 < y1) store_pair<T>(psi_o + (size_t)(r + 1) * nx, cL, vec, outL, outR, psn);
+                if (r + 1 < y1) store_pair<T>(psi_o + (size_t)PF_CHK((r + 1), ny) * nx, cL, nx, vec, outL, outR, psn);
                 DP1 = dphi_row(d);
             } else {
                 DP1 = DP0;  // ghost row ny mirrors row ny-1 = r
@@ -678,7 +680,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
                 const V<T> num =
                     fma(bc<T>(dt * cs), fma(bc<T>(Dc), sD, sA), fma(bc<T>(omk), u, bc<T>(T(1))) * DP0.C());
                 const V<T> un = fma(num, rcp2(fma(bc<T>(-omk), phin_cur, bc<T>(T(1) + kk))), u);
-                store_pair<T>(U_o + (size_t)r * nx, cL, vec, outL, outR, un);
+                store_pair<T>(U_o + (size_t)PF_CHK(r, ny) * nx, cL, nx, vec, outL, outR, un);
             }
             phin_cur = phn;
             P[0] = P[1];
@@ -715,6 +717,8 @@ template <typename T, int S> int occ_one(bool ds) {
 }
 
 }  // namespace
+
+PF_BOUNDS_READER(bounds_step2d)
 
 // The 2D kernel is warp-granular: `bx` must be 64 (columns a warp holds) and
 // `grid` counts warps.

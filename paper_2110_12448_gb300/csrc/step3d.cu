@@ -166,9 +166,14 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             iF1 = T(1) / (T(1) - omk * zc);
         }
 
-        auto PS = [&](int z, int y, int x) -> T& { return s_psi[((z & 7) * PY + y) * PX + x]; };
+        // shared-memory elements of the block (the checked build bounds every
+        // ring access by the whole allocation: the unconditional owned-flux
+        // loads read one ring cell past an array on purpose)
+        constexpr long long SM_ELEMS = (long long)(TL::smem / sizeof(T));
+        const long long NN = sxy * nz;  // cells of the instance
+        auto PS = [&](int z, int y, int x) -> T& { return s_psi[PF_CHK(((z & 7) * PY + y) * PX + x, 8 * PX * PY)]; };
         auto RG = [&](T* base, int slots, int z, int y, int x) -> T& {
-            return base[((z & (slots - 1)) * AY + y) * AX + x];
+            return s_psi[PF_CHK((base - s_psi) + (((z & (slots - 1)) * AY + y) * AX + x), SM_ELEMS)];
         };
 
         // plane loads, split into a global fetch into registers (issued one
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                 if (i < PX * PY) {
                     const int px = i % PX, py = i / PX;
                     const int gx = xidx(x0 - 2 + px), gy = mirror_idx(y0 - 2 + py, ny);
-                    pv[k] = __ldg(psi + rz * sxy + (long long)gy * nx + gx);
+                    pv[k] = __ldg(psi + PF_CHK(rz * sxy + (long long)gy * nx + gx, NN));
                 }
             }
         };
@@ -204,13 +209,13 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             fetch_psi(vz);
             put_psi(vz);
         };
-        auto fetch_U = [&](int vz) { uv = __ldg(Uf + mirror_idx(vz, nz) * sxy + (long long)my * nx + mx); };
+        auto fetch_U = [&](int vz) { uv = __ldg(Uf + PF_CHK(mirror_idx(vz, nz) * sxy + (long long)my * nx + mx, NN)); };
         auto put_U = [&](int vz) { RG(s_U, 4, vz, ty, tx) = uv; };
         auto load_U_plane = [&](int vz) {
             fetch_U(vz);
             put_U(vz);
         };
-        auto grain_at = [&](int p) -> int { return grain[mirror_idx(p, nz) * sxy + (long long)my * nx + mx]; };
+        auto grain_at = [&](int p) -> int { return grain[PF_CHK(mirror_idx(p, nz) * sxy + (long long)my * nx + mx, NN)]; };
         // crystal frame of the phase-1 cell, reloaded only when its grain changes
         T R[9];
         int gR = -1;
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
         auto phase1 = [&](int p, int g, T& psin) -> T {
             if (g != gR) {
 #pragma unroll
-                for (int q = 0; q < 9; ++q) R[q] = __ldg(rot + 9 * g + q);
+                for (int q = 0; q < 9; ++q) R[q] = __ldg(rot + 9 * PF_CHK(g, rec.n_grains) + q);
                 gR = g;
             }
             auto P = [&](int dx, int dy, int dz) -> T { return PS(p + dz, jy + dy, jx + dx); };
@@ -414,21 +419,23 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             }
 #pragma unroll
             for (int q = 0; q < NFI; ++q) {
-                fiD[q * NT] = ok[q] ? oD[q] : T(0);
-                fiA[q * NT] = ok[q] ? oA[q] : T(0);
+                s_psi[PF_CHK((fiD - s_psi) + q * NT, SM_ELEMS)] = ok[q] ? oD[q] : T(0);
+                s_psi[PF_CHK((fiA - s_psi) + q * NT, SM_ELEMS)] = ok[q] ? oA[q] : T(0);
             }
 #pragma unroll
             for (int q = 0; q < NFZ; ++q) {
-                fzD[q * NT] = ok[NFI + q] ? oD[NFI + q] : T(0);
-                fzA[q * NT] = ok[NFI + q] ? oA[NFI + q] : T(0);
+                s_psi[PF_CHK((fzD - s_psi) + q * NT, SM_ELEMS)] = ok[NFI + q] ? oD[NFI + q] : T(0);
+                s_psi[PF_CHK((fzA - s_psi) + q * NT, SM_ELEMS)] = ok[NFI + q] ? oA[NFI + q] : T(0);
             }
         };
         // eight/eighteen-flux sums of an output cell at plane r: own fluxes
         // plus the negated owned fluxes of the neighbours that share them
         auto flux_sum = [&](int bufz_cur, int bufz_prev, T& sD, T& sA) {
-            auto FI = [&](int f, int k, int dx, int dy) -> T { return s_fi[(f * NFI + k) * NT + tid + dy * AX + dx]; };
+            auto FI = [&](int f, int k, int dx, int dy) -> T {
+                return s_fi[PF_CHK((f * NFI + k) * NT + tid + dy * AX + dx, 2 * NFI * NT)];
+            };
             auto FZ = [&](int b, int f, int k, int dx, int dy) -> T {
-                return s_fz[((b * 2 + f) * NFZ + k) * NT + tid + dy * AX + dx];
+                return s_fz[PF_CHK(((b * 2 + f) * NFZ + k) * NT + tid + dy * AX + dx, 2 * 2 * NFZ * NT)];
             };
             T s[2];
 #pragma unroll
@@ -465,7 +472,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                 (void)phase1(z0 - 1, grain_at(z0 - 1), d);
             }
             phin_cur = phase1(z0, grain_at(z0), psn);
-            if (do_p2 && z0 < z1) psi_o[z0 * sxy + (long long)vy * nx + vx] = psn;
+            if (do_p2 && z0 < z1) psi_o[PF_CHK(z0 * sxy + (long long)vy * nx + vx, NN)] = psn;
             if (z0 - 1 < 0) copy_plane(z0 - 1, z0);
         }
         __syncthreads();
@@ -492,7 +499,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                 if (r + 1 < nz) {
                     T psn;
                     phin_next = phase1(r + 1, g1, psn);
-                    if (do_p2 && r + 1 < z1) psi_o[(r + 1) * sxy + (long long)vy * nx + vx] = psn;
+                    if (do_p2 && r + 1 < z1) psi_o[PF_CHK((r + 1) * sxy + (long long)vy * nx + vx, NN)] = psn;
                 } else {
                     copy_plane(r + 1, r);
                 }
@@ -508,7 +515,7 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                 const T dph = RG(s_dphi, 4, r, ty, tx);
                 const T un = u0 + (dt * (Dc * sD + sA) * cs + (T(1) + omk * u0) * dph) *
                                       M3<T>::rcp(T(1) + kk - omk * phin_cur);
-                U_o[r * sxy + (long long)vy * nx + vx] = un;
+                U_o[PF_CHK(r * sxy + (long long)vy * nx + vx, NN)] = un;
             }
             phin_cur = phin_next;
         }
@@ -556,6 +563,8 @@ template <typename T, int S> int occ_s(int bx, int by) {
 }
 
 }  // namespace
+
+PF_BOUNDS_READER(bounds_step3d)
 
 bool launch_step3d(int prec, int scheme, int bx, int by, int grid, cudaStream_t st, const WorkItem* work, int n_work,
                    const InstRec* recs, int lp, StepClock clk) {

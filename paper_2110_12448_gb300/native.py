@@ -99,6 +99,7 @@ def lib():
                 "pf_set_tile": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
                 "pf_get_tile": (C.c_int, [vp, P(C.c_int), P(C.c_int), P(C.c_int)]),
                 "pf_resident_units": (C.c_int, [vp]),
+                "pf_debug_bounds": (C.c_int, [P(C.c_uint64), P(C.c_int)]),
                 "pf_destroy": (C.c_int, [vp]),
                 "pf_status_string": (C.c_char_p, [C.c_int]),
                 "pf_last_cuda_error": (C.c_char_p, []),
@@ -119,6 +120,17 @@ def lib():
                 f.argtypes = args
             _lib = L
     return _lib
+
+
+def debug_bounds():
+    """(failures, first source line) of a bounds-checked build; None in a
+    build without the checks."""
+    n, line = C.c_uint64(), C.c_int()
+    rc = lib().pf_debug_bounds(C.byref(n), C.byref(line))
+    if rc == PF_ERR_STATE:
+        return None
+    _check(rc, "pf_debug_bounds")
+    return n.value, line.value
 
 
 def status_string(code: int) -> str:

@@ -91,3 +91,8 @@ def test_directional_parameters_accepted_and_bound():
     bound = 2 * 0.64 / (16 / 3 * (1 / F1min))
     assert native.required_bytes(_p(**dict(d_small, dt=bound * 0.99))) > 0
     assert native.required_bytes(_p(**dict(d_small, dt=bound * 1.01))) == 0
+
+
+def test_unchecked_build_reports_no_bounds_record():
+    # the default library compiles the index checks away
+    assert native.debug_bounds() is None
