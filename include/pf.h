@@ -236,6 +236,14 @@ int pf_resident_units(pf_sim* s);
  * the checks (counts 0). */
 int pf_debug_bounds(unsigned long long* failures, int* first_line);
 
+/* Host-side fault injection for tests of the error paths (no GPU fault is
+ * made): after `after_steps` more steps have launched (pf_step or
+ * pf_group_step, all handles of the process), the next step is not launched
+ * and the call returns PF_ERR_CUDA with pf_last_cuda_error() naming the
+ * injection; the handles advance by the steps that did launch (a graph
+ * replay counts as its 16 steps and fails whole).  after_steps < 0 disarms. */
+int pf_debug_inject_launch_failure(long long after_steps);
+
 int pf_destroy(pf_sim* s);
 const char* pf_status_string(int code);
 /* Text of the last CUDA error seen by any call (thread-local). */

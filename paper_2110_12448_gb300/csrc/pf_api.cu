@@ -2,6 +2,7 @@
 // the caller's device buffer, work lists, launches, observation and the
 // batching groups (one persistent launch per class, CUDA-graph replay).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +25,24 @@ int cuda_fail(cudaError_t e, const char* what) {
     g_last_cuda = buf;
     return PF_ERR_CUDA;
 }
+// Host-side fault injection (pf_debug_inject_launch_failure): the number of
+// steps that may still launch before an injected launch failure (-1: off).
+std::atomic<long long> g_inject{-1};
+
+// True if launching the next k steps runs into the armed failure (which is
+// then consumed and reported like a CUDA error); else the k steps are counted.
+bool inject_hits(long long k) {
+    long long v = g_inject.load();
+    if (v < 0) return false;
+    if (v < k) {
+        g_inject.store(-1);
+        g_last_cuda = "injected launch failure (pf_debug_inject_launch_failure)";
+        return true;
+    }
+    g_inject.store(v - k);
+    return false;
+}
+
 #define CK(call)                                       \
     do {                                               \
         cudaError_t e_ = (call);                       \
@@ -401,7 +420,15 @@ int pf_step(pf_sim* s, int64_t n) {
         if (rc != PF_OK) return rc;
     }
     for (int64_t i = 0; i < n; ++i) {
-        if (!launch_sim_step(s, s->step + i)) return PF_ERR_INVALID;
+        // on a failure the handle stays consistent: it has advanced by the i steps launched
+        if (inject_hits(1)) {
+            s->step += i;
+            return PF_ERR_CUDA;
+        }
+        if (!launch_sim_step(s, s->step + i)) {
+            s->step += i;
+            return PF_ERR_INVALID;
+        }
     }
     if (n > 0) CK(cudaGetLastError());
     s->step += n;
@@ -615,6 +642,11 @@ int pf_debug_bounds(unsigned long long* failures, int* first_line) {
     *failures = c[0] + c[1] + c[2];
     *first_line = l[0] ? l[0] : (l[1] ? l[1] : l[2]);
     return (r0 == 1 && r1 == 1 && r2 == 1) ? PF_ERR_STATE : PF_OK;
+}
+
+int pf_debug_inject_launch_failure(long long after_steps) {
+    g_inject.store(after_steps < 0 ? -1 : after_steps);
+    return PF_OK;
 }
 
 int pf_resident_units(pf_sim* s) {
@@ -891,10 +923,17 @@ int pf_group_step(pf_group* g, int64_t n, int use_graph) {
     }
     int64_t done = 0;
     const int GL = 16;  // launches per graph replay (even)
+    // on a failure the group and its members advance by the `done` steps launched
+    auto stop = [&](int rc) {
+        g->launches += done;
+        for (pf_sim* s : g->members) s->step += done;
+        return rc;
+    };
     // the legacy default stream cannot be captured into a graph
     if (use_graph && n >= GL && g->st != nullptr && g->st != cudaStreamPerThread) {
         if ((g->launches & 1) != 0) {
-            if (!group_launch_once(g, 1)) return PF_ERR_INVALID;
+            if (inject_hits(1)) return stop(PF_ERR_CUDA);
+            if (!group_launch_once(g, 1)) return stop(PF_ERR_INVALID);
             ++done;
         }
         if (!g->graph) {
@@ -911,12 +950,16 @@ int pf_group_step(pf_group* g, int64_t n, int use_graph) {
             g->graph_len = GL;
         }
         while (n - done >= GL) {
-            CK(cudaGraphLaunch(g->graph, g->st));
+            if (inject_hits(GL)) return stop(PF_ERR_CUDA);
+            const cudaError_t e = cudaGraphLaunch(g->graph, g->st);
+            if (e != cudaSuccess) return stop(cuda_fail(e, "cudaGraphLaunch"));
             done += GL;
         }
     }
-    for (; done < n; ++done)
-        if (!group_launch_once(g, (int)((g->launches + done) & 1))) return PF_ERR_INVALID;
+    for (; done < n; ++done) {
+        if (inject_hits(1)) return stop(PF_ERR_CUDA);
+        if (!group_launch_once(g, (int)((g->launches + done) & 1))) return stop(PF_ERR_INVALID);
+    }
     CK(cudaGetLastError());
     g->launches += n;
     for (pf_sim* s : g->members) s->step += n;

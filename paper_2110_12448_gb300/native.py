@@ -100,6 +100,7 @@ def lib():
                 "pf_get_tile": (C.c_int, [vp, P(C.c_int), P(C.c_int), P(C.c_int)]),
                 "pf_resident_units": (C.c_int, [vp]),
                 "pf_debug_bounds": (C.c_int, [P(C.c_uint64), P(C.c_int)]),
+                "pf_debug_inject_launch_failure": (C.c_int, [C.c_longlong]),
                 "pf_destroy": (C.c_int, [vp]),
                 "pf_status_string": (C.c_char_p, [C.c_int]),
                 "pf_last_cuda_error": (C.c_char_p, []),
@@ -131,6 +132,11 @@ def debug_bounds():
         return None
     _check(rc, "pf_debug_bounds")
     return n.value, line.value
+
+
+def inject_launch_failure(after_steps: int):
+    """Arm (>= 0) or disarm (< 0) the host-side injected launch failure."""
+    _check(lib().pf_debug_inject_launch_failure(int(after_steps)), "pf_debug_inject_launch_failure")
 
 
 def status_string(code: int) -> str:
