@@ -53,10 +53,10 @@ def dist_env():
 TRAFFIC = {
     # profiles/k_step2d_sbar21_f32_orientation_sweep_10x1024sq.md
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
-                "sha256": "9854506c6ca4a8a58d75ec80f866bf6ed480ba5f78525c2ca32329f5e4693873", "bytes": 154593536},
+                "sha256": "80863230f0d9aa5072ff497585917f2625b80d4e592830dda8fdbfbf7cb09a5a", "bytes": 155363072},
     # profiles/k_step3d_sbar120_f32_dendrite_256cube.md
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
-                   "sha256": "19935abcc464729f045d148f0c9d5df216a7ec0229da75f2c0ddb505b2daa1b0", "bytes": 262713856},
+                   "sha256": "4ddef8d8116e529fedd75ae324c5437aefd82e1b627e2f18f4db4b6d5fc6c94e", "bytes": 262745088},
 }
 
 
