@@ -266,9 +266,18 @@ class Sim:
         d["axis"] = tuple(o.axis)
         return d
 
-    def get_fields(self):
-        psi = np.zeros(self.shape, self.np_dtype)
-        U = np.zeros(self.shape, self.np_dtype)
+    def get_fields(self, out=None):
+        """Copy of the current psi, U.  `out` = (psi, U) writes into caller
+        arrays instead (C-contiguous, the handle's shape and dtype), e.g. views
+        of pinned host tensors, which the copy reaches at full link speed."""
+        if out is None:
+            psi = np.zeros(self.shape, self.np_dtype)
+            U = np.zeros(self.shape, self.np_dtype)
+        else:
+            psi, U = out
+            for a in (psi, U):
+                if a.shape != tuple(self.shape) or a.dtype != self.np_dtype or not a.flags.c_contiguous:
+                    raise ValueError("get_fields(out=...): arrays must be C-contiguous with the handle's shape and dtype")
         _check(lib().pf_get_fields(self.h, C.c_void_p(psi.ctypes.data), C.c_void_p(U.ctypes.data)), "pf_get_fields")
         return psi, U
 

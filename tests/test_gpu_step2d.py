@@ -217,3 +217,18 @@ def test_checkpoint_resume_bitwise(native):
     out = c.get_fields()
     assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
     assert c.steps_done == 60
+
+
+def test_get_fields_into_pinned_buffers(native):
+    # reading straight into caller (pinned) arrays gives the same fields as a fresh copy
+    import torch
+    w = synth.free_dendrite_2d(70, ny=33)
+    s = native.Sim.from_workload(w, "f32")
+    s.step(5)
+    a, b = s.get_fields()
+    hp = torch.empty(s.shape, dtype=torch.float32).pin_memory()
+    hu = torch.empty(s.shape, dtype=torch.float32).pin_memory()
+    s.get_fields(out=(hp.numpy(), hu.numpy()))
+    assert np.array_equal(hp.numpy(), a) and np.array_equal(hu.numpy(), b)
+    with pytest.raises(ValueError):
+        s.get_fields(out=(np.zeros(s.shape, np.float64), np.zeros(s.shape, np.float64)))
