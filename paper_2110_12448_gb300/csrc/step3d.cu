@@ -81,6 +81,60 @@ template <typename T> __device__ __forceinline__ T aniso_a3(const T g[3], const 
     return T(1) - T(3) * eps + T(4) * eps * q;
 }
 
+// The D~ fluxes of the D term (alpha = 1 - phi, beta = U) and of the
+// approximated anti-trapping term (alpha from delta phi, beta = psi) share
+// their stencils and weights, so S-bar_{1,2,0} evaluates them as one pair
+// (D, A): packed FP32x2 arithmetic in FP32, two scalars in FP64.
+template <typename T> struct P2;
+template <> struct P2<float> {
+    float2 v;
+    __device__ __forceinline__ float d() const { return v.x; }
+    __device__ __forceinline__ float a() const { return v.y; }
+};
+template <> struct P2<double> {
+    double x, y;
+    __device__ __forceinline__ double d() const { return x; }
+    __device__ __forceinline__ double a() const { return y; }
+};
+__device__ __forceinline__ P2<float> p2(float d, float a) {
+    P2<float> r;
+    r.v = make_float2(d, a);
+    return r;
+}
+__device__ __forceinline__ P2<double> p2(double d, double a) {
+    P2<double> r;
+    r.x = d;
+    r.y = a;
+    return r;
+}
+__device__ __forceinline__ P2<float> operator+(P2<float> a, P2<float> b) {
+    P2<float> r;
+    r.v = __fadd2_rn(a.v, b.v);
+    return r;
+}
+__device__ __forceinline__ P2<float> operator-(P2<float> a, P2<float> b) {
+    P2<float> r;
+    r.v = __ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v);  // exactly a - b
+    return r;
+}
+__device__ __forceinline__ P2<float> operator*(P2<float> a, P2<float> b) {
+    P2<float> r;
+    r.v = __fmul2_rn(a.v, b.v);
+    return r;
+}
+__device__ __forceinline__ P2<double> operator+(P2<double> a, P2<double> b) { return p2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ P2<double> operator-(P2<double> a, P2<double> b) { return p2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ P2<double> operator*(P2<double> a, P2<double> b) { return p2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ P2<float> fma2(P2<float> a, P2<float> b, P2<float> c) {
+    P2<float> r;
+    r.v = __ffma2_rn(a.v, b.v, c.v);
+    return r;
+}
+__device__ __forceinline__ P2<double> fma2(P2<double> a, P2<double> b, P2<double> c) {
+    return p2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <typename T> __device__ __forceinline__ P2<T> bc2(T c) { return p2(c, c); }
+
 template <typename T> struct ConstOf3;
 template <> struct ConstOf3<float> {
     static __device__ __forceinline__ const float* get(const InstRec& r) { return r.cf; }
@@ -318,23 +372,27 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             T* fzD = s_fz + (buf * 2 * NFZ) * NT + tid;
             T* fzA = s_fz + (buf * 2 * NFZ + NFZ) * NT + tid;
             const T u0 = bU(0, 0, 0), p0 = bP(0, 0, 0);
+            // (D, A) pairs of alpha and beta
+            auto A2 = [&](int dx, int dy, int dz) -> P2<T> { return p2(aD(dx, dy, dz), aA(dx, dy, dz)); };
+            auto B2 = [&](int dx, int dy, int dz) -> P2<T> { return p2(bU(dx, dy, dz), bP(dx, dy, dz)); };
+            const P2<T> b00 = p2(u0, p0);
             // face toward e: returns (D, A) flux
             auto face = [&](const int e[3], T& fD, T& fA) {
                 if (ISO) {
-                    T nD = aD(0, 0, 0) + aD(e[0], e[1], e[2]), nA = aA(0, 0, 0) + aA(e[0], e[1], e[2]);
-                    T mD = T(0), mA = T(0);
+                    const P2<T> n = A2(0, 0, 0) + A2(e[0], e[1], e[2]);
+                    P2<T> m = bc2<T>(T(0));
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         if (e[q] != 0) continue;
 #pragma unroll
                         for (int s2 = -1; s2 <= 1; s2 += 2) {
                             const int t[3] = {q == 0 ? s2 : 0, q == 1 ? s2 : 0, q == 2 ? s2 : 0};
-                            mD += aD(t[0], t[1], t[2]) + aD(e[0] + t[0], e[1] + t[1], e[2] + t[2]);
-                            mA += aA(t[0], t[1], t[2]) + aA(e[0] + t[0], e[1] + t[1], e[2] + t[2]);
+                            m = m + (A2(t[0], t[1], t[2]) + A2(e[0] + t[0], e[1] + t[1], e[2] + t[2]));
                         }
                     }
-                    fD = T(2) * (T(0.25) * nD + T(1.0 / 16.0) * mD) * (bU(e[0], e[1], e[2]) - u0);
-                    fA = T(2) * (T(0.25) * nA + T(1.0 / 16.0) * mA) * (bP(e[0], e[1], e[2]) - p0);
+                    const P2<T> f = fma2(bc2<T>(T(0.5)), n, bc2<T>(T(1.0 / 8.0)) * m) * (B2(e[0], e[1], e[2]) - b00);
+                    fD = f.d();
+                    fA = f.a();
                 } else {
                     fD = T(0.5) * (aD(0, 0, 0) + aD(e[0], e[1], e[2])) * (bU(e[0], e[1], e[2]) - u0);
                     T gf[3];
@@ -360,20 +418,19 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             // edge toward d = e1 + e2 (e3 the third axis)
             auto edge = [&](const int e1[3], const int e2[3], int ax3, T& fD, T& fA) {
                 const int d[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
-                T nD = aD(0, 0, 0) + aD(e1[0], e1[1], e1[2]) + aD(e2[0], e2[1], e2[2]) + aD(d[0], d[1], d[2]);
-                T nA = aA(0, 0, 0) + aA(e1[0], e1[1], e1[2]) + aA(e2[0], e2[1], e2[2]) + aA(d[0], d[1], d[2]);
-                T mD = T(0), mA = T(0);
+                const P2<T> n = ((A2(0, 0, 0) + A2(e1[0], e1[1], e1[2])) + A2(e2[0], e2[1], e2[2])) + A2(d[0], d[1], d[2]);
+                P2<T> m = bc2<T>(T(0));
 #pragma unroll
                 for (int s3 = -1; s3 <= 1; s3 += 2) {
                     int t[3] = {0, 0, 0};
                     t[ax3] = s3;
-                    mD += aD(t[0], t[1], t[2]) + aD(e1[0] + t[0], e1[1] + t[1], e1[2] + t[2]) +
-                          aD(e2[0] + t[0], e2[1] + t[1], e2[2] + t[2]) + aD(d[0] + t[0], d[1] + t[1], d[2] + t[2]);
-                    mA += aA(t[0], t[1], t[2]) + aA(e1[0] + t[0], e1[1] + t[1], e1[2] + t[2]) +
-                          aA(e2[0] + t[0], e2[1] + t[1], e2[2] + t[2]) + aA(d[0] + t[0], d[1] + t[1], d[2] + t[2]);
+                    m = m + (((A2(t[0], t[1], t[2]) + A2(e1[0] + t[0], e1[1] + t[1], e1[2] + t[2])) +
+                              A2(e2[0] + t[0], e2[1] + t[1], e2[2] + t[2])) +
+                             A2(d[0] + t[0], d[1] + t[1], d[2] + t[2]));
                 }
-                fD = (T(3.0 / 16.0) * nD + T(1.0 / 32.0) * mD) * (bU(d[0], d[1], d[2]) - u0);
-                fA = (T(3.0 / 16.0) * nA + T(1.0 / 32.0) * mA) * (bP(d[0], d[1], d[2]) - p0);
+                const P2<T> f = fma2(bc2<T>(T(3.0 / 16.0)), n, bc2<T>(T(1.0 / 32.0)) * m) * (B2(d[0], d[1], d[2]) - b00);
+                fD = f.d();
+                fA = f.a();
             };
             // Every flux is evaluated unconditionally and zeroed afterwards where
             // its stencil leaves the ring region, so that the compiler can share
@@ -437,26 +494,23 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             auto FZ = [&](int b, int f, int k, int dx, int dy) -> T {
                 return s_fz[PF_CHK(((b * 2 + f) * NFZ + k) * NT + tid + dy * AX + dx, 2 * 2 * NFZ * NT)];
             };
-            T s[2];
-#pragma unroll
-            for (int f = 0; f < 2; ++f) {
-                T a = (FI(f, 0, 0, 0) - FI(f, 0, -1, 0)) + (FI(f, 1, 0, 0) - FI(f, 1, 0, -1));
-                a += FZ(bufz_cur, f, 0, 0, 0) - FZ(bufz_prev, f, 0, 0, 0);
-                if (ISO) {
-                    // in-plane edges: own +x+y, +x-y; received -x-y from (-1,-1), -x+y from (-1,+1)
-                    a += (FI(f, 2, 0, 0) - FI(f, 2, -1, -1)) + (FI(f, 3, 0, 0) - FI(f, 3, -1, 1));
-                    // edges to the next plane (own) and from the previous plane (received):
-                    // +x-z = -(-x+z of (+1,0)), -x-z = -(+x+z of (-1,0)),
-                    // +y-z = -(-y+z of (0,+1)), -y-z = -(+y+z of (0,-1))
-                    a += (FZ(bufz_cur, f, 1, 0, 0) + FZ(bufz_cur, f, 2, 0, 0) + FZ(bufz_cur, f, 3, 0, 0) +
-                          FZ(bufz_cur, f, 4, 0, 0)) -
-                         (FZ(bufz_prev, f, 2, 1, 0) + FZ(bufz_prev, f, 1, -1, 0) + FZ(bufz_prev, f, 4, 0, 1) +
-                          FZ(bufz_prev, f, 3, 0, -1));
-                }
-                s[f] = a;
+            auto FI2 = [&](int k, int dx, int dy) -> P2<T> { return p2(FI(0, k, dx, dy), FI(1, k, dx, dy)); };
+            auto FZ2 = [&](int b, int k, int dx, int dy) -> P2<T> { return p2(FZ(b, 0, k, dx, dy), FZ(b, 1, k, dx, dy)); };
+            P2<T> a = (FI2(0, 0, 0) - FI2(0, -1, 0)) + (FI2(1, 0, 0) - FI2(1, 0, -1));
+            a = a + (FZ2(bufz_cur, 0, 0, 0) - FZ2(bufz_prev, 0, 0, 0));
+            if (ISO) {
+                // in-plane edges: own +x+y, +x-y; received -x-y from (-1,-1), -x+y from (-1,+1)
+                a = a + ((FI2(2, 0, 0) - FI2(2, -1, -1)) + (FI2(3, 0, 0) - FI2(3, -1, 1)));
+                // edges to the next plane (own) and from the previous plane (received):
+                // +x-z = -(-x+z of (+1,0)), -x-z = -(+x+z of (-1,0)),
+                // +y-z = -(-y+z of (0,+1)), -y-z = -(+y+z of (0,-1))
+                a = a + ((((FZ2(bufz_cur, 1, 0, 0) + FZ2(bufz_cur, 2, 0, 0)) + FZ2(bufz_cur, 3, 0, 0)) +
+                          FZ2(bufz_cur, 4, 0, 0)) -
+                         (((FZ2(bufz_prev, 2, 1, 0) + FZ2(bufz_prev, 1, -1, 0)) + FZ2(bufz_prev, 4, 0, 1)) +
+                          FZ2(bufz_prev, 3, 0, -1)));
             }
-            sD = s[0];
-            sA = s[1];
+            sD = a.d();
+            sA = a.a();
         };
 
         // ---- prologue ----
