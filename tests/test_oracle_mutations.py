@@ -16,6 +16,17 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "pf_oracle.c")
 
 # (name, text to find, replacement): each a mistake someone could make
+# The 2D and 3D rates spell the frozen-temperature terms alike; each thermal
+# mutation is applied inside one rate's block (its own comment and the three
+# lines below it), so that it hits exactly one of them.
+_THERMAL_BODY = (
+    "        double zeta = (j * h - q->yT - q->Vp * t) / q->lT;\n"
+    "        double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u + zeta;\n"
+    "        return ((L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * F2)) / (ac * ac) - SQ2 * ph * G) / F1;\n")
+THERMAL_BLOCKS = {
+    "2d": "        /* Eq. PF_a with the frozen-temperature functions F1, F2 */\n" + _THERMAL_BODY,
+    "3d": "        /* Eq. PF_a with the frozen-temperature functions F1, F2 (pulling along +y) */\n" + _THERMAL_BODY,
+}
 MUTATIONS = [
     ("lap21_weights_swapped", "return (2.0 / 3.0) * lap_10(f, i, j, h) + (1.0 / 3.0) * lap_01(f, i, j, h);",
      "return (1.0 / 3.0) * lap_10(f, i, j, h) + (2.0 / 3.0) * lap_01(f, i, j, h);"),
@@ -61,17 +72,19 @@ MUTATIONS = [
     ("tip_radius_no_window", "        w = rho;\n", "        w = w;\n"),
     ("tip_radius_combination_3d", "2.0 / (1.0 / rx + 1.0 / rz)", "0.5 * (rx + rz)"),
     ("tip_radius_transverse_axis", "ex[0] = ez[1] * epar[2] - ez[2] * epar[1];", "ex[0] = ez[1] * epar[2] + ez[2] * epar[1];"),
-    ("thermal_F1_dropped",
-     "return ((L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * F2)) / (ac * ac) - SQ2 * ph * G) / F1;",
-     "return ((L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * F2)) / (ac * ac) - SQ2 * ph * G);"),
-    ("thermal_F2_sign", "double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u + zeta;",
-     "double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u - zeta;"),
-    ("thermal_F1_sign", "double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u + zeta;",
-     "double F1 = 1.0 + (1.0 - q->k) * zeta, F2 = u + zeta;"),
-    ("thermal_pulling_sign", "double zeta = (j * h - q->yT - q->Vp * t) / q->lT;",
-     "double zeta = (j * h - q->yT + q->Vp * t) / q->lT;"),
-    ("thermal_row_offset", "double zeta = (j * h - q->yT - q->Vp * t) / q->lT;",
-     "double zeta = ((j + 1) * h - q->yT - q->Vp * t) / q->lT;"),
+    *[(f"thermal_{name}_{dim}", blk, blk.replace(old, new)) for dim, blk in THERMAL_BLOCKS.items() for name, old, new in [
+        ("F1_dropped",
+         "return ((L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * F2)) / (ac * ac) - SQ2 * ph * G) / F1;",
+         "return ((L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * F2)) / (ac * ac) - SQ2 * ph * G);"),
+        ("F2_sign", "double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u + zeta;",
+         "double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u - zeta;"),
+        ("F1_sign", "double F1 = 1.0 - (1.0 - q->k) * zeta, F2 = u + zeta;",
+         "double F1 = 1.0 + (1.0 - q->k) * zeta, F2 = u + zeta;"),
+        ("pulling_sign", "double zeta = (j * h - q->yT - q->Vp * t) / q->lT;",
+         "double zeta = (j * h - q->yT + q->Vp * t) / q->lT;"),
+        ("row_offset", "double zeta = (j * h - q->yT - q->Vp * t) / q->lT;",
+         "double zeta = ((j + 1) * h - q->yT - q->Vp * t) / q->lT;"),
+    ]],
     ("thermal_clock_frozen", "dpsi_dt_2d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, q->t0 + (double)s * dt)",
      "dpsi_dt_2d(q, &Ppsi, &Pphi, &PU, &Pg, rot, i, j, q->t0)"),
     ("t0_chain_rule_factor", "Pdphi.v[c] = dt * (1.0 - ph * ph) / SQ2 * Pnew.v[c];",
