@@ -125,8 +125,37 @@ def step(p: Params, rot, grain, psi, U, nsteps=1, want_rate=False):
     return (psi, U, rate) if want_rate else (psi, U)
 
 
+# Three-shell 3D combinations T_{s1,s2,s3} (Eq. tau_3D): the weights (s1, s2, s3)
+# of the <100>, <110> and <111> base discretizations, normalised by their sum.
+# Sec. 6.1 names these as the isotropic solutions of Eqs. Constrain_Lap1/2 (L),
+# Constrain_Div1/2 (D~) and the App. A constraints (G); "m1" spells the weight -1
+# of T_{0,4,-1}.  The paper runs no simulation with a <111> shell (Sec. 6.2.1,
+# pinning), so these serve the symbol pins only.
+COMBOS3 = {"120": (1, 2, 0), "201": (2, 0, 1), "04m1": (0, 4, -1), "441": (4, 4, 1), "561": (5, 6, 1),
+           "762": (7, 6, 2)}
+_SHELLS3 = ("100", "010", "001")
+
+
+def apply_combo(p: Params, fam: str, weights, a, b=None):
+    """T_{s1,s2,s3} of Eq. tau_3D for fam in {"lap", "div", "grad2"}: the
+    weighted mean of the three 3D base operators (each from the C oracle)."""
+    if fam not in ("lap", "div", "grad2") or len(weights) != 3 or sum(weights) == 0:
+        raise ValueError(f"bad combination {fam} {weights}")
+    tot = float(sum(weights))
+    out = np.zeros(_shape(p))
+    for w, sh in zip(weights, _SHELLS3):
+        if w != 0:
+            out += (w / tot) * apply(p, f"{fam}_{sh}", a, b)
+    return out
+
+
 def apply(p: Params, op: str, a, b=None, rot=None):
-    """Evaluate one operator at every cell (boundary rule of p)."""
+    """Evaluate one operator at every cell (boundary rule of p).  Besides the C
+    oracle's operators, op may name a three-shell combination "<fam>_c<key>"
+    with key in COMBOS3 (e.g. "lap_c441")."""
+    fam, _, key = op.partition("_c")
+    if key in COMBOS3 and op not in OPS:
+        return apply_combo(p, fam, COMBOS3[key], a, b)
     shape = _shape(p)
     a = _f64(a, shape)
     b = _f64(b, shape) if b is not None else None

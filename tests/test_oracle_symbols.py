@@ -198,3 +198,70 @@ def test_divergence_with_unit_alpha_is_laplacian(oracle, dim, div, lap):
     b = rng.normal(size=shape)
     one = np.ones(shape)
     assert np.allclose(oracle.apply(p, div, one, b), oracle.apply(p, lap, b), rtol=0, atol=1e-12)
+
+
+# Three-shell combinations of Eq. tau_3D that Sec. 6.1 names as isotropic
+# solutions (row f4: symbol tools only; no <111> scheme is simulated).
+COMBO_QUARTIC = {"lap": ("lin", 1.0, lambda k: q3(k, 2.0) / 12),
+                 "div": ("bil", 2.0, lambda k: 2 / 3 * q3(k, 2.0)),
+                 "grad2": ("quad", 1.0, lambda k: q3(k, 2.0) / 3)}
+
+
+@pytest.mark.parametrize("fam", ["lap", "div", "grad2"])
+@pytest.mark.parametrize("key", ["201", "04m1", "441", "561", "762"])
+def test_symbol_isotropic_combinations_3d(oracle, fam, key):
+    """L, D~ and G_{2,0,1}, _{0,4,-1}, _{4,4,1}, _{5,6,1}, _{7,6,2} (Sec. 6.1.1,
+    6.1.2, App. A): every such combination has the isotropic k^4 error of the
+    continuum-normalised form, (k^2)^2 / 12 for L and (2/3)(k^2)^2 for D~ as
+    for L_{1,2,0} and D~_{1,2,0}; G likewise with (k^2)^2 / 3."""
+    kind, c2, quartic = COMBO_QUARTIC[fam]
+    for d in dirs(3, 6):
+        k = tuple(KMAG * x for x in d)
+        S = symbol(oracle, 3, f"{fam}_c{key}", kind, k)
+        k2 = sum(x * x for x in k)
+        got = (S + c2 * k2) / k2 ** 2
+        assert abs(got.imag) < 1e-6
+        assert abs(got.real - quartic(k) / k2 ** 2) < 2e-3, (fam, key, d, got)
+
+
+def _quartic_about_kz_pi(O, op, d):
+    """k^4 coefficient of the Laplacian symbol about (0, 0, pi) along the
+    in-plane direction d, from S(r d, pi) = S0 + a r^2 + b r^4 at two radii."""
+    s0 = symbol(O, 3, op, "lin", (0.0, 0.0, math.pi)).real
+    r1, r2 = 0.04, 0.08
+    f1 = symbol(O, 3, op, "lin", (r1 * d[0], r1 * d[1], math.pi)).real - s0
+    f2 = symbol(O, 3, op, "lin", (r2 * d[0], r2 * d[1], math.pi)).real - s0
+    a, b = np.linalg.solve([[r1 ** 2, r1 ** 4], [r2 ** 2, r2 ** 4]], [f1, f2])
+    return a, b
+
+
+def test_cross_section_kz_pi_441_isotropic_120_not(oracle):
+    """Sec. 6.1.1 (Fig. of the 3D Laplacian symbols): L_{1,2,0} is isotropic only
+    in the cross section k_z = 0, L_{4,4,1} in both k_z = 0 and k_z = pi.
+    About (0, 0, pi) the exact symbols are (4 cx + 4 cy + 2 cx cy - 46) / 9 for
+    L_{4,4,1} and (2 cx cy - 14) / 3 for L_{1,2,0}: both fall off as -k^2/3,
+    the first with the isotropic quartic (k^2)^2 / 36, the second with
+    (kx^4 + ky^4 + 6 kx^2 ky^2) / 36, twice as large on the diagonal."""
+    ax, dg = (1.0, 0.0), (1 / math.sqrt(2), 1 / math.sqrt(2))
+    for op in ("lap_c441", "lap_c120"):
+        for d in (ax, dg, (math.cos(0.4), math.sin(0.4))):
+            a, _ = _quartic_about_kz_pi(oracle, op, d)
+            assert abs(a + 1 / 3) < 1e-3, (op, d, a)
+    b441 = [_quartic_about_kz_pi(oracle, "lap_c441", d)[1] for d in (ax, dg, (math.cos(0.4), math.sin(0.4)))]
+    assert np.allclose(b441, 1 / 36, rtol=0, atol=2e-3), b441
+    b_ax = _quartic_about_kz_pi(oracle, "lap_c120", ax)[1]
+    b_dg = _quartic_about_kz_pi(oracle, "lap_c120", dg)[1]
+    assert abs(b_ax - 1 / 36) < 2e-3 and abs(b_dg - 2 / 36) < 2e-3, (b_ax, b_dg)
+    assert abs(symbol(oracle, 3, "lap_c441", "lin", (0.0, 0.0, math.pi)).real + 4.0) < 1e-12
+    assert abs(symbol(oracle, 3, "lap_c120", "lin", (0.0, 0.0, math.pi)).real + 4.0) < 1e-12
+
+
+@pytest.mark.parametrize("fam", ["lap", "div", "grad2"])
+def test_combination_120_is_the_two_shell_scheme(oracle, fam):
+    """Eq. tau_3D with (1, 2, 0) reproduces the oracle's own S-bar_{1,2,0} operators."""
+    rng = np.random.default_rng(5)
+    n = 7
+    p = oracle.params(dim=3, nx=n, ny=n, nz=n, h=0.9, bc=oracle.BC_PERIODIC)
+    a, b = rng.normal(size=(n,) * 3), rng.normal(size=(n,) * 3)
+    bb = b if fam == "div" else None
+    assert np.allclose(oracle.apply(p, f"{fam}_c120", a, bb), oracle.apply(p, f"{fam}_120", a, bb), rtol=0, atol=1e-12)
