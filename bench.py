@@ -56,7 +56,7 @@ TRAFFIC = {
                 "sha256": "80863230f0d9aa5072ff497585917f2625b80d4e592830dda8fdbfbf7cb09a5a", "bytes": 155363072},
     # profiles/k_step3d_sbar120_f32_dendrite_256cube.md
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
-                   "sha256": "4ddef8d8116e529fedd75ae324c5437aefd82e1b627e2f18f4db4b6d5fc6c94e", "bytes": 262745088},
+                   "sha256": "c61f12b619648a147f6a766017b0050881de28269c5f3989897a750f80b1898c", "bytes": 262906368},
 }
 
 
