@@ -229,6 +229,13 @@ template <typename T, typename F> __device__ __forceinline__ V<T> appb_corner2(F
     const V<T> m2 = fma(dx, dx, dy * dy);
     return mk(M<T>::sqrt_(m2.x()), M<T>::sqrt_(m2.y()));
 }
+// App. B magnitude m at a flux point raised to at least half of the two-point
+// slope |d| s (s = 1 / |e|): the quotient slope / m, the unit normal's
+// component along e, then stays within [-2, 2]; it leaves that range only
+// where grad psi has no direction (reading R-A21G)
+template <typename T> __device__ __forceinline__ V<T> appb_floor2(V<T> m, V<T> d, T s) {
+    return mk(fmax(m.x(), T(0.5) * s * fabs(d.x())), fmax(m.y(), T(0.5) * s * fabs(d.y())));
+}
 // f / m per column with the guard on |grad psi| of the standard anti-trapping forms
 template <typename T> __device__ __forceinline__ V<T> guarded_div2(V<T> f, V<T> m, T hh) {
     const V<T> q = f * rcp2(m);
@@ -555,11 +562,20 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
                 // App. B: each anti-trapping flux divided by |grad psi| at its point;
                 // ps(dx, dy) = psi at columns (L + dx, R + dx), row q + dy
                 auto ps = [&](int dx, int dy) -> V<T> { return Pq[2 + dy].pat(dx); };
+                const T ihd = ih * T(0.70710678118654752440);  // 1 / |e| of the <11> fluxes
                 if (need_x)
-                    FXpA = guarded_div2<T>(FXpA, appb_face2<T>([&](int p, int t) { return ps(p, t); }, ih), hh);
-                FYpA = guarded_div2<T>(FYpA, appb_face2<T>([&](int p, int t) { return ps(t, p); }, ih), hh);
-                FPPA = guarded_div2<T>(FPPA, appb_corner2<T>([&](int p, int t) { return ps(p, t); }, ih), hh);
-                FMPA = guarded_div2<T>(FMPA, appb_corner2<T>([&](int p, int t) { return ps(p - 1, t); }, ih), hh);
+                    FXpA = guarded_div2<T>(
+                        FXpA, appb_floor2<T>(appb_face2<T>([&](int p, int t) { return ps(p, t); }, ih), b0.E() - p0c, ih),
+                        hh);
+                FYpA = guarded_div2<T>(
+                    FYpA, appb_floor2<T>(appb_face2<T>([&](int p, int t) { return ps(t, p); }, ih), b1.C() - p0c, ih), hh);
+                FPPA = guarded_div2<T>(
+                    FPPA, appb_floor2<T>(appb_corner2<T>([&](int p, int t) { return ps(p, t); }, ih), b1.E() - p0c, ihd),
+                    hh);
+                FMPA = guarded_div2<T>(
+                    FMPA,
+                    appb_floor2<T>(appb_corner2<T>([&](int p, int t) { return ps(p - 1, t); }, ih), b1.W() - p0c, ihd),
+                    hh);
             }
             sD = ((FXpD - mk(shup(FXpD.y()), FXpD.x())) + (FYpD - cFYm_D)) + ((FPPD + FMPD) - (cFDmm_D + cFDpm_D));
             sA = ((FXpA - mk(shup(FXpA.y()), FXpA.x())) + (FYpA - cFYm_A)) + ((FPPA + FMPA) - (cFDmm_A + cFDpm_A));

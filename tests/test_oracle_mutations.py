@@ -93,6 +93,11 @@ MUTATIONS = [
      "Pdphi.v[c] = dt / SQ2 * Pnew.v[c];"),
     ("t0_uses_new_phi", "                Pnew.v[c] = ph; /* phi^n on the left-hand side */",
      "                Pnew.v[c] = tanh((Ppsi.v[c] + dt * Pnew.v[c]) / SQ2);"),
+    ("at21_floor_dropped_face", "        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);\n", ""),
+    ("at21_floor_dropped_corner",
+     "        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / (SQ2 * h));\n", ""),
+    ("at21_floor_factor", "        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);",
+     "        m = fmax(m, 2.0 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);"),
     ("periodic_x_as_mirror", "if (bc == OR_BC_PERIODIC_X) return axis == 0 ? OR_BC_PERIODIC : OR_BC_MIRROR;",
      "if (bc == OR_BC_PERIODIC_X) return OR_BC_MIRROR;"),
 ]
@@ -119,6 +124,7 @@ def test_pins_catch_mutation(source, name, old, new):
                             os.path.join(ROOT, "tests", "test_oracle_step.py"),
                             os.path.join(ROOT, "tests", "test_oracle_tip_radius.py"),
                             os.path.join(ROOT, "tests", "test_oracle_directional.py"),
-                            os.path.join(ROOT, "tests", "test_oracle_time_level.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_time_level.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_at21_guard.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"mutation {name} survived every pin:\n{r.stdout[-2000:]}"
