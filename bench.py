@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS & %HBM peak, batched FP32 vs plain FP64 at stated error; p50/p99 latency"
 THETAS = tuple(range(0, 50, 5))
+PHYS_STEPS = 20000
 DS_THETAS = (0, 10, 20, 30, 40)
 DS_VP, DS_LT = 0.1, 2000.0
 OBS_EVERY = 100
@@ -211,6 +212,151 @@ def fp64_plain(stream, n=200, steps=2000):
             "tip_y": o["tip"][1]}
 
 
+# tip operating state of the orientation sweep: all three 2D schemes, FP32,
+# run to the sweep's full length; an FP64 run of one angle states the FP32 error
+PHYS_SCHEMES = ("S10", "S21", "SBAR21")
+PHYS_FP64_THETA = 30.0
+# Table 1: seconds per isothermal run of Sec. 4.3.2 on one Tesla P100 (context)
+PAPER_TABLE1_S = {"S10": 1359.0, "S21": 4612.0, "SBAR21": 3883.0}
+
+
+def run_batch(stream, ws, precision, obs_back=1000, keep=()):
+    """Step a batch of workloads (one group, autotuned tile) to ws[0].steps.
+    Returns (device ms of the steps, per-instance tip state at the end,
+    tile, {index: (psi, U)} for the indices in `keep`).  The tip state: growth
+    angle of the tip seen from the seed centre and of the tip's track over the
+    second half of the run (the direction of its displacement, measured like the
+    paper's alpha by tracking the tip), tip velocity over the last `obs_back`
+    steps, tip radius, sigma* and the tip Peclet number rho V / (2 D)."""
+    import math
+
+    import torch
+
+    from paper_2110_12448_gb300 import autotune
+    from paper_2110_12448_gb300 import native as N
+    tile, _ = autotune.tune(ws, precision)
+    sims = []
+    with torch.cuda.stream(stream):
+        for w in ws:
+            sims.append(N.Sim.from_workload(w, precision, stream=stream))
+            sims[-1].set_tile(*tile)
+    group = N.Group(len(sims), sum(N.Group.work_items(s) for s in sims), stream=stream)
+    for s in sims:
+        group.add(s)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    half = ws[0].steps // 2
+    mid = None
+    for k in (half, ws[0].steps - half - obs_back, obs_back):
+        a.record(stream)
+        group.step(k)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+        obs = [s.observe(0, allow_nonfinite=True) for s in sims]
+        if mid is None:
+            mid = [o["tip"] for o in obs]
+    rows = []
+    for w, s, o, t1 in zip(ws, sims, obs, mid):
+        ok = o["found"] and not o["nonfinite"]
+        tr = s.tip_radius(o, 0) if ok else {"rho": float("nan"), "sigma_star": float("nan")}
+        track = math.degrees(math.atan2(-(o["tip"][0] - t1[0]), o["tip"][1] - t1[1])) if ok else float("nan")
+        rows.append({"alpha_deg": o["angle_xy_deg"] if ok else float("nan"), "alpha_track_deg": track,
+                     "v_tip": o["v_tip"] if ok else float("nan"),
+                     "rho": tr["rho"], "sigma_star": tr["sigma_star"],
+                     "peclet": tr["rho"] * o["v_tip"] / (2 * w.D) if ok else float("nan"),
+                     "nonfinite": o["nonfinite"]})
+    fields = {i: sims[i].get_fields() for i in keep}
+    group.close()
+    for s in sims:
+        s.close()
+    return ms, rows, tile, fields
+
+
+def _table(thetas, rows):
+    r6 = lambda v: None if v != v else round(float(v), 6)  # noqa: E731
+    t = {"theta_deg": [float(x) for x in thetas]}
+    for key in ("alpha_deg", "alpha_track_deg", "v_tip", "rho", "sigma_star", "peclet"):
+        t[key] = [r6(r[key]) for r in rows]
+    t["alpha_over_alpha0"] = [None if (x == 0 or r["alpha_track_deg"] != r["alpha_track_deg"]) else
+                              r6(r["alpha_track_deg"] / x) for x, r in zip(thetas, rows)]
+    t["nonfinite_instances"] = sum(1 for r in rows if r["nonfinite"])
+    return t
+
+
+def orientation_physics(stream, n, steps):
+    """The orientation sweep's physical output (growth angle and tip velocity
+    vs crystal angle) for the three 2D schemes, FP32, after `steps` steps, and
+    FP32 against FP64 for one angle of S-bar_{2,1}."""
+    import math
+
+    import numpy as np
+
+    from paper_2110_12448_gb300 import synth
+    out = {"grid": f"10 x {n}^2", "steps": steps, "schemes": {}}
+    i30 = THETAS.index(int(PHYS_FP64_THETA))
+    for scheme in PHYS_SCHEMES:
+        ws = [synth.free_dendrite_2d(n, float(t), scheme, steps=steps) for t in THETAS]
+        ms, rows, tile, f32 = run_batch(stream, ws, "f32", keep=(i30,) if scheme == "SBAR21" else ())
+        out["schemes"][scheme] = dict(_table(THETAS, rows), glups=round(len(ws) * ws[0].n_cells * steps / ms / 1e6, 3),
+                                      device_s=round(ms / 1e3, 3), tile=list(tile))
+        if scheme == "SBAR21":
+            w64 = [synth.free_dendrite_2d(n, PHYS_FP64_THETA, scheme, steps=steps)]
+            ms64, rows64, _, f64 = run_batch(stream, w64, "f64", keep=(0,))
+            (p32, u32), (p64, u64) = f32[i30], f64[0]
+            s2 = math.sqrt(2.0)
+            r32 = rows[i30]
+            out["fp32_vs_fp64"] = {
+                "scheme": scheme, "theta_deg": PHYS_FP64_THETA, "steps": steps,
+                "max_abs_dphi": float(np.max(np.abs(np.tanh(p32.astype(np.float64) / s2) - np.tanh(p64 / s2)))),
+                "max_abs_dU": float(np.max(np.abs(u32.astype(np.float64) - u64))),
+                "v_tip_f32": r32["v_tip"], "v_tip_f64": rows64[0]["v_tip"],
+                "v_tip_rel_err": abs(r32["v_tip"] - rows64[0]["v_tip"]) / abs(rows64[0]["v_tip"]),
+                "alpha_deg_f32": r32["alpha_deg"], "alpha_deg_f64": rows64[0]["alpha_deg"],
+                "fp64_glups": round(w64[0].n_cells * steps / ms64 / 1e6, 3)}
+    return out
+
+
+def run_paper2d(args):
+    """The isothermal runs of Sec. 4.3.2 (781^2, h/W = 1.2, W/d0* = 16,
+    eps4 = 0.014, Omega = 0.43, k = 0.1, 20 345 steps): for each 2D scheme the
+    ten crystal angles as one batch, and one run alone, timed on the device;
+    with the tip state (growth angle, tip velocity, tip radius, sigma*) at the
+    paper's measuring time and the paper's seconds per run on a P100 beside."""
+    import torch
+
+    from paper_2110_12448_gb300 import synth
+    stream = torch.cuda.Stream()
+    clocks = Clocks(0)
+    res = {}
+    cells = 0
+    total_ms = 0.0
+    with clocks:
+        for scheme in PHYS_SCHEMES:
+            ws = [synth.paper_isothermal_2d(float(t), scheme) for t in THETAS]
+            ms, rows, tile, _ = run_batch(stream, ws, "f32")
+            one = [synth.paper_isothermal_2d(30.0, scheme)]
+            ms1, _, tile1, _ = run_batch(stream, one, "f32")
+            cells += len(ws) * ws[0].n_cells * ws[0].steps
+            total_ms += ms
+            res[scheme] = dict(_table(THETAS, rows), s_per_run_in_batch=round(ms / 1e3 / len(ws), 4),
+                               s_per_run_alone=round(ms1 / 1e3, 4), paper_p100_s_per_run=PAPER_TABLE1_S[scheme],
+                               tile_batch=list(tile), tile_alone=list(tile1),
+                               glups_batch=round(len(ws) * ws[0].n_cells * ws[0].steps / ms / 1e6, 3))
+    w = synth.paper_isothermal_2d(0.0, "SBAR21")
+    line = {"metric": METRIC, "value": cells / (total_ms / 1e3) / 1e9, "unit": "GLUPS", "n_gpus": 1,
+            "steps": w.steps, "warmup": 0, "ms_per_step": total_ms / (len(PHYS_SCHEMES) * w.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"isothermal runs of Sec. 4.3.2: {w.nx}^2, h/W = {w.h}, W/d0* = 16, eps4 = "
+                                   f"{w.eps4}, Omega = {-w.U0}, k = {w.k}, {w.steps} steps; 10 crystal angles x "
+                                   f"{len(PHYS_SCHEMES)} schemes (one batch per scheme), FP32 fields",
+                       "cells_per_gpu": 10 * w.n_cells},
+            "clocks": clocks.summary(), "paper_runs": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """Served stream: Poisson arrivals of mixed 2D/3D runs (sizes and step
     counts scaled by --serve-scale), continuous batching by an 80 % HBM
@@ -351,23 +497,18 @@ def run_native(args):
     per_step = sorted(a.elapsed_time(b) / c for a, b, c in pairs)
     ms, value = aggregate(ms, cells, args.steps, world, device="cuda")
 
-    # tip operating state per instance of the orientation sweep (growth angle
-    # vs crystal angle, tip velocity, tip radius and sigma*), measured on the
-    # device after the timed region
+    # latency of the device tip-radius fit (pf_tip_radius, host round trip
+    # included) on the sweep's instances after the timed region; the physical
+    # tip state is measured by orientation_physics at the sweep's full length
     sweep = None
     if args.workload == "sweep2d" and rank == 0:
-        sweep = {"theta_deg": [], "alpha_deg": [], "v_tip": [], "rho": [], "sigma_star": []}
         tr_s = []
-        for t, s in zip(THETAS, sims):
+        for s in sims:
             ob = s.observe(0)
             t0 = time.perf_counter()
-            tr = s.tip_radius(ob, 0)
+            s.tip_radius(ob, 0)
             tr_s.append(time.perf_counter() - t0)
-            for key, v in (("theta_deg", float(t)), ("alpha_deg", ob["angle_xy_deg"]), ("v_tip", ob["v_tip"]),
-                           ("rho", tr["rho"]), ("sigma_star", tr["sigma_star"])):
-                sweep[key].append(None if v != v else round(v, 6))
-        sweep["at_step"] = sims[0].steps_done
-        sweep["tip_radius_call_ms_p50"] = statistics.median(tr_s) * 1e3
+        sweep = {"tip_radius_call_ms_p50": statistics.median(tr_s) * 1e3, "at_step": sims[0].steps_done}
 
     # directional solidification: most advanced tip of each misorientation relative to
     # the isotherm T0 and the distance to the well-oriented grain's tip (Sec. 4.2)
@@ -439,9 +580,11 @@ def run_native(args):
                 "tile": list(tile) if tile else None,
                 "gpu_launches": n_launch + 2 * len(sims) * (args.steps // OBS_EVERY)}
         if sweep:
-            line["directional" if args.workload == "directional2d" else "orientation_sweep"] = sweep
+            line["directional" if args.workload == "directional2d" else "tip_radius_call"] = sweep
         if world == 1 and not args.no_fp64:
             line["fp64_plain"] = fp64_plain(stream)
+        if world == 1 and not args.no_physics and args.workload == "sweep2d":
+            line["orientation_physics"] = orientation_physics(stream, args.n, PHYS_STEPS)
         if world == 1 and not args.no_cpu and args.workload == "sweep2d":
             line["cpu_baseline"] = cpu_baseline(args.n, args.scheme)
         print(json.dumps(line), flush=True)
@@ -460,7 +603,7 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--scheme", default="SBAR21", choices=["SBAR21", "S21", "S10", "SBAR120", "S100"])
     ap.add_argument("--n", type=int, default=None, help="grid side (default 1024 in 2D, 256 in 3D)")
-    ap.add_argument("--workload", default="sweep2d", choices=["sweep2d", "dendrite3d", "poly2d", "directional2d", "serve"])
+    ap.add_argument("--workload", default="sweep2d", choices=["sweep2d", "dendrite3d", "poly2d", "directional2d", "serve", "paper2d"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
     ap.add_argument("--window", type=float, default=20.0, help="serve: arrival window in seconds")
     ap.add_argument("--serve-scale", type=float, default=0.25, help="serve: scale of sides and step counts")
@@ -468,6 +611,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
     ap.add_argument("--no-tune", action="store_true", help="use the default tile instead of the autotuner's")
+    ap.add_argument("--no-physics", action="store_true",
+                    help="skip the orientation sweep's tip-state runs (three schemes to 2e4 steps, FP64 check)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -479,6 +624,8 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "paper2d":
+        return run_paper2d(args)
     return run_native(args)
 
 

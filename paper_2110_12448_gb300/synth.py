@@ -131,6 +131,33 @@ def orientation_sweep_2d(n: int = 1024, scheme: str = "SBAR21", steps: int = 200
     return [free_dendrite_2d(n, float(t), scheme, steps) for t in thetas]
 
 
+A1 = 5.0 * math.sqrt(2.0) / 8.0  # a1 of d0 = a1 W / lambda (Sec. 2.1)
+
+
+def paper_isothermal_2d(theta_deg: float = 0.0, scheme: str = "SBAR21", W_d0: float = 16.0, h: float = 1.2,
+                        eps4: float = 0.014, k: float = 0.1, Omega: float = 0.43, side_d0: float = 1.5e4,
+                        seed_d0: float = 50.0, t_d0: float = 1.5e6) -> Workload:
+    """The isothermal runs behind Sec. 4.3.2 (Figs. of alpha/alpha0 and sigma*
+    vs alpha0, and the scheme timings of Table 1): a circular seed of radius
+    50 d0* at the centre of a square box of side 1.5e4 d0* with no-flux
+    walls, melt at scaled supersaturation Omega = 0.43, W/d0* = 16, h/W = 1.2,
+    eps4 = 0.014, k = 0.1 (the paper's k throughout), dt = 0.8 h^2 / (4 D),
+    run to t = 1.5e6 d0*^2 / D.  d0* = d0 (1 - (1-k) Omega) / k with
+    d0 = a1 W / lambda fixes lambda; D = a2 lambda; U0 = -Omega.
+    Defaults: a 781^2 grid and 20 345 steps."""
+    lam = W_d0 * A1 * (1.0 - (1.0 - k) * Omega) / k
+    D = A2 * lam
+    dt = 0.8 * h * h / (4.0 * D)
+    d0s = 1.0 / W_d0  # d0* in units of W
+    n = int(round(side_d0 * d0s / h))
+    steps = int(round(t_d0 * d0s * d0s / D / dt))
+    c = ((n - 1) / 2 * h, (n - 1) / 2 * h, 0.0)
+    seeds = np.array([[c[0], c[1], 0.0, seed_d0 * d0s]])
+    return Workload(2, n, n, 1, h, dt, k, eps4, lam, D, -Omega, scheme, seeds, np.zeros(1, np.int16),
+                    rot2d(theta_deg).reshape(1, 9), np.array([c]), steps,
+                    f"paper_isothermal_2d_{n}^2_theta{theta_deg:g}_{scheme}")
+
+
 def free_dendrite_3d(n: int = 256, scheme: str = "SBAR120", steps: int = 10000, seed: int = SEED_BASE + 2,
                      **phys) -> Workload:
     p = _physics_2d(**phys)
