@@ -54,7 +54,7 @@ def dist_env():
 TRAFFIC = {
     # profiles/k_step2d_sbar21_f32_orientation_sweep_10x1024sq.md
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
-                "sha256": "80863230f0d9aa5072ff497585917f2625b80d4e592830dda8fdbfbf7cb09a5a", "bytes": 155363072},
+                "sha256": "2c3054b08514666c37bee63e29a1212ad130f7c85e7b23bda1d8a4aeabc6be40", "bytes": 154640640},
     # profiles/k_step3d_sbar120_f32_dendrite_256cube.md
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
                    "sha256": "c61f12b619648a147f6a766017b0050881de28269c5f3989897a750f80b1898c", "bytes": 262906368},
