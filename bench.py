@@ -274,6 +274,21 @@ def run_batch(stream, ws, precision, obs_back=1000, keep=()):
     return ms, rows, tile, fields
 
 
+def ivantsov_peclet_2d(omega):
+    """Peclet number P = rho V / (2 D) of the 2D Ivantsov needle at
+    supersaturation omega: omega = sqrt(pi P) exp(P) erfc(sqrt(P)), by
+    bisection (the left side increases with P)."""
+    import math
+    lo, hi = 1e-9, 50.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if math.sqrt(math.pi * mid) * math.exp(mid) * math.erfc(math.sqrt(mid)) < omega:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
 def _table(thetas, rows):
     r6 = lambda v: None if v != v else round(float(v), 6)  # noqa: E731
     t = {"theta_deg": [float(x) for x in thetas]}
@@ -294,7 +309,8 @@ def orientation_physics(stream, n, steps):
     import numpy as np
 
     from paper_2110_12448_gb300 import synth
-    out = {"grid": f"10 x {n}^2", "steps": steps, "schemes": {}}
+    w0 = synth.free_dendrite_2d(n, 0.0, "SBAR21", steps=steps)
+    out = {"grid": f"10 x {n}^2", "steps": steps, "ivantsov_peclet": ivantsov_peclet_2d(-w0.U0), "schemes": {}}
     i30 = THETAS.index(int(PHYS_FP64_THETA))
     for scheme in PHYS_SCHEMES:
         ws = [synth.free_dendrite_2d(n, float(t), scheme, steps=steps) for t in THETAS]
@@ -352,7 +368,7 @@ def run_paper2d(args):
                                    f"{w.eps4}, Omega = {-w.U0}, k = {w.k}, {w.steps} steps; 10 crystal angles x "
                                    f"{len(PHYS_SCHEMES)} schemes (one batch per scheme), FP32 fields",
                        "cells_per_gpu": 10 * w.n_cells},
-            "clocks": clocks.summary(), "paper_runs": res}
+            "clocks": clocks.summary(), "ivantsov_peclet": ivantsov_peclet_2d(-w.U0), "paper_runs": res}
     print(json.dumps(line), flush=True)
     return 0
 
