@@ -373,6 +373,51 @@ def run_paper2d(args):
     return 0
 
 
+# Table 2: seconds per isothermal 3D run of Sec. 6.2.2 on one Tesla P100 (context)
+PAPER_TABLE2_S = {"S100": 5445.0, "SBAR120": 25155.0}
+PAPER3D_THETAS = (0.0, 15.0, 30.0)
+
+
+def run_paper3d(args):
+    """The isothermal 3D runs of Sec. 6.2.2 (h/W = 1.2, W/d0* = 16,
+    eps4 = 0.014, Omega = 0.25, k = 0.1, crystal turned about z by
+    alpha0 = 0, 15, 30 deg, to t = 1.5e6 d0*^2 / D) in a 320^3 cube (the
+    paper's cube of side 9.6e4 d0* does not fit one GPU), one run at a time:
+    growth angle by tip tracking, tip radii, sigma*, seconds per run beside
+    Table 2."""
+    import torch
+
+    from paper_2110_12448_gb300 import synth
+    stream = torch.cuda.Stream()
+    clocks = Clocks(0)
+    n = args.n
+    res = {}
+    cells = 0
+    total_ms = 0.0
+    with clocks:
+        for scheme in ("S100", "SBAR120"):
+            ws = [synth.paper_isothermal_3d(t, scheme, n=n) for t in PAPER3D_THETAS]
+            rows, secs = [], []
+            for w in ws:
+                ms, r, tile, _ = run_batch(stream, [w], "f32")
+                rows += r
+                secs.append(round(ms / 1e3, 3))
+                cells += w.n_cells * w.steps
+                total_ms += ms
+            res[scheme] = dict(_table(PAPER3D_THETAS, rows), s_per_run=secs,
+                               paper_p100_s_per_run=PAPER_TABLE2_S[scheme], tile=list(tile))
+    w = synth.paper_isothermal_3d(0.0, "SBAR120", n=n)
+    line = {"metric": METRIC, "value": cells / (total_ms / 1e3) / 1e9, "unit": "GLUPS", "n_gpus": 1,
+            "steps": w.steps, "warmup": 0, "ms_per_step": total_ms / (2 * len(PAPER3D_THETAS) * w.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"isothermal 3D runs of Sec. 6.2.2 in a {n}^3 cube: h/W = {w.h}, W/d0* = 16, "
+                                   f"eps4 = {w.eps4}, Omega = {-w.U0}, k = {w.k}, {w.steps} steps; alpha0 = 0, 15, "
+                                   f"30 deg about z x S_100, S-bar_120, FP32 fields", "cells_per_gpu": w.n_cells},
+            "clocks": clocks.summary(), "paper_runs": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """Served stream: Poisson arrivals of mixed 2D/3D runs (sizes and step
     counts scaled by --serve-scale), continuous batching by an 80 % HBM
@@ -618,8 +663,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--scheme", default="SBAR21", choices=["SBAR21", "S21", "S10", "SBAR120", "S100"])
-    ap.add_argument("--n", type=int, default=None, help="grid side (default 1024 in 2D, 256 in 3D)")
-    ap.add_argument("--workload", default="sweep2d", choices=["sweep2d", "dendrite3d", "poly2d", "directional2d", "serve", "paper2d"])
+    ap.add_argument("--n", type=int, default=None,
+                    help="grid side (default 1024 in 2D, 256 for dendrite3d, 320 for paper3d)")
+    ap.add_argument("--workload", default="sweep2d", choices=["sweep2d", "dendrite3d", "poly2d", "directional2d", "serve", "paper2d", "paper3d"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
     ap.add_argument("--window", type=float, default=20.0, help="serve: arrival window in seconds")
     ap.add_argument("--serve-scale", type=float, default=0.25, help="serve: scale of sides and step counts")
@@ -633,7 +679,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.n is None:
-        args.n = 256 if args.workload == "dendrite3d" else 1024
+        args.n = {"dendrite3d": 256, "paper3d": 320}.get(args.workload, 1024)
     if args.workload == "dendrite3d" and args.scheme in ("SBAR21", "S21", "S10"):
         args.scheme = {"S10": "S100"}.get(args.scheme, "SBAR120")
     if args.impl == "reference":
@@ -642,6 +688,8 @@ def main():
         return run_serve(args)
     if args.workload == "paper2d":
         return run_paper2d(args)
+    if args.workload == "paper3d":
+        return run_paper3d(args)
     return run_native(args)
 
 
