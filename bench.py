@@ -216,6 +216,7 @@ def fp64_plain(stream, n=200, steps=2000):
 # run to the sweep's full length; an FP64 run of one angle states the FP32 error
 PHYS_SCHEMES = ("S10", "S21", "SBAR21")
 PHYS_FP64_THETA = 30.0
+PHYS_FP64_BATCH_STEPS = 200  # timed steps of each scheme's ten-instance batch in FP64
 # Table 1: seconds per isothermal run of Sec. 4.3.2 on one Tesla P100 (context)
 PAPER_TABLE1_S = {"S10": 1359.0, "S21": 4612.0, "SBAR21": 3883.0}
 
@@ -289,6 +290,36 @@ def ivantsov_peclet_2d(omega):
     return 0.5 * (lo + hi)
 
 
+def batch_rate(stream, ws, precision, steps, warm=5):
+    """GLUPS of one batch of workloads (one group, autotuned tile) over `steps`
+    timed steps after `warm` untimed ones."""
+    import torch
+
+    from paper_2110_12448_gb300 import autotune
+    from paper_2110_12448_gb300 import native as N
+    tile, _ = autotune.tune(ws, precision)
+    sims = []
+    with torch.cuda.stream(stream):
+        for w in ws:
+            sims.append(N.Sim.from_workload(w, precision, stream=stream))
+            sims[-1].set_tile(*tile)
+    group = N.Group(len(sims), sum(N.Group.work_items(s) for s in sims), stream=stream)
+    for s in sims:
+        group.add(s)
+    group.step(warm)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    group.step(steps)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    group.close()
+    for s in sims:
+        s.close()
+    return sum(w.n_cells for w in ws) * steps / ms / 1e6
+
+
 def _table(thetas, rows):
     r6 = lambda v: None if v != v else round(float(v), 6)  # noqa: E731
     t = {"theta_deg": [float(x) for x in thetas]}
@@ -316,7 +347,8 @@ def orientation_physics(stream, n, steps):
         ws = [synth.free_dendrite_2d(n, float(t), scheme, steps=steps) for t in THETAS]
         ms, rows, tile, f32 = run_batch(stream, ws, "f32", keep=(i30,) if scheme == "SBAR21" else ())
         out["schemes"][scheme] = dict(_table(THETAS, rows), glups=round(len(ws) * ws[0].n_cells * steps / ms / 1e6, 3),
-                                      device_s=round(ms / 1e3, 3), tile=list(tile))
+                                      device_s=round(ms / 1e3, 3), tile=list(tile),
+                                      fp64_batch_glups=round(batch_rate(stream, ws, "f64", PHYS_FP64_BATCH_STEPS), 3))
         if scheme == "SBAR21":
             w64 = [synth.free_dendrite_2d(n, PHYS_FP64_THETA, scheme, steps=steps)]
             ms64, rows64, _, f64 = run_batch(stream, w64, "f64", keep=(0,))
