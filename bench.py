@@ -184,7 +184,29 @@ def cpu_baseline(n, scheme, max_seconds=20.0):
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": w.n_cells * steps / dt / 1e9, "unit": "GLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{steps} steps of one {w.nx}x{w.ny} instance (alpha0={THETAS[3]} deg) of the 10, FP64, {dt:.1f} s"}
+            "sample": f"{steps} steps of one {w.nx}x{w.ny} instance (alpha0={THETAS[3]} deg) of the 10, FP64, {dt:.1f} s",
+            "single_thread": cpu_baseline_1thread(n, scheme)}
+
+
+def cpu_baseline_1thread(n, scheme, steps=2):
+    """The same oracle sample on one host thread (a fresh process, so that
+    OpenMP starts with OMP_NUM_THREADS=1): `steps` steps of the same instance."""
+    import subprocess
+    import sys
+    code = ("import sys, time; sys.path.insert(0, {root!r}); import bench; from oracle import oracle as O; "
+            "w = bench.workloads({n}, {scheme!r})[3]; "
+            "p = O.params(nx=w.nx, ny=w.ny, scheme={code}, h=w.h, dt=w.dt, k=w.k, eps4=w.eps4, lam=w.lam, D=w.D); "
+            "psi, U, g = O.init_seeds(p, w.U0, w.seeds, w.seed_grain); O.step(p, w.rots, g, psi, U, 1); "
+            "t0 = time.perf_counter(); O.step(p, w.rots, g, psi, U, {steps}); "
+            "print(w.n_cells * {steps} / (time.perf_counter() - t0) / 1e9)").format(
+        root=ROOT, n=n, scheme=scheme, steps=steps, code={"SBAR21": 2, "S21": 1, "S10": 0}[scheme])
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
+                           capture_output=True, text=True, timeout=120, check=True)
+        v = float(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal: the all-core figure stands
+        return {"error": str(e)[:200]}
+    return {"value": v, "unit": "GLUPS", "cores": 1, "sample": f"{steps} steps of the same instance, one thread"}
 
 
 def fp64_plain(stream, n=200, steps=2000):
