@@ -124,6 +124,7 @@ static inline double* PA(const pad_t* p, int i, int j, int k) {
 /* fill interior from src and ghosts by the boundary rule */
 static void pad_fill(pad_t* p, const double* src, int bc) {
     int zl = p->dim == 3 ? -2 : 0, zh = p->dim == 3 ? p->nz + 2 : 1;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = zl; k < zh; ++k)
         for (int j = -2; j < p->ny + 2; ++j)
             for (int i = -2; i < p->nx + 2; ++i) {
@@ -665,9 +666,10 @@ int or_step(const or_params* q, int n_grains, const double* rot, const int16_t* 
         /* pass 0 + 1: ghosts, phi = tanh(psi / sqrt 2) (Eq. 1) */
         pad_fill(&Ppsi, psi, q->bc);
         pad_fill(&PU, U, q->bc);
+#pragma omp parallel for schedule(static)
         for (size_t c = 0; c < padN; ++c) Pphi.v[c] = tanh(Ppsi.v[c] / SQ2);
         /* pass 2: d psi/dt and psi' at every cell */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
         for (int kk = 0; kk < nz; ++kk)
             for (int j = 0; j < q->ny; ++j)
                 for (int i = 0; i < q->nx; ++i) {
@@ -682,6 +684,7 @@ int or_step(const or_params* q, int n_grains, const double* rot, const int16_t* 
          * phi^n in place of phi' (T0) */
         if (q->time_level == OR_T0) {
             pad_fill(&Pnew, dpsi, q->bc);
+#pragma omp parallel for schedule(static)
             for (size_t c = 0; c < padN; ++c) {
                 double ph = Pphi.v[c];
                 Pdphi.v[c] = dt * (1.0 - ph * ph) / SQ2 * Pnew.v[c];
@@ -689,6 +692,7 @@ int or_step(const or_params* q, int n_grains, const double* rot, const int16_t* 
             }
         } else {
             pad_fill(&Pnew, psin, q->bc);
+#pragma omp parallel for schedule(static)
             for (size_t c = 0; c < padN; ++c) {
                 double phn = tanh(Pnew.v[c] / SQ2);
                 Pdphi.v[c] = phn - Pphi.v[c];
@@ -697,12 +701,13 @@ int or_step(const or_params* q, int n_grains, const double* rot, const int16_t* 
         }
         /* alpha of the U equation: 1 - phi (D term) in Pomp, and
          * (1 + (1-k) U) d phi/dt / sqrt 2 (anti-trapping) in Palpha */
+#pragma omp parallel for schedule(static)
         for (size_t c = 0; c < padN; ++c) {
             Pomp.v[c] = 1.0 - Pphi.v[c];
             Palpha.v[c] = (1.0 + (1.0 - k) * PU.v[c]) * Pdphi.v[c] / (SQ2 * dt);
         }
         /* pass 4: U' (Eq. PF_b, conservative form of reading T1) */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
         for (int kk = 0; kk < nz; ++kk)
             for (int j = 0; j < q->ny; ++j)
                 for (int i = 0; i < q->nx; ++i) {
