@@ -166,7 +166,7 @@ WORKLOAD_TEXT = {
 }
 
 
-def cpu_baseline(n, scheme, max_seconds=20.0):
+def cpu_baseline(n, scheme, max_seconds=15.0, max_steps=400):
     """FP64 oracle on the host cores, bounded sample: one instance, a few steps."""
     import numpy as np
     from oracle import oracle as O
@@ -178,7 +178,7 @@ def cpu_baseline(n, scheme, max_seconds=20.0):
     O.step(p, w.rots, g, psi, U, 1)  # warm
     steps = 0
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < max_seconds and steps < 50:
+    while time.perf_counter() - t0 < max_seconds and steps < max_steps:
         psi, U = O.step(p, w.rots, g, psi, U, 1)
         steps += 1
     dt = time.perf_counter() - t0
