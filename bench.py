@@ -211,7 +211,11 @@ def cpu_baseline_1thread(n, scheme, steps=2):
 
 def fp64_plain(stream, n=200, steps=2000):
     """Comparator: the plain single-instance FP64 step (200 x 200 free
-    dendrite, one launch per step through pf_step), GLUPS and us/step."""
+    dendrite, one launch per step through pf_step), GLUPS and us/step (mean,
+    and p50/p99 over individually timed steps); and the same instance stepped
+    through a one-member group replayed from a CUDA graph."""
+    import statistics
+
     import torch
 
     from paper_2110_12448_gb300 import native as N
@@ -228,9 +232,30 @@ def fp64_plain(stream, n=200, steps=2000):
     b.synchronize()
     ms = a.elapsed_time(b)
     o = s.observe(0)
+    # per-step times: one event pair around each of 200 single steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(200)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        s.step(1)
+        e1.record(stream)
+    ev[-1][1].synchronize()
+    per = sorted(e0.elapsed_time(e1) * 1e3 for e0, e1 in ev)
+    # the same instance through a one-member group (persistent launch + CUDA graph)
+    g = N.Group(1, N.Group.work_items(s), stream=stream)
+    g.add(s)
+    g.step(10)
+    a.record(stream)
+    g.step(steps)
+    b.record(stream)
+    b.synchronize()
+    ms_graph = a.elapsed_time(b)
+    g.close()
     s.close()
     return {"value": w.n_cells * steps / (ms / 1e3) / 1e9, "unit": "GLUPS", "us_per_step": ms * 1e3 / steps,
-            "workload": f"free dendrite 2D {n}x{n}, SBAR21, FP64, {steps} steps, one launch per step",
+            "us_per_step_p50": statistics.median(per), "us_per_step_p99": per[int(0.99 * (len(per) - 1))],
+            "graph_us_per_step": ms_graph * 1e3 / steps,
+            "workload": f"free dendrite 2D {n}x{n}, SBAR21, FP64, {steps} steps, one launch per step "
+                        f"(graph: the same instance in a one-member group, replayed from a CUDA graph)",
             "tip_y": o["tip"][1]}
 
 
