@@ -212,6 +212,19 @@ int pf_set_fields(pf_sim* s, const void* psi_host, const void* U_host);
 int pf_get_step(pf_sim* s, int64_t* step);
 int pf_set_step(pf_sim* s, int64_t step);
 
+/* Moving frame for directional solidification (Sec. 4.3.3 and 6.2.3 pull
+ * the sample along +y; the paper does not say how its boxes follow the tip):
+ * moves the state `rows` cells toward -y, as if the box had been moved up by
+ * rows*h.  Cell (x, y, z) takes the values of (x, y + rows, z); the vacated
+ * top rows continue the last row: psi decreasing by h per row (a signed
+ * distance into the melt), U and the grain index copied.  The frozen
+ * temperature is kept in place: yT decreases by rows*h, so the next step sees
+ * the same temperature at every material point.  Later observations are in
+ * the moved frame (the tips remembered for V move with it).  1 <= rows < ny.
+ * Synchronises the stream.  Errors: PF_ERR_INVALID (rows out of range),
+ * PF_ERR_STATE (the handle belongs to a group), PF_ERR_CUDA. */
+int pf_shift_frame(pf_sim* s, int rows);
+
 /* Device addresses of the current psi, U (precision of the handle) and the
  * int16 grain map; valid until the next pf_step / pf_group_step. */
 int pf_device_fields(pf_sim* s, void** psi, void** U, void** grain);

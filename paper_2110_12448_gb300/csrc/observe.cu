@@ -338,6 +338,31 @@ template <typename T> __global__ void k_fill(T* __restrict__ p, T v, long long n
         p[c] = v;
 }
 
+// Frame shift by `rows` cells toward -y: dst(x, y, z) = src(x, y + rows, z)
+// for y + rows < ny; the vacated top rows take the last row's value plus
+// `slope` per row beyond it (psi: -h, a signed distance continued into the
+// melt; U and the grain index: 0, a copy of the last row).  src and dst do
+// not overlap.
+template <typename T>
+__global__ void k_shift_rows(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny, int nz, int rows,
+                             double slope) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx);
+        const long long yz = c / nx;
+        const int y = (int)(yz % ny), z = (int)(yz / ny);
+        const int ys = y + rows;
+        const long long plane = (long long)z * ny;
+        if (ys < ny) {
+            dst[c] = src[(plane + ys) * nx + x];
+        } else {
+            const T top = src[(plane + ny - 1) * nx + x];
+            // product and sum rounded separately (no contraction): top - k h exactly as written
+            dst[c] = slope == 0.0 ? top : (T)__dadd_rn((double)top, __dmul_rn(slope, (double)(ys - (ny - 1))));
+        }
+    }
+}
+
 }  // namespace
 
 // Fixed scratch for pf_observe_fields_noalloc: OBS_BLOCKS block partials and
@@ -405,6 +430,21 @@ cudaError_t launch_init_seeds(int prec, int dim, int nx, int ny, int nz, double 
     else
         k_init_seeds<double><<<grid, block, 0, st>>>(dim, nx, ny, nz, h, U0, seeds, n_seeds,
                                                      static_cast<double*>(psi), static_cast<double*>(U), grain);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_rows(int kind, const void* src, void* dst, int nx, int ny, int nz, int rows, double slope,
+                              cudaStream_t st) {
+    const int grid = 4 * 152, block = 256;
+    if (kind == 0)
+        k_shift_rows<float><<<grid, block, 0, st>>>(static_cast<const float*>(src), static_cast<float*>(dst), nx, ny, nz,
+                                                    rows, slope);
+    else if (kind == 1)
+        k_shift_rows<double><<<grid, block, 0, st>>>(static_cast<const double*>(src), static_cast<double*>(dst), nx, ny,
+                                                     nz, rows, slope);
+    else
+        k_shift_rows<int16_t><<<grid, block, 0, st>>>(static_cast<const int16_t*>(src), static_cast<int16_t*>(dst), nx,
+                                                      ny, nz, rows, 0.0);
     return cudaGetLastError();
 }
 

@@ -592,6 +592,30 @@ int pf_set_step(pf_sim* s, int64_t step) {
     return PF_OK;
 }
 
+int pf_shift_frame(pf_sim* s, int rows) {
+    if (!s || rows <= 0 || rows >= s->p.ny) return PF_ERR_INVALID;
+    if (s->group) return PF_ERR_STATE;
+    const int nx = s->p.nx, ny = s->p.ny, nz = s->p.dim == 3 ? s->p.nz : 1;
+    const int cur = (int)(s->step & 1), oth = cur ^ 1;
+    const int kind = s->p.precision == PF_F64 ? 1 : 0;
+    const size_t b = s->L.N * s->L.esz;
+    // grain index through the free U buffer (N int16 fit in N field values)
+    CK(launch_shift_rows(2, s->grain, s->U[oth], nx, ny, nz, rows, 0.0, s->st));
+    CK(cudaMemcpyAsync(s->grain, s->U[oth], s->L.N * sizeof(int16_t), cudaMemcpyDeviceToDevice, s->st));
+    CK(launch_shift_rows(kind, s->psi[cur], s->psi[oth], nx, ny, nz, rows, -s->p.h, s->st));
+    CK(launch_shift_rows(kind, s->U[cur], s->U[oth], nx, ny, nz, rows, 0.0, s->st));
+    CK(cudaMemcpyAsync(s->psi[cur], s->psi[oth], b, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(s->U[cur], s->U[oth], b, cudaMemcpyDeviceToDevice, s->st));
+    // the frame moved up by rows h: the isotherms sit rows h lower in it
+    s->p.yT -= rows * s->p.h;
+    InstRec r = make_rec(s, 0);
+    CK(cudaMemcpyAsync(s->rec, &r, sizeof(r), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    // remembered tip positions follow the frame, so the next V is continuous
+    for (size_t slot = 0; slot < s->have_prev.size(); ++slot) s->prev[4 * slot + 2] -= rows * s->p.h;
+    return PF_OK;
+}
+
 int pf_device_fields(pf_sim* s, void** psi, void** U, void** grain) {
     if (!s) return PF_ERR_INVALID;
     const int cur = (int)(s->step & 1);

@@ -172,5 +172,8 @@ struct SeedDev {
 cudaError_t launch_init_seeds(int prec, int dim, int nx, int ny, int nz, double h, double U0, const SeedDev* seeds,
                               int n_seeds, void* psi, void* U, int16_t* grain, cudaStream_t st);
 cudaError_t launch_fill(int prec, void* p, double v, long long n, cudaStream_t st);
+// frame shift of one field toward -y (kind 0: float, 1: double, 2: int16 grain index)
+cudaError_t launch_shift_rows(int kind, const void* src, void* dst, int nx, int ny, int nz, int rows, double slope,
+                              cudaStream_t st);
 
 }  // namespace pf

@@ -95,6 +95,7 @@ def lib():
                 "pf_set_fields": (C.c_int, [vp, vp, vp]),
                 "pf_get_step": (C.c_int, [vp, P(i64)]),
                 "pf_set_step": (C.c_int, [vp, i64]),
+                "pf_shift_frame": (C.c_int, [vp, C.c_int]),
                 "pf_device_fields": (C.c_int, [vp, P(vp), P(vp), P(vp)]),
                 "pf_set_tile": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
                 "pf_get_tile": (C.c_int, [vp, P(C.c_int), P(C.c_int), P(C.c_int)]),
@@ -294,6 +295,11 @@ class Sim:
 
     def set_step(self, n: int):
         _check(lib().pf_set_step(self.h, int(n)), "pf_set_step")
+
+    def shift_frame(self, rows: int):
+        """Move the state `rows` cells toward -y (a box that follows the tip
+        upward); the frozen temperature stays put (pf_shift_frame)."""
+        _check(lib().pf_shift_frame(self.h, int(rows)), "pf_shift_frame")
 
     def device_fields(self):
         a, b, c = C.c_void_p(), C.c_void_p(), C.c_void_p()

@@ -214,3 +214,55 @@ def test_group_graph_clock_3d(native):
     gp, gu = s.get_fields()
     op, ou = O.step(oracle_params(w, step=50), rots, g, psi, U, 35)
     assert rel_err(gp, op) < 35e-12 and rel_err(gu, ou) < 35e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_shift_frame_moves_state_and_keeps_temperature(native, prec):
+    """pf_shift_frame: cell (x, y) takes (x, y + m); the top m rows continue
+    the last row (psi minus h per row, U and grain copied), bit for bit; and
+    the next step equals the oracle's step on the shifted state with the
+    isotherm yT moved down by m h (FP64: 1e-12 relative)."""
+    w, psi, U, g, rots = ds_state(21, 90, 53)
+    if prec == "f32":
+        psi, U = psi.astype(np.float32), U.astype(np.float32)
+    s = gpu_sim(native, w, prec, g, rots, psi, U, step=41)
+    s.step(3)
+    p3, u3 = s.get_fields()
+    g3 = s.get_grain_index()
+    m = 7
+    s.shift_frame(m)
+    p4, u4 = s.get_fields()
+    g4 = s.get_grain_index()
+    assert np.array_equal(p4[:-m], p3[m:]) and np.array_equal(u4[:-m], u3[m:]) and np.array_equal(g4[:-m], g3[m:])
+    steps_up = np.arange(1, m + 1)[:, None] * w.h
+    want_top = (p3[-1].astype(np.float64)[None, :] - steps_up).astype(p3.dtype)
+    assert np.array_equal(p4[-m:], want_top)
+    assert np.array_equal(u4[-m:], np.repeat(u3[-1:], m, axis=0))
+    assert np.array_equal(g4[-m:], np.repeat(g3[-1:], m, axis=0))
+    assert s.steps_done == 44
+    if prec == "f64":
+        s.step(1)
+        gp, gu = s.get_fields()
+        op, ou = O.step(oracle_params(w, step=44, yT=w.yT - m * w.h), rots, g4, p4, u4, 1)
+        assert rel_err(gp, op) < 1e-12 and rel_err(gu, ou) < 1e-12
+
+
+def test_shift_frame_3d_and_invalid_calls(native):
+    w = synth.free_dendrite_3d(24, steps=1)
+    w.nx, w.ny, w.nz = 20, 26, 12
+    w.seeds = np.array([[10.0, 10.0, 5.0, 4.0]])
+    s = native.Sim.from_workload(w, "f32")
+    s.step(2)
+    p0, u0 = s.get_fields()  # [z, y, x]
+    s.shift_frame(5)
+    p1, u1 = s.get_fields()
+    assert np.array_equal(p1[:, :-5, :], p0[:, 5:, :]) and np.array_equal(u1[:, :-5, :], u0[:, 5:, :])
+    assert np.array_equal(u1[:, -5:, :], np.repeat(u0[:, -1:, :], 5, axis=1))
+    for bad in (0, -1, w.ny):
+        with pytest.raises(native.PfError):
+            s.shift_frame(bad)
+    g = native.Group(2, native.Group.work_items(s))
+    g.add(s)
+    with pytest.raises(native.PfError):
+        s.shift_frame(1)  # a group member: PF_ERR_STATE
+    g.close()
