@@ -222,6 +222,60 @@ def directional_2d(nx: int = 256, ny: int = 512, theta_deg: float = 0.0, scheme:
                     bc_x=1, thermal=1, Vp=Vp, lT=lT, yT=yT, psi_init=psi, U_init=U)
 
 
+def paper_directional_2d(theta_deg: float = 0.0, scheme: str = "SBAR21", W_d0: float = 110.4, h: float = 1.2,
+                         eps4: float = 0.014, k: float = 0.1, dt_s: float = 1e-5, D_um2_s: float = 1270.0,
+                         Vp_um_s: float = 86.0, G_K_cm: float = 19.0, m_K_wt: float = -3.02, c_inf_wt: float = 1.3,
+                         Lx_um: float = 191.0, Ly_um: float = 491.0, finger_W: float = 150.0, finger_R: float = 5.0,
+                         delta0: float = 0.03, steps: int = 400000) -> Workload:
+    """The 2D directional-solidification runs of Sec. 4.3.3 (SCN-1.3 wt%
+    acetone, Vp = 86 um/s, G = 19 K/cm, W/d0 = 110.4, h/W = 1.2, dt = 1e-5 s,
+    eps4 = 0.014, k = 0.1, m = -3.02 K/wt%, D = 1270 um^2/s, a 191 x 491 um^2
+    box periodic in x) in the model's units.  The paper does not give W (nor
+    Gamma); the Delta t rule of its isothermal runs, dt = 0.8 h^2 / (4 D), with
+    the stated dt fixes it: W = 0.210 um, d0 = 1.90 nm (its 3D runs give the
+    same d0 by the 3D rule).  Then lambda = a1 W/d0, D~ = a2 lambda,
+    tau0 = dt / dt~, Vp~ = Vp tau0 / W and lT~ = (|m| c_inf (1-k)/k) / (G W).
+
+    Dendrite tips grow just below the liquidus of c_inf (zeta = 1, where
+    U = -1 is in equilibrium), lT~ = 88 600 W above the solidus isotherm T0
+    (zeta = 0), so the box is placed there: a planar front at y0 = Ly/8,
+    `delta0` below the liquidus (zeta = 1 - delta0, yT = y0 - lT~ (1 - delta0)),
+    with a finger of length `finger_W` and radius
+    `finger_R` (W; psi = the signed distance to a capsule) along the crystal
+    axis, turned by theta from the pulling axis, in a melt at c_inf (U = -1
+    everywhere).  The finger
+    grows into the dendrite whose tip the runs follow (pf_shift_frame keeps it
+    inside the box)."""
+    lam = A1 * W_d0
+    D = A2 * lam
+    dt = 0.8 * h * h / (4.0 * D)
+    tau0 = dt_s / dt
+    W_um = math.sqrt(D_um2_s * tau0 / D)
+    Vp = Vp_um_s * tau0 / W_um
+    lT = abs(m_K_wt) * c_inf_wt * (1.0 - k) / k / (G_K_cm * 1e-4) / W_um  # Delta T0 / G in units of W
+    nx = int(round(Lx_um / (h * W_um)))
+    ny = int(round(Ly_um / (h * W_um)))
+    x = np.arange(nx) * h
+    y = np.arange(ny) * h
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    y0 = ny * h / 8.0
+    xc = nx * h / 2.0
+    t = math.radians(theta_deg)
+    ax, ay = -math.sin(t), math.cos(t)  # crystal axis (+y turned counter-clockwise by theta)
+    Lx = nx * h
+    dist = np.full(X.shape, np.inf)
+    for img in (-Lx, 0.0, Lx):  # the capsule and its periodic images: psi stays periodic in x
+        s_ = np.clip((X - xc - img) * ax + (Y - y0) * ay, 0.0, finger_W)  # nearest point of the finger's axis
+        dist = np.minimum(dist, np.hypot(X - (xc + img + s_ * ax), Y - (y0 + s_ * ay)))
+    psi = np.maximum(-(Y - y0), finger_R - dist)  # signed distance to front + capsule
+    U = np.full((ny, nx), -1.0)
+    c = (xc, y0, 0.0)
+    return Workload(2, nx, ny, 1, h, dt, k, eps4, lam, D, -1.0, scheme,
+                    np.array([[xc, -100.0 * h, 0.0, h]]), np.zeros(1, np.int16), rot2d(theta_deg).reshape(1, 9),
+                    np.array([c]), steps, f"paper_directional_2d_{nx}x{ny}_theta{theta_deg:g}_{scheme}",
+                    bc_x=1, thermal=1, Vp=Vp, lT=lT, yT=y0 - lT * (1.0 - delta0), psi_init=psi, U_init=U)
+
+
 def place_seeds(rng: np.random.Generator, dim: int, extent, n_seeds: int, r: float, tries: int = 1000):
     """Rejection sampling: centres >= 2r from the walls and >= 4r apart;
     after `tries` failures the radius shrinks by 0.8 and placement restarts."""
