@@ -185,8 +185,11 @@ int pf_step(pf_sim* s, int64_t n);
  * the grain with psi >= 0 whose neighbour along the lattice axis closest to
  * the growth axis has psi < 0, the linearly interpolated psi = 0 crossing
  * with the largest projection on the growth axis (the crystal axis with the
- * largest +y component); ties go to the lowest cell index.  Returns
- * PF_ERR_NONFINITE (with *out filled) when NaN/Inf cells exist. */
+ * largest +y component); ties go to the lowest cell index.  g = -2: every
+ * cell, with +y as the growth axis: the most advanced interface along the
+ * pulling axis, which Sec. 4.3.3 and 6.2.3 track in directional
+ * solidification (unlike a tilted crystal axis it is periodic in x).
+ * Returns PF_ERR_NONFINITE (with *out filled) when NaN/Inf cells exist. */
 int pf_observe(pf_sim* s, int grain, pf_obs* out);
 
 /* Synchronise the stream and measure the tip radius of grain g (-1 as in

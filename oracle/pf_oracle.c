@@ -874,15 +874,18 @@ int or_init_seeds(const or_params* q, double U0, int n_seeds, const double* seed
  * grain = -1 uses every cell with grain 0's centre and axes. */
 int or_observe(const or_params* q, int n_grains, const double* rot, const double* centres, const int16_t* grain,
                const double* psi, const double* U, int g, double* out) {
-    if (check_params(q) || g < -1 || g >= n_grains) return -1;
+    if (check_params(q) || g < -2 || g >= n_grains) return -1;
     const int nz = q->dim == 3 ? q->nz : 1, dim = q->dim;
     const int gg = g < 0 ? 0 : g;
     const double* R = rot + 9 * gg;
     const double* cg = centres + 3 * gg;
     /* growth axis: the crystal axis (+-column of R) with the largest
-     * y component; ties keep the first in the order (+a0, -a0, +a1, ...) */
+     * y component; ties keep the first in the order (+a0, -a0, +a1, ...).
+     * g = -2: the pulling axis +y (the most advanced interface along y that
+     * Sec. 4.3.3 and 6.2.3 track in directional solidification) */
     double d[3] = {0, 0, 0}, best = -INFINITY;
-    for (int a = 0; a < dim; ++a)
+    if (g == -2) d[1] = 1.0;
+    for (int a = 0; a < dim && g != -2; ++a)
         for (int s = 1; s >= -1; s -= 2) {
             double yc = s * R[1 * 3 + a];
             if (yc > best) {

@@ -161,7 +161,7 @@ struct pf_sim {
     int bx, by, sweep, n_work, grid;
     bool work_dirty;
     std::vector<WorkItem> work_h;
-    std::vector<int> have_prev;       // per grain + 1 (index 0 = global)
+    std::vector<int> have_prev;       // per grain + 2 (index 0: pulling axis, 1: global)
     std::vector<double> prev;         // t, x, y, z per slot
     pf_group* group;
 };
@@ -341,8 +341,8 @@ int pf_create(const pf_params* p, void* dev_mem, size_t bytes, void* stream, pf_
     s->centres_h[2] = p->dim == 3 ? (p->nz - 1) * 0.5 * p->h : 0.0;
     s->step = 0;
     s->group = nullptr;
-    s->have_prev.assign(2, 0);
-    s->prev.assign(8, 0.0);
+    s->have_prev.assign(3, 0);
+    s->prev.assign(12, 0.0);
     default_tile(s);
     int rc;
     if ((rc = upload_rot(s)) != PF_OK) { delete s; return rc; }
@@ -372,8 +372,8 @@ int pf_set_grains(pf_sim* s, int n_grains, const double* rot9, const double* cen
             s->centres_h[3 * g + 2] = s->p.dim == 3 ? (s->p.nz - 1) * 0.5 * s->p.h : 0.0;
         }
     }
-    s->have_prev.assign(n_grains + 1, 0);
-    s->prev.assign(4 * (n_grains + 1), 0.0);
+    s->have_prev.assign(n_grains + 2, 0);
+    s->prev.assign(4 * (n_grains + 2), 0.0);
     s->work_dirty = true;  // the instance record carries the grain count
     return upload_rot(s);
 }
@@ -436,20 +436,25 @@ int pf_step(pf_sim* s, int64_t n) {
 }
 
 int pf_observe(pf_sim* s, int grain, pf_obs* out) {
-    if (!s || !out || grain < -1 || grain >= s->n_grains) return PF_ERR_INVALID;
+    if (!s || !out || grain < -2 || grain >= s->n_grains) return PF_ERR_INVALID;
     const int dim = s->p.dim;
     const int gg = grain < 0 ? 0 : grain;
     const double* R = &s->rot_h[9 * gg];
-    // growth axis: crystal axis (+- column of R) with the largest y component
+    // growth axis: crystal axis (+- column of R) with the largest y component,
+    // or +y itself (grain -2: the pulling axis of directional solidification)
     double d[3] = {0, 0, 0}, best = -INFINITY;
-    for (int a = 0; a < dim; ++a)
-        for (int sg = 1; sg >= -1; sg -= 2) {
-            const double yc = sg * R[3 + a];
-            if (yc > best) {
-                best = yc;
-                for (int q = 0; q < 3; ++q) d[q] = q < dim ? sg * R[q * 3 + a] : 0.0;
+    if (grain == -2) {
+        d[1] = 1.0;
+    } else {
+        for (int a = 0; a < dim; ++a)
+            for (int sg = 1; sg >= -1; sg -= 2) {
+                const double yc = sg * R[3 + a];
+                if (yc > best) {
+                    best = yc;
+                    for (int q = 0; q < 3; ++q) d[q] = q < dim ? sg * R[q * 3 + a] : 0.0;
+                }
             }
-        }
+    }
     int ea = 0;
     for (int a = 1; a < dim; ++a)
         if (std::fabs(d[a]) > std::fabs(d[ea])) ea = a;
@@ -464,7 +469,7 @@ int pf_observe(pf_sim* s, int grain, pf_obs* out) {
     a.nx = s->p.nx;
     a.ny = s->p.ny;
     a.nz = dim == 3 ? s->p.nz : 1;
-    a.grain_filter = grain;
+    a.grain_filter = grain < 0 ? -1 : grain;
     a.h = s->p.h;
     a.k = s->p.k;
     for (int q = 0; q < 3; ++q) {
@@ -487,7 +492,7 @@ int pf_observe(pf_sim* s, int grain, pf_obs* out) {
     out->found = r.tip_index >= 0 ? 1 : 0;
     out->tip_index = r.tip_index;
     out->tip_score = r.tip_index >= 0 ? r.score : -INFINITY;
-    const int slot = grain + 1;
+    const int slot = grain + 2;
     if (r.tip_index >= 0) {
         for (int q = 0; q < 3; ++q) out->tip[q] = r.tip[q];
         const double rx = r.tip[0] - a.cg[0], ry = r.tip[1] - a.cg[1], rz = dim == 3 ? r.tip[2] - a.cg[2] : 0.0;

@@ -169,7 +169,7 @@ def test_observe_matches_oracle(native, prec):
     psi, U = s.get_fields()
     gmap = s.get_grain_index()
     po = oracle_params(w)
-    for g in range(-1, w.n_grains):
+    for g in range(-2, w.n_grains):  # -2: the pulling axis +y
         a = s.observe(g)
         b = O.observe(po, w.rots, w.centres, gmap, psi.astype(np.float64), U.astype(np.float64), g)
         assert a["found"] == int(b["found"])

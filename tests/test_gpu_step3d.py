@@ -107,7 +107,7 @@ def test_init_and_observe_3d(native, prec):
     s.step(20)
     psi, U = s.get_fields()
     po = oracle_params(w)
-    for g in range(-1, w.n_grains):
+    for g in range(-2, w.n_grains):  # -2: the pulling axis +y
         a = s.observe(g)
         b = O.observe(po, w.rots, w.centres, gg, psi.astype(np.float64), U.astype(np.float64), g)
         assert a["found"] == int(b["found"]) and a["tip_index"] == int(b["tip_index"])

@@ -166,3 +166,28 @@ def test_periodic_x_commutes_with_shifts_3d(scheme):
     for m in (1, 6):
         b = O.step(p, rot, np.roll(g, m, 2), np.roll(psi, m, 2), np.roll(U, m, 2), 2)
         assert np.array_equal(np.roll(a[0], m, 2), b[0]) and np.array_equal(np.roll(a[1], m, 2), b[1])
+
+
+def test_observe_pulling_axis_tip_on_a_tilted_front(oracle):
+    """Observation g = -2 takes the pulling axis +y as the growth axis (the most
+    advanced interface along y, tracked in Sec. 4.3.3 and 6.2.3); g = -1 the
+    crystal axis.  On the planar front psi = Y0 + s (x - x0) - y (linear, so
+    the interpolated crossing is exact: y = Y0 + s (x - x0)) rising to the
+    right, with the crystal turned 30 deg counter-clockwise (axis
+    (-1/2, sqrt3/2)), the +y tip is the last column and the crystal-axis tip
+    the first, whose projection falls as -1/2 + s sqrt3/2 < 0 per unit x."""
+    nx, ny, h, Y0, x0, slope = 24, 20, 0.8, 7.3, 4.0, 0.2
+    p = oracle.params(dim=2, nx=nx, ny=ny, h=h)
+    y, x = np.mgrid[0:ny, 0:nx] * h
+    psi = (Y0 + slope * (x - x0)) - y
+    U = np.zeros_like(psi)
+    t = np.radians(30.0)
+    rot = np.array([[np.cos(t), -np.sin(t), 0.0], [np.sin(t), np.cos(t), 0.0], [0.0, 0.0, 1.0]]).reshape(1, 9)
+    centres = np.array([[nx * h / 2, ny * h / 2, 0.0]])
+    g = np.zeros((ny, nx), np.int16)
+    o2 = oracle.observe(p, rot, centres, g, psi, U, g=-2)
+    o1 = oracle.observe(p, rot, centres, g, psi, U, g=-1)
+    xe = (nx - 1) * h
+    assert abs(o2["tip_x"] - xe) < 1e-12 and abs(o2["tip_y"] - (Y0 + slope * (xe - x0))) < 1e-12
+    assert abs(o2["score"] - (o2["tip_y"] - centres[0, 1])) < 1e-12
+    assert abs(o1["tip_x"] - 0.0) < 1e-12 and abs(o1["tip_y"] - (Y0 + slope * (0.0 - x0))) < 1e-12

@@ -98,6 +98,7 @@ MUTATIONS = [
      "        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / (SQ2 * h));\n", ""),
     ("at21_floor_factor", "        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);",
      "        m = fmax(m, 2.0 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);"),
+    ("observe_pulling_axis_as_x", "    if (g == -2) d[1] = 1.0;", "    if (g == -2) d[0] = 1.0;"),
     ("periodic_x_as_mirror", "if (bc == OR_BC_PERIODIC_X) return axis == 0 ? OR_BC_PERIODIC : OR_BC_MIRROR;",
      "if (bc == OR_BC_PERIODIC_X) return OR_BC_MIRROR;"),
 ]
