@@ -497,6 +497,84 @@ def run_paper3d(args):
     return 0
 
 
+PAPER_DS_THETAS = (0.0, 30.0)
+PAPER_DS_STEPS = 4000000
+
+
+def run_paper_ds2d(args):
+    """The 2D directional runs of Sec. 4.3.3 in model units (synth.
+    paper_directional_2d): one dendrite per box at alpha0 = 0 and 30 deg for
+    the three 2D schemes, the box following the tip (pf_shift_frame keeps the
+    most advanced interface along +y, observed with pf_observe(-2), between 50
+    and 60% of its height).  Reports the steady tip undercooling
+    Delta = 1 - zeta_tip (mean and spread over the last quarter of the run),
+    the tip speed against Vp, and delta(alpha0) = (Delta(alpha0) - Delta(0)) lT,
+    the distance between the tips that Fig. 2D_DS compares across schemes."""
+    import torch
+
+    from paper_2110_12448_gb300 import native as N
+    from paper_2110_12448_gb300 import synth
+    stream = torch.cuda.Stream()
+    steps = args.steps if args.steps != 2000 else PAPER_DS_STEPS
+    chunk = min(100000, max(1, steps // 20))  # observations (and frame moves) per run: about 20 or more
+    clocks = Clocks(0)
+    res = {}
+    cells = 0
+    total_ms = 0.0
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with clocks:
+        for scheme in ("SBAR21", "S21", "S10"):
+            res[scheme] = {}
+            for th in PAPER_DS_THETAS:
+                w = synth.paper_directional_2d(th, scheme)
+                with torch.cuda.stream(stream):
+                    s = N.Sim.from_workload(w, "f32", stream=stream)
+                s.set_tile(64, 1, 8)  # one instance: short sweeps fill the GPU
+                off, done, hist = 0.0, 0, []
+                while done < steps:
+                    k = min(chunk, steps - done)
+                    a.record(stream)
+                    s.step(k)
+                    b.record(stream)
+                    b.synchronize()
+                    total_ms += a.elapsed_time(b)
+                    done += k
+                    o = s.observe(-2)
+                    yt = o["tip"][1]
+                    zeta = (yt - (w.yT - off) - w.Vp * done * w.dt) / w.lT
+                    hist.append((done, yt + off, 1.0 - zeta))
+                    if yt > 0.6 * w.ny * w.h:
+                        rows = int((yt - 0.5 * w.ny * w.h) / w.h)
+                        s.shift_frame(rows)
+                        off += rows * w.h
+                cells += w.n_cells * steps
+                q = max(1, len(hist) // 4)  # the last quarter of the observations
+                last = [d for _, _, d in hist[-q:]]
+                (n1, y1, _), (n2, y2, _) = hist[max(0, len(hist) - q - 1)], hist[-1]
+                v = (y2 - y1) / ((n2 - n1) * w.dt) if n2 > n1 else float("nan")
+                res[scheme][f"{th:g}"] = {"Delta": statistics.fmean(last), "Delta_spread": max(last) - min(last),
+                                          "v_tip": v, "Vp": w.Vp,
+                                          "frame_moved_W": off}
+                s.close()
+            base = res[scheme]["0"]["Delta"]
+            for th in PAPER_DS_THETAS[1:]:
+                r = res[scheme][f"{th:g}"]
+                r["delta_W"] = (r["Delta"] - base) * w.lT
+                r["delta_um"] = r["delta_W"] * math.sqrt(1270.0 * (1e-5 / w.dt) / w.D)  # W in um (synth's mapping)
+    w = synth.paper_directional_2d(0.0)
+    line = {"metric": METRIC, "value": cells / (total_ms / 1e3) / 1e9, "unit": "GLUPS", "n_gpus": 1, "steps": steps,
+            "warmup": 0, "ms_per_step": total_ms / (3 * len(PAPER_DS_THETAS) * steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"directional runs of Sec. 4.3.3 in model units: {w.nx}x{w.ny}, Vp = {w.Vp:.4f} "
+                                   f"W/tau0, lT = {w.lT:.0f} W, h/W = {w.h}, eps4 = {w.eps4}, k = {w.k}, periodic x, "
+                                   f"box following the tip, alpha0 = 0 and 30 deg x three schemes, {steps} steps each, "
+                                   f"FP32 fields", "cells_per_gpu": w.n_cells},
+            "clocks": clocks.summary(), "paper_ds_runs": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """Served stream: Poisson arrivals of mixed 2D/3D runs (sizes and step
     counts scaled by --serve-scale), continuous batching by an 80 % HBM
@@ -744,7 +822,7 @@ def main():
     ap.add_argument("--scheme", default="SBAR21", choices=["SBAR21", "S21", "S10", "SBAR120", "S100"])
     ap.add_argument("--n", type=int, default=None,
                     help="grid side (default 1024 in 2D, 256 for dendrite3d, 320 for paper3d)")
-    ap.add_argument("--workload", default="sweep2d", choices=["sweep2d", "dendrite3d", "poly2d", "directional2d", "serve", "paper2d", "paper3d"])
+    ap.add_argument("--workload", default="sweep2d", choices=["sweep2d", "dendrite3d", "poly2d", "directional2d", "serve", "paper2d", "paper3d", "paper_ds2d"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
     ap.add_argument("--window", type=float, default=20.0, help="serve: arrival window in seconds")
     ap.add_argument("--serve-scale", type=float, default=0.25, help="serve: scale of sides and step counts")
@@ -769,6 +847,8 @@ def main():
         return run_paper2d(args)
     if args.workload == "paper3d":
         return run_paper3d(args)
+    if args.workload == "paper_ds2d":
+        return run_paper_ds2d(args)
     return run_native(args)
 
 
