@@ -99,6 +99,20 @@ MUTATIONS = [
     ("at21_floor_factor", "        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);",
      "        m = fmax(m, 2.0 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);"),
     ("observe_pulling_axis_as_x", "    if (g == -2) d[1] = 1.0;", "    if (g == -2) d[0] = 1.0;"),
+    ("at_std2_no_normalisation", "((V2(b, i + dx, j + dy) - V2(b, i, j)) / h) / sqrt(m2);",
+     "((V2(b, i + dx, j + dy) - V2(b, i, j)) / h);"),
+    ("at_std3_one_sided_alpha", "s += 0.5 * (F3(a, e[0], e[1], e[2]) + F3(a, 0, 0, 0)) * ((F3(b,",
+     "s += F3(a, 0, 0, 0) * ((F3(b,"),
+    ("lap120_weights", "(1.0 / 3.0) * lap_100(f, i, j, k, h) + (2.0 / 3.0) * lap_010(f, i, j, k, h)",
+     "(2.0 / 3.0) * lap_100(f, i, j, k, h) + (1.0 / 3.0) * lap_010(f, i, j, k, h)"),
+    ("psi_update_half_dt", "psin[c] = psi[c] + dt * r;", "psin[c] = psi[c] + 0.5 * dt * r;"),
+    ("U_denominator_sign", "(1.0 + (1.0 - k) * u) * dph) / (1.0 + k - (1.0 - k) * phn);",
+     "(1.0 + (1.0 - k) * u) * dph) / (1.0 + k + (1.0 - k) * phn);"),
+    ("G_term_dropped_2d",
+     "    return (L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * u)) / (ac * ac) - SQ2 * ph * G;\n}\n\n"
+     "static double dpsi_dt_3d(",
+     "    return (L + N + SQ2 * (ph - q->lambda * (1.0 - ph * ph) * u)) / (ac * ac);\n}\n\nstatic double dpsi_dt_3d("),
+    ("growth_axis_lowest_y", "            if (yc > best) {", "            if (-yc > best) {"),
     ("periodic_x_as_mirror", "if (bc == OR_BC_PERIODIC_X) return axis == 0 ? OR_BC_PERIODIC : OR_BC_MIRROR;",
      "if (bc == OR_BC_PERIODIC_X) return OR_BC_MIRROR;"),
 ]
