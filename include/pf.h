@@ -219,13 +219,20 @@ int pf_set_step(pf_sim* s, int64_t step);
  * the sample along +y; the paper does not say how its boxes follow the tip):
  * moves the state `rows` cells toward -y, as if the box had been moved up by
  * rows*h.  Cell (x, y, z) takes the values of (x, y + rows, z); the vacated
- * top rows continue the last row: psi decreasing by h per row (a signed
- * distance into the melt), U and the grain index copied.  The frozen
+ * top rows are melt the frame moves into: psi continues the last row,
+ * decreasing by h per row (a signed distance into the melt); U continues the
+ * steady far field of a frame moving at Vp through the melt,
+ * U0 + (U_last - U0) exp(-Vp k h / D) k rows beyond the last row (with no
+ * frozen temperature, Vp = 0: a copy of the last row); the grain index is
+ * copied.  The frozen
  * temperature is kept in place: yT decreases by rows*h, so the next step sees
  * the same temperature at every material point.  Later observations are in
  * the moved frame (the tips remembered for V move with it).  1 <= rows < ny.
- * Synchronises the stream.  Errors: PF_ERR_INVALID (rows out of range),
- * PF_ERR_STATE (the handle belongs to a group), PF_ERR_CUDA. */
+ * Synchronises the stream.  Errors: PF_ERR_INVALID (rows out of range, or a
+ * frozen temperature that the moved frame would put where pf_create refuses
+ * it: F1 = 1 - (1-k) zeta below 0.05 on the grid, or the explicit step
+ * unstable at 1/F1, at the current step; nothing is moved), PF_ERR_STATE
+ * (the handle belongs to a group), PF_ERR_CUDA. */
 int pf_shift_frame(pf_sim* s, int rows);
 
 /* Device addresses of the current psi, U (precision of the handle) and the

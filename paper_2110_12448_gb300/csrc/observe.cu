@@ -339,13 +339,14 @@ template <typename T> __global__ void k_fill(T* __restrict__ p, T v, long long n
 }
 
 // Frame shift by `rows` cells toward -y: dst(x, y, z) = src(x, y + rows, z)
-// for y + rows < ny; the vacated top rows take the last row's value plus
-// `slope` per row beyond it (psi: -h, a signed distance continued into the
-// melt; U and the grain index: 0, a copy of the last row).  src and dst do
-// not overlap.
+// for y + rows < ny.  The vacated top rows, k rows beyond the last one, take
+// (mode 0) the last row's value, (mode 1) the last row's value plus a k (psi:
+// a = -h, a signed distance continued into the melt) or (mode 3) the value
+// a + (last - a) exp(-b k) (U: the steady far field a + C exp(-Vp y / D) ahead
+// of a front pulled at Vp, b = Vp h / D).  src and dst do not overlap.
 template <typename T>
-__global__ void k_shift_rows(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny, int nz, int rows,
-                             double slope) {
+__global__ void k_shift_rows(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny, int nz, int rows, int mode,
+                             double a, double b) {
     const long long n = (long long)nx * ny * nz;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx);
@@ -358,7 +359,10 @@ __global__ void k_shift_rows(const T* __restrict__ src, T* __restrict__ dst, int
         } else {
             const T top = src[(plane + ny - 1) * nx + x];
             // product and sum rounded separately (no contraction): top - k h exactly as written
-            dst[c] = slope == 0.0 ? top : (T)__dadd_rn((double)top, __dmul_rn(slope, (double)(ys - (ny - 1))));
+            const double kk = (double)(ys - (ny - 1));
+            dst[c] = mode == 0   ? top
+                     : mode == 1 ? (T)__dadd_rn((double)top, __dmul_rn(a, kk))
+                                 : (T)(a + ((double)top - a) * exp(-b * kk));
         }
     }
 }
@@ -433,18 +437,18 @@ cudaError_t launch_init_seeds(int prec, int dim, int nx, int ny, int nz, double 
     return cudaGetLastError();
 }
 
-cudaError_t launch_shift_rows(int kind, const void* src, void* dst, int nx, int ny, int nz, int rows, double slope,
-                              cudaStream_t st) {
+cudaError_t launch_shift_rows(int kind, const void* src, void* dst, int nx, int ny, int nz, int rows, int mode,
+                              double a, double b, cudaStream_t st) {
     const int grid = 4 * 152, block = 256;
     if (kind == 0)
         k_shift_rows<float><<<grid, block, 0, st>>>(static_cast<const float*>(src), static_cast<float*>(dst), nx, ny, nz,
-                                                    rows, slope);
+                                                    rows, mode, a, b);
     else if (kind == 1)
         k_shift_rows<double><<<grid, block, 0, st>>>(static_cast<const double*>(src), static_cast<double*>(dst), nx, ny,
-                                                     nz, rows, slope);
+                                                     nz, rows, mode, a, b);
     else
         k_shift_rows<int16_t><<<grid, block, 0, st>>>(static_cast<const int16_t*>(src), static_cast<int16_t*>(dst), nx,
-                                                      ny, nz, rows, 0.0);
+                                                      ny, nz, rows, 0, 0.0, 0.0);
     return cudaGetLastError();
 }
 

@@ -600,15 +600,26 @@ int pf_set_step(pf_sim* s, int64_t step) {
 int pf_shift_frame(pf_sim* s, int rows) {
     if (!s || rows <= 0 || rows >= s->p.ny) return PF_ERR_INVALID;
     if (s->group) return PF_ERR_STATE;
+    if (s->p.thermal == PF_FROZEN_GRADIENT) {
+        // the moved frame must pass the creation checks (F1 = 1 - (1-k) zeta >= 0.05 over the grid,
+        // explicit step stable at 1 / F1min) at the current step; zeta only falls later
+        pf_params q = s->p;
+        q.yT = s->p.yT - rows * s->p.h + s->p.Vp * s->p.dt * (double)s->step;
+        if (!valid_params(&q)) return PF_ERR_INVALID;
+    }
     const int nx = s->p.nx, ny = s->p.ny, nz = s->p.dim == 3 ? s->p.nz : 1;
     const int cur = (int)(s->step & 1), oth = cur ^ 1;
     const int kind = s->p.precision == PF_F64 ? 1 : 0;
     const size_t b = s->L.N * s->L.esz;
     // grain index through the free U buffer (N int16 fit in N field values)
-    CK(launch_shift_rows(2, s->grain, s->U[oth], nx, ny, nz, rows, 0.0, s->st));
+    CK(launch_shift_rows(2, s->grain, s->U[oth], nx, ny, nz, rows, 0, 0.0, 0.0, s->st));
     CK(cudaMemcpyAsync(s->grain, s->U[oth], s->L.N * sizeof(int16_t), cudaMemcpyDeviceToDevice, s->st));
-    CK(launch_shift_rows(kind, s->psi[cur], s->psi[oth], nx, ny, nz, rows, -s->p.h, s->st));
-    CK(launch_shift_rows(kind, s->U[cur], s->U[oth], nx, ny, nz, rows, 0.0, s->st));
+    // psi continues as a signed distance into the melt; U continues the steady far field of the
+    // moving frame, U0 + C exp(-Vp y / D) (Vp = 0, isothermal: the last row, a zero-gradient far field)
+    const double vp = s->p.thermal == PF_FROZEN_GRADIENT ? s->p.Vp : 0.0;
+    CK(launch_shift_rows(kind, s->psi[cur], s->psi[oth], nx, ny, nz, rows, 1, -s->p.h, 0.0, s->st));
+    CK(launch_shift_rows(kind, s->U[cur], s->U[oth], nx, ny, nz, rows, vp > 0.0 ? 3 : 0, s->p.U0,
+                         vp * s->p.h / s->p.D, s->st));
     CK(cudaMemcpyAsync(s->psi[cur], s->psi[oth], b, cudaMemcpyDeviceToDevice, s->st));
     CK(cudaMemcpyAsync(s->U[cur], s->U[oth], b, cudaMemcpyDeviceToDevice, s->st));
     // the frame moved up by rows h: the isotherms sit rows h lower in it

@@ -172,8 +172,9 @@ struct SeedDev {
 cudaError_t launch_init_seeds(int prec, int dim, int nx, int ny, int nz, double h, double U0, const SeedDev* seeds,
                               int n_seeds, void* psi, void* U, int16_t* grain, cudaStream_t st);
 cudaError_t launch_fill(int prec, void* p, double v, long long n, cudaStream_t st);
-// frame shift of one field toward -y (kind 0: float, 1: double, 2: int16 grain index)
-cudaError_t launch_shift_rows(int kind, const void* src, void* dst, int nx, int ny, int nz, int rows, double slope,
-                              cudaStream_t st);
+// frame shift of one field toward -y (kind 0: float, 1: double, 2: int16 grain index); vacated
+// rows, k beyond the last: mode 0 copy the last row, 1 continue it by a k, 3 a + (last - a) exp(-b k)
+cudaError_t launch_shift_rows(int kind, const void* src, void* dst, int nx, int ny, int nz, int rows, int mode,
+                              double a, double b, cudaStream_t st);
 
 }  // namespace pf

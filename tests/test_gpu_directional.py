@@ -218,8 +218,10 @@ def test_group_graph_clock_3d(native):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_shift_frame_moves_state_and_keeps_temperature(native, prec):
-    """pf_shift_frame: cell (x, y) takes (x, y + m); the top m rows continue
-    the last row (psi minus h per row, U and grain copied), bit for bit; and
+    """pf_shift_frame: cell (x, y) takes (x, y + m), bit for bit; the top m
+    rows are melt: psi continues the last row minus h per row (bit for bit), U
+    continues the steady far field U0 + (U_last - U0) exp(-Vp k h / D) (to
+    rounding), the grain index is copied; and
     the next step equals the oracle's step on the shifted state with the
     isotherm yT moved down by m h (FP64: 1e-12 relative)."""
     w, psi, U, g, rots = ds_state(21, 90, 53)
@@ -237,7 +239,9 @@ def test_shift_frame_moves_state_and_keeps_temperature(native, prec):
     steps_up = np.arange(1, m + 1)[:, None] * w.h
     want_top = (p3[-1].astype(np.float64)[None, :] - steps_up).astype(p3.dtype)
     assert np.array_equal(p4[-m:], want_top)
-    assert np.array_equal(u4[-m:], np.repeat(u3[-1:], m, axis=0))
+    ks = np.arange(1, m + 1)[:, None]
+    want_u = w.U0 + (u3[-1].astype(np.float64)[None, :] - w.U0) * np.exp(-w.Vp * w.h / w.D * ks)
+    assert np.abs(u4[-m:] - want_u).max() <= (1e-14 if prec == "f64" else 1e-6)
     assert np.array_equal(g4[-m:], np.repeat(g3[-1:], m, axis=0))
     assert s.steps_done == 44
     if prec == "f64":
@@ -257,7 +261,7 @@ def test_shift_frame_3d_and_invalid_calls(native):
     s.shift_frame(5)
     p1, u1 = s.get_fields()
     assert np.array_equal(p1[:, :-5, :], p0[:, 5:, :]) and np.array_equal(u1[:, :-5, :], u0[:, 5:, :])
-    assert np.array_equal(u1[:, -5:, :], np.repeat(u0[:, -1:, :], 5, axis=1))
+    assert np.array_equal(u1[:, -5:, :], np.repeat(u0[:, -1:, :], 5, axis=1))  # isothermal: a copy
     for bad in (0, -1, w.ny):
         with pytest.raises(native.PfError):
             s.shift_frame(bad)
@@ -266,3 +270,54 @@ def test_shift_frame_3d_and_invalid_calls(native):
     with pytest.raises(native.PfError):
         s.shift_frame(1)  # a group member: PF_ERR_STATE
     g.close()
+
+
+def test_moving_frame_keeps_the_pulled_planar_front(native):
+    """The pulled planar front of the oracle pin (V W / D = 0.016, Vp = 0.1,
+    lT = 150, front on its isotherm, 4 cells wide like the pin: with lT above
+    the diffusion length D/V = 63 W a wider front is constitutionally
+    unstable), FP64, for the pin's 1e4 steps, once in a static box and once in
+    a box shifted back by pf_shift_frame whenever the front passes 32 W: the
+    two fronts agree in the lab frame within 0.05 W, stay within 0.25 W of the
+    isotherm yT + Vp t, and the tip speed along the pulling axis
+    (pf_observe(-2)) stays within 2% of Vp across the shifts.  A shift that
+    would put F1 = 1 - (1-k) zeta below 0.05 on the grid is refused and moves
+    nothing."""
+    nx, ny, h, dt = 4, 220, 0.8, 0.02
+    k, lam = 0.15, 10.0
+    D = 0.6267 * lam
+    Vp, lT, yT = 0.1, 150.0, 30.0
+    y = (np.arange(ny) * h)[:, None] * np.ones((1, nx))
+    eta = y - yT
+    psi = -eta
+    U = np.where(eta < 0, 0.0, -1.0 + np.exp(-Vp * np.maximum(eta, 0) / D))
+    p = native.make_params(2, nx, ny, 1, h, dt, k, 0.0, lam, D, -1.0, "SBAR21", "f64", bc_x=native.PF_BC_PERIODIC,
+                           thermal=native.PF_FROZEN_GRADIENT, Vp=Vp, lT=lT, yT=yT)
+    lab = {}
+    for moving in (False, True):
+        s = native.Sim(p)
+        s.set_fields(psi, U)
+        s.observe(-2)
+        off, shifts, speeds = 0.0, 0, []
+        for chunk in range(10):
+            s.step(1000)
+            o = s.observe(-2)
+            if chunk >= 1:
+                speeds.append(o["v_tip"])
+            lab[moving] = o["tip"][1] + off  # lab position, taken before any shift of this chunk
+            if moving and o["tip"][1] > 32.0:
+                rows = int(round((o["tip"][1] - 30.0) / h))
+                s.shift_frame(rows)
+                off += rows * h
+                shifts += 1
+        t = s.steps_done * dt
+        assert abs(lab[moving] - (yT + Vp * t)) < 0.25
+        assert max(abs(v - Vp) for v in speeds) < 0.02 * Vp, speeds
+        if moving:
+            assert shifts >= 3
+            before = s.get_fields()
+            with pytest.raises(native.PfError):
+                s.shift_frame(100)  # zeta at the top would reach 1.5: F1 < 0
+            after = s.get_fields()
+            assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    assert abs(lab[True] - lab[False]) < 0.05
