@@ -52,10 +52,10 @@ def dist_env():
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is byte-identical to the one captured (sha256 of the .cu file).
 TRAFFIC = {
-    # profiles/k_step2d_sbar21_f32_orientation_sweep_10x1024sq.md
+    # ncu capture of one k_step2d<float, S-bar_21> launch of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38)
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
                 "sha256": "2c3054b08514666c37bee63e29a1212ad130f7c85e7b23bda1d8a4aeabc6be40", "bytes": 154640640},
-    # profiles/k_step3d_sbar120_f32_dendrite_256cube.md
+    # ncu capture of one k_step3d<float, S-bar_120, 30, 14> launch of the 256^3 free dendrite
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
                    "sha256": "c61f12b619648a147f6a766017b0050881de28269c5f3989897a750f80b1898c", "bytes": 262906368},
 }
@@ -111,10 +111,22 @@ class Clocks:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, window="the timed region"):
         self.index = index
+        self.window = window
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.edges = []  # one-shot samples taken right before and right after
+
+    def once(self):
+        """One synchronous sample (a row in the sampler's format), or None."""
+        try:
+            r = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+            row = r.stdout.strip().splitlines()[0]
+            return row if row.count(",") >= 8 else None
+        except Exception:
+            return None
 
     def __enter__(self):
         try:
@@ -124,6 +136,13 @@ class Clocks:
         except Exception:
             self.p = None
         return self
+
+    def mark(self):
+        """A synchronous sample at this point (call right before and right
+        after the timed region, so that short timed regions still carry one)."""
+        row = self.once()
+        if row:
+            self.edges.append(row)
 
     def __exit__(self, *a):
         if self.p:
@@ -136,12 +155,17 @@ class Clocks:
     def summary(self):
         try:
             self.f.flush()
-            rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+            sampled = [r for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+            rows = [r.split(",") for r in sampled + self.edges]
             sm = [float(r[1]) for r in rows]
             mx = max(float(r[2]) for r in rows)
             names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
             reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
-            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
+                    "samples": len(sampled), "edge_samples": len(self.edges),
+                    "edge_sm_mhz": [float(r.split(",")[1]) for r in self.edges],
+                    "window": f"200 ms sampler over {self.window}, plus one sample right before and one right "
+                              f"after the timed region"}
         except Exception as e:  # pragma: no cover
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)}
 
@@ -660,6 +684,10 @@ def run_native(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.Stream()
     ws = workloads(args.n, args.scheme, args.workload)
+    # the clock sampler runs from before the autotuner (seconds of load on a
+    # fresh box) to the end of the timed region
+    clocks = Clocks(local, window="the autotuner, the warm-up and the timed region")
+    clocks.__enter__()
     tile = None
     if not args.no_tune:
         from paper_2110_12448_gb300 import autotune
@@ -675,9 +703,11 @@ def run_native(args):
     for s in sims:
         group.add(s)
     cells = sum(s.n_cells for s in sims)
+    observes = [0]
 
-    def steps(k, ev=None):
-        """k steps with observe every OBS_EVERY; returns kernel-only event pairs."""
+    def steps(k):
+        """k steps with the FP64 observe of every instance every OBS_EVERY
+        steps and after the last one; returns kernel-only event pairs."""
         done = 0
         pairs = []
         while done < k:
@@ -689,31 +719,47 @@ def run_native(args):
             b.record(stream)
             pairs.append((a, b, chunk))
             done += chunk
-            if sims[0].steps_done % OBS_EVERY == 0:
+            if sims[0].steps_done % OBS_EVERY == 0 or done == k:
                 for s in sims:
                     s.observe(0)
+                observes[0] += 1
         return pairs
 
     steps(args.warmup)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = Clocks(local)
-    with clocks:
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pairs = steps(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
+    observes[0] = 0
+    clocks.mark()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pairs = steps(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark()
+    clocks.__exit__()
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
     kern_ms = sum(a.elapsed_time(b) for a, b, _ in pairs)
     n_launch = sum(c for _, _, c in pairs)
-    per_step = sorted(a.elapsed_time(b) / c for a, b, c in pairs)
+    n_observe = observes[0]
     ms, value = aggregate(ms, cells, args.steps, world, device="cuda")
+
+    # per-step latency after the timed region: 200 single steps of the batch,
+    # each launched directly and bracketed by its own events
+    lat = []
+    for _ in range(200):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        group.step(1, use_graph=False)
+        b.record(stream)
+        lat.append((a, b))
+    torch.cuda.synchronize()
+    per_step = sorted(a.elapsed_time(b) for a, b in lat)
 
     # latency of the device tip-radius fit (pf_tip_radius, host round trip
     # included) on the sweep's instances after the timed region; the physical
@@ -755,8 +801,10 @@ def run_native(args):
                     "frac": tf / FP32_PEAK_TFLOPS, "flop_per_cell": fpc, "kernel": kname,
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
-    # end to end through the public API: state in from pinned host buffers,
-    # K steps, state and observation back, all inside the timed region
+    # end to end through the public API: the state of every instance queued in
+    # from pinned host buffers (pf_set_fields_async), the K steps with their
+    # observes, and the state queued back out (pf_get_fields_async), one
+    # synchronisation at the end; all inside the timed region
     if args.no_e2e:
         host = []
     else:
@@ -764,39 +812,44 @@ def run_native(args):
                  torch.empty(s.shape, dtype=torch.float32 if args.precision == "f32" else torch.float64).pin_memory())
                 for s in sims]
     for s, (hp, hu) in zip(sims, host):
-        a, b = s.get_fields()
-        hp.numpy()[...] = a
-        hu.numpy()[...] = b
+        s.get_fields(out=(hp.numpy(), hu.numpy()))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s, (hp, hu) in zip(sims, host):
-        s.set_fields(hp.numpy(), hu.numpy())
+        s.set_fields_async(hp.numpy(), hu.numpy())
     if host:
         steps(args.steps)
     h2d = d2h = 0
     for s, (hp, hu) in zip(sims, host):
-        s.get_fields(out=(hp.numpy(), hu.numpy()))  # straight into the pinned buffers
+        s.get_fields_async(hp.numpy(), hu.numpy())  # straight into the pinned buffers
         h2d += hp.numel() * hp.element_size() * 2
         d2h += hp.numel() * hp.element_size() * 2
-    torch.cuda.synchronize()
+    if host:
+        sims[0].synchronize()
     e2e_s = time.perf_counter() - t0
     e2e = None if not host else {"value": cells * args.steps * world / e2e_s / 1e9, "unit": "GLUPS",
-                                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+                                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+                                 "copies": "pf_set_fields_async / pf_get_fields_async on the batch's stream, "
+                                           "pinned host buffers, one synchronisation"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": WORKLOAD_TEXT[args.workload].format(n=args.n, n2=2 * args.n, scheme=args.scheme) +
-                                       f", FP32 fields, batched persistent launch + CUDA graph, observe every "
-                                       f"{OBS_EVERY} steps",
-                           "cells_per_gpu": cells, "l2": f"state {cells * 16 / 1e6:.0f} MB per step > 129 MB L2"},
+                                       f", {args.precision.upper()} fields, batched persistent launch + CUDA graph, "
+                                       f"FP64 observe of every instance every {OBS_EVERY} steps and after the last "
+                                       f"timed step ({n_observe} inside the timed region)",
+                           "cells_per_gpu": cells,
+                           "l2": f"state {cells * 2 * (4 if args.precision == 'f32' else 8) / 1e6:.0f} MB per step "
+                                 f"> 129 MB L2, no flush"},
                 "roofline": roof, "roofline_alu": roof_alu, "e2e": e2e, "clocks": clocks.summary(),
                 "latency_ms_per_step": {"p50": statistics.median(per_step),
                                         "p99": per_step[min(len(per_step) - 1, int(0.99 * len(per_step)))],
-                                        "over": f"{len(per_step)} chunks of up to {OBS_EVERY} steps"},
+                                        "over": f"{len(per_step)} single steps of the whole batch after the timed "
+                                                f"region, each launched directly with its own events"},
                 "tile": list(tile) if tile else None,
-                "gpu_launches": n_launch + 2 * len(sims) * (args.steps // OBS_EVERY)}
+                "gpu_launches": n_launch + 2 * len(sims) * n_observe}
         if sweep:
             line["directional" if args.workload == "directional2d" else "tip_radius_call"] = sweep
         if world == 1 and not args.no_fp64:

@@ -212,6 +212,17 @@ int pf_tip_radius(pf_sim* s, int grain, const double tip[3], double v_tip, pf_ti
  * handle's precision each) and of the step counter. */
 int pf_get_fields(pf_sim* s, void* psi_host, void* U_host);
 int pf_set_fields(pf_sim* s, const void* psi_host, const void* U_host);
+/* The same copies queued on the handle's stream without waiting: the host
+ * arrays must stay valid (and, for pf_get_fields_async, unread) until the
+ * stream has passed the copies -- pf_synchronize, or any later synchronising
+ * call on the stream.  Copies from or to pinned (page-locked) host memory run
+ * asynchronously at the full host-link rate; pageable memory makes the CUDA
+ * runtime stage them.  Work of other streams (a group on another stream) is
+ * not ordered against these copies: the caller orders it. */
+int pf_set_fields_async(pf_sim* s, const void* psi_host, const void* U_host);
+int pf_get_fields_async(pf_sim* s, void* psi_host, void* U_host);
+/* Wait until all work queued on the handle's stream has finished. */
+int pf_synchronize(pf_sim* s);
 int pf_get_step(pf_sim* s, int64_t* step);
 int pf_set_step(pf_sim* s, int64_t step);
 
@@ -227,7 +238,9 @@ int pf_set_step(pf_sim* s, int64_t step);
  * copied.  The frozen
  * temperature is kept in place: yT decreases by rows*h, so the next step sees
  * the same temperature at every material point.  Later observations are in
- * the moved frame (the tips remembered for V move with it).  1 <= rows < ny.
+ * the moved frame: the tips remembered for V and the grains' reference points
+ * (pf_set_grains' centres) move with it, so growth angles and V carry on
+ * unchanged.  1 <= rows < ny.
  * Synchronises the stream.  Errors: PF_ERR_INVALID (rows out of range, or a
  * frozen temperature that the moved frame would put where pf_create refuses
  * it: F1 = 1 - (1-k) zeta below 0.05 on the grid, or the explicit step
@@ -283,15 +296,19 @@ const char* pf_last_cuda_error(void);
  * fields: psi_dev, U_dev (nx*ny*nz elements of p->precision) and, when
  * grain >= 0, the int16 grain map grain_dev; rot9 is the observed grain's
  * crystal-to-lab matrix (grain 0's for grain = -1) and centre3 its reference
- * point.  Only p->dim, nx, ny, nz, h, k and precision are read.  The call
- * synchronises `stream` (NULL = legacy default stream) and fills *out like
- * pf_observe, except step, t and v_tip, which are 0 (no history is kept).
+ * point.  grain = -2 observes every cell with +y as the growth axis (the
+ * pulling axis, as in pf_observe; rot9 is then not used for the axis).  Only
+ * p->dim, nx, ny, nz, h, k and precision are read.  The call synchronises
+ * `stream` (NULL = legacy default stream) and fills *out like pf_observe,
+ * except step, t and v_tip, which are 0 (no history is kept).
  *
  * Scratch: instead of memory from the caller, the block partials live in a
  * fixed 22 KB array in the library's device globals, which every GPU that
- * loads the library holds until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls share the array:
+ * loads the library holds until the process exits.  Every call looks up that
+ * array's device address on the current device (cudaGetSymbolAddress, which
+ * allocates nothing), so the entry point stays valid across a device reset;
+ * the first call on a device may load the library's device code, so make it
+ * before any stream capture.  All calls share the array:
  * calls whose work overlaps on a device (two streams, two host threads) race
  * and must be serialised by the caller.  Grids above PF_NOALLOC_MAX_CELLS
  * cells are rejected with PF_ERR_INVALID.  Never allocates device memory. */

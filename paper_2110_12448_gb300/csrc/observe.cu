@@ -11,7 +11,6 @@
 // choice is reproducible on any FP64 implementation of the same formula.
 #include <cfloat>
 #include <math_constants.h>
-#include <mutex>
 
 #include "pf_internal.cuh"
 
@@ -376,24 +375,16 @@ __global__ void k_shift_rows(const T* __restrict__ src, T* __restrict__ dst, int
 // kernels overlap on a device race on it.
 static __device__ __align__(256) ObsPartial g_noalloc_scratch[OBS_BLOCKS + 1];
 
-// Device address of the scratch on the current device.  The first call on a
-// device looks it up with cudaGetSymbolAddress (a host-side name of a
-// __device__ array is not a device address) and caches it per device.
+// Device address of the scratch on the current device, looked up on every
+// call with cudaGetSymbolAddress (a host-side name of a __device__ array is
+// not a device address).  Nothing is cached, so the address stays right after
+// the device's context has been torn down and made again (cudaDeviceReset):
+// the module is then loaded anew, possibly at another address.
 cudaError_t noalloc_scratch(ObsPartial** partials, ObsPartial** result) {
-    static std::mutex mu;
-    static void* addr[256] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        addr[dev] = p;
-    }
-    *partials = static_cast<ObsPartial*>(addr[dev]);
+    *partials = static_cast<ObsPartial*>(p);
     *result = *partials + OBS_BLOCKS;
     return cudaSuccess;
 }

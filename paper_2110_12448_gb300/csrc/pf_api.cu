@@ -575,6 +575,30 @@ int pf_set_fields(pf_sim* s, const void* psi_host, const void* U_host) {
     return PF_OK;
 }
 
+int pf_set_fields_async(pf_sim* s, const void* psi_host, const void* U_host) {
+    if (!s || (!psi_host && !U_host)) return PF_ERR_INVALID;
+    const int cur = (int)(s->step & 1);
+    const size_t b = s->L.N * s->L.esz;
+    if (psi_host) CK(cudaMemcpyAsync(s->psi[cur], psi_host, b, cudaMemcpyHostToDevice, s->st));
+    if (U_host) CK(cudaMemcpyAsync(s->U[cur], U_host, b, cudaMemcpyHostToDevice, s->st));
+    return PF_OK;
+}
+
+int pf_get_fields_async(pf_sim* s, void* psi_host, void* U_host) {
+    if (!s || (!psi_host && !U_host)) return PF_ERR_INVALID;
+    const int cur = (int)(s->step & 1);
+    const size_t b = s->L.N * s->L.esz;
+    if (psi_host) CK(cudaMemcpyAsync(psi_host, s->psi[cur], b, cudaMemcpyDeviceToHost, s->st));
+    if (U_host) CK(cudaMemcpyAsync(U_host, s->U[cur], b, cudaMemcpyDeviceToHost, s->st));
+    return PF_OK;
+}
+
+int pf_synchronize(pf_sim* s) {
+    if (!s) return PF_ERR_INVALID;
+    CK(cudaStreamSynchronize(s->st));
+    return PF_OK;
+}
+
 int pf_get_step(pf_sim* s, int64_t* step) {
     if (!s || !step) return PF_ERR_INVALID;
     *step = s->step;
@@ -627,8 +651,10 @@ int pf_shift_frame(pf_sim* s, int rows) {
     InstRec r = make_rec(s, 0);
     CK(cudaMemcpyAsync(s->rec, &r, sizeof(r), cudaMemcpyHostToDevice, s->st));
     CK(cudaStreamSynchronize(s->st));
-    // remembered tip positions follow the frame, so the next V is continuous
+    // remembered tip positions follow the frame, so the next V is continuous,
+    // and so do the grains' reference points, so growth angles are unchanged
     for (size_t slot = 0; slot < s->have_prev.size(); ++slot) s->prev[4 * slot + 2] -= rows * s->p.h;
+    for (int g = 0; g < s->n_grains; ++g) s->centres_h[3 * g + 1] -= rows * s->p.h;
     return PF_OK;
 }
 
@@ -720,7 +746,7 @@ const char* pf_last_cuda_error(void) { return g_last_cuda.c_str(); }
 
 int pf_observe_fields_noalloc(const pf_params* p, const void* psi_dev, const void* U_dev, const int16_t* grain_dev,
                               const double* rot9, const double* centre3, int grain, void* stream, pf_obs* out) {
-    if (!p || !psi_dev || !U_dev || !rot9 || !centre3 || !out || grain < -1) return PF_ERR_INVALID;
+    if (!p || !psi_dev || !U_dev || !rot9 || !centre3 || !out || grain < -2) return PF_ERR_INVALID;
     if (grain >= 0 && !grain_dev) return PF_ERR_INVALID;
     if (p->dim != 2 && p->dim != 3) return PF_ERR_INVALID;
     if (p->precision != PF_F32 && p->precision != PF_F64) return PF_ERR_INVALID;
@@ -729,15 +755,21 @@ int pf_observe_fields_noalloc(const pf_params* p, const void* psi_dev, const voi
     const long long N = (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
     if (N > PF_NOALLOC_MAX_CELLS) return PF_ERR_INVALID;
     const int dim = p->dim;
+    // growth axis as in pf_observe: the crystal axis with the largest +y
+    // component, or +y itself for grain -2 (the pulling axis)
     double d[3] = {0, 0, 0}, best = -INFINITY;
-    for (int a = 0; a < dim; ++a)
-        for (int sg = 1; sg >= -1; sg -= 2) {
-            const double yc = sg * rot9[3 + a];
-            if (yc > best) {
-                best = yc;
-                for (int q = 0; q < 3; ++q) d[q] = q < dim ? sg * rot9[q * 3 + a] : 0.0;
+    if (grain == -2) {
+        d[1] = 1.0;
+    } else {
+        for (int a = 0; a < dim; ++a)
+            for (int sg = 1; sg >= -1; sg -= 2) {
+                const double yc = sg * rot9[3 + a];
+                if (yc > best) {
+                    best = yc;
+                    for (int q = 0; q < 3; ++q) d[q] = q < dim ? sg * rot9[q * 3 + a] : 0.0;
+                }
             }
-        }
+    }
     int ea = 0;
     for (int a = 1; a < dim; ++a)
         if (std::fabs(d[a]) > std::fabs(d[ea])) ea = a;
@@ -750,7 +782,7 @@ int pf_observe_fields_noalloc(const pf_params* p, const void* psi_dev, const voi
     a.nx = p->nx;
     a.ny = p->ny;
     a.nz = dim == 3 ? p->nz : 1;
-    a.grain_filter = grain;
+    a.grain_filter = grain < 0 ? -1 : grain;
     a.h = p->h;
     a.k = p->k;
     for (int q = 0; q < 3; ++q) {

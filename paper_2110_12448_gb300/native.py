@@ -93,6 +93,9 @@ def lib():
                 "pf_tip_radius": (C.c_int, [vp, C.c_int, P(C.c_double), C.c_double, P(Tip)]),
                 "pf_get_fields": (C.c_int, [vp, vp, vp]),
                 "pf_set_fields": (C.c_int, [vp, vp, vp]),
+                "pf_get_fields_async": (C.c_int, [vp, vp, vp]),
+                "pf_set_fields_async": (C.c_int, [vp, vp, vp]),
+                "pf_synchronize": (C.c_int, [vp]),
                 "pf_get_step": (C.c_int, [vp, P(i64)]),
                 "pf_set_step": (C.c_int, [vp, i64]),
                 "pf_shift_frame": (C.c_int, [vp, C.c_int]),
@@ -286,6 +289,28 @@ class Sim:
         psi = np.ascontiguousarray(psi, dtype=self.np_dtype).reshape(self.shape)
         U = np.ascontiguousarray(U, dtype=self.np_dtype).reshape(self.shape)
         _check(lib().pf_set_fields(self.h, C.c_void_p(psi.ctypes.data), C.c_void_p(U.ctypes.data)), "pf_set_fields")
+
+    def set_fields_async(self, psi, U):
+        """Queue the upload of psi, U (C-contiguous arrays of the handle's shape
+        and dtype, ideally views of pinned host tensors) on the handle's stream
+        without waiting; the arrays must stay alive until synchronize()."""
+        for a in (psi, U):
+            if a.shape != tuple(self.shape) or a.dtype != self.np_dtype or not a.flags.c_contiguous:
+                raise ValueError("set_fields_async: arrays must be C-contiguous with the handle's shape and dtype")
+        _check(lib().pf_set_fields_async(self.h, C.c_void_p(psi.ctypes.data), C.c_void_p(U.ctypes.data)),
+               "pf_set_fields_async")
+
+    def get_fields_async(self, psi, U):
+        """Queue the download of the current psi, U into caller arrays without
+        waiting; read them only after synchronize()."""
+        for a in (psi, U):
+            if a.shape != tuple(self.shape) or a.dtype != self.np_dtype or not a.flags.c_contiguous:
+                raise ValueError("get_fields_async: arrays must be C-contiguous with the handle's shape and dtype")
+        _check(lib().pf_get_fields_async(self.h, C.c_void_p(psi.ctypes.data), C.c_void_p(U.ctypes.data)),
+               "pf_get_fields_async")
+
+    def synchronize(self):
+        _check(lib().pf_synchronize(self.h), "pf_synchronize")
 
     @property
     def steps_done(self) -> int:

@@ -1,0 +1,112 @@
+"""The accuracy contract at its full horizon: the 2D free dendrite (200 x 200,
+h = 0.8, dt = 0.02, k = 0.15, eps4 = 0.02, lambda = 10, D = 0.6267 lambda,
+U0 = -0.55, seed r = 10 h, S-bar_{2,1}) run for 10^4 steps on the GPU and by
+the FP64 oracle, observed every 1000 steps.
+
+Tip velocity: V over each 1000-step interval in which the tip still moves
+(V > 0.05 W / tau0; after about 7000 steps the arms reach the walls) must
+agree with the oracle's within 0.5 %.
+
+Fields: max |d phi| and max |d U| against the oracle after 10^4 steps are
+reported (printed as a CONTRACT line, and written as JSON to the directory
+named by PF_REPORT_DIR when set).  Their bounds follow from what limits each
+build.  The oracle itself amplifies a one-time 1e-10 perturbation of psi to
+7e-7 by step 10^4, and the oracle with psi and U rounded to FP32 after every
+step (exact arithmetic otherwise) ends 2e-4 / 3e-4 away: any build that stores
+FP32 fields misses 1e-4 on this workload.
+  * FP64: 1e-9 (rounding of 1e-16 per step, amplified).
+  * FP32 fields (fast exp2/reciprocal): 5e-3 on phi and U (measured ~2e-3).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2110_12448_gb300 import synth
+from tests.helpers import oracle_params
+
+pytestmark = pytest.mark.gpu
+
+STEPS, EVERY = 10000, 1000
+
+
+@pytest.fixture(scope="module")
+def native():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_12448_gb300 import native as N
+    N.lib()
+    return N
+
+
+def _tips(obs):
+    return [(o[0], o[1]) for o in obs]
+
+
+@pytest.fixture(scope="module")
+def oracle_run():
+    w = synth.free_dendrite_2d(200)
+    p = oracle_params(w)
+    psi, U, g = O.init_seeds(p, w.U0, w.seeds, w.seed_grain)
+    tips = []
+    for _ in range(STEPS // EVERY):
+        psi, U = O.step(p, w.rots, g, psi, U, EVERY)
+        o = O.observe(p, w.rots, w.centres, g, psi, U, 0)
+        tips.append((o["tip_x"], o["tip_y"]))
+    return w, psi, U, tips
+
+
+def gpu_run(N, w, prec):
+    s = N.Sim.from_workload(w, prec)
+    tips = []
+    for _ in range(STEPS // EVERY):
+        s.step(EVERY)
+        o = s.observe(0)
+        tips.append(o["tip"][:2])
+    psi, U = s.get_fields()
+    s.close()
+    return psi.astype(np.float64), U.astype(np.float64), tips
+
+
+def speeds(tips, dt):
+    return [math.hypot(b[0] - a[0], b[1] - a[1]) / (EVERY * dt) for a, b in zip(tips, tips[1:])]
+
+
+def report(name, d):
+    line = json.dumps(dict(d, build=name))
+    print("CONTRACT", line)
+    out = os.environ.get("PF_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, f"contract_{name}.json"), "w") as f:
+            f.write(line + "\n")
+
+
+def compare(N, oracle_run, prec):
+    w, psi, U, tips = oracle_run
+    gp, gu, gt = gpu_run(N, w, prec)
+    dphi = float(np.max(np.abs(np.tanh(gp / math.sqrt(2)) - np.tanh(psi / math.sqrt(2)))))
+    du = float(np.max(np.abs(gu - U)))
+    vo, vg = speeds(tips, w.dt), speeds(gt, w.dt)
+    moving = [i for i, v in enumerate(vo) if v > 0.05]
+    verr = max(abs(vg[i] - vo[i]) / vo[i] for i in moving)
+    report(prec, {"steps": STEPS, "max_abs_dphi": dphi, "max_abs_dU": du, "v_tip_max_rel_err": verr,
+                  "v_tip_oracle": vo, "v_tip_gpu": vg, "intervals_moving": len(moving)})
+    assert len(moving) >= 5  # the dendrite grows for most of the run
+    return dphi, du, verr
+
+
+def test_fp64_10k_steps(native, oracle_run):
+    dphi, du, verr = compare(native, oracle_run, "f64")
+    assert dphi < 1e-9 and du < 1e-9
+    assert verr < 1e-9
+
+
+def test_fp32_10k_steps(native, oracle_run):
+    dphi, du, verr = compare(native, oracle_run, "f32")
+    assert verr < 5e-3  # the contract's tip-velocity bound, 0.5 %
+    assert dphi < 5e-3 and du < 5e-3

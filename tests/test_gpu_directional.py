@@ -251,6 +251,52 @@ def test_shift_frame_moves_state_and_keeps_temperature(native, prec):
         assert rel_err(gp, op) < 1e-12 and rel_err(gu, ou) < 1e-12
 
 
+def test_shift_frame_keeps_growth_angle(native):
+    """The grains' reference points move with the frame: the growth angle of
+    a grain and of the pulling axis is unchanged by a shift, and the tip sits
+    m h lower in the moved frame (planar front with sine modes near the bottom
+    of the box, so the shifted rows hold no interface)."""
+    w = synth.directional_2d(96, 120, 20.0, "SBAR21", Vp=0.1, lT=500.0)
+    s = native.Sim.from_workload(w, "f64")
+    s.step(10)
+    before = {g: s.observe(g) for g in (0, -2)}
+    m = 5
+    s.shift_frame(m)
+    for g, b in before.items():
+        a = s.observe(g)
+        assert a["found"] == b["found"] == 1
+        assert abs(a["tip"][1] - (b["tip"][1] - m * w.h)) <= 1e-9
+        assert abs(a["tip"][0] - b["tip"][0]) <= 1e-12
+        assert abs(a["angle_xy_deg"] - b["angle_xy_deg"]) <= 1e-9, (g, a["angle_xy_deg"], b["angle_xy_deg"])
+
+
+@pytest.mark.parametrize("scheme", ["SBAR120", "S100"])
+def test_shift_frame_3d_frozen_gradient(native, scheme):
+    """3D pf_shift_frame with a frozen temperature: the top m rows of U
+    continue the steady far field U0 + (U_last - U0) exp(-Vp k h / D) in every
+    z plane, psi the signed distance; the next step equals the oracle's on the
+    shifted state with the isotherm yT moved down by m h (FP64, 1e-12)."""
+    w, psi, U, g, rots = ds_state3(34, 20, 26, 12, scheme, lT=80.0, Vp=0.2)
+    s = gpu_sim3(native, w, "f64", g, rots, psi, U, step=13)
+    s.step(2)
+    p3, u3 = s.get_fields()  # [z, y, x]
+    g3 = s.get_grain_index()
+    m = 4
+    s.shift_frame(m)
+    p4, u4 = s.get_fields()
+    g4 = s.get_grain_index()
+    assert np.array_equal(p4[:, :-m], p3[:, m:]) and np.array_equal(u4[:, :-m], u3[:, m:])
+    assert np.array_equal(g4[:, :-m], g3[:, m:])
+    ks = np.arange(1, m + 1)[None, :, None]
+    assert np.array_equal(p4[:, -m:], p3[:, -1:] - ks * w.h)
+    want_u = w.U0 + (u3[:, -1:] - w.U0) * np.exp(-w.Vp * w.h / w.D * ks)
+    assert np.abs(u4[:, -m:] - want_u).max() <= 1e-14
+    s.step(1)
+    gp, gu = s.get_fields()
+    op, ou = O.step(oracle_params(w, step=15, yT=w.yT - m * w.h), rots, g4, p4, u4, 1)
+    assert rel_err(gp, op) < 1e-12 and rel_err(gu, ou) < 1e-12
+
+
 def test_shift_frame_3d_and_invalid_calls(native):
     w = synth.free_dendrite_3d(24, steps=1)
     w.nx, w.ny, w.nz = 20, 26, 12

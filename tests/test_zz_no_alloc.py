@@ -8,7 +8,8 @@ memory.  The test calls it through the C-ABI twice in a row, on two
 different states, and checks each result against pf_observe on the same
 handle: the tip cell and position exactly (both sides take the decision with
 the same FP64 formula), the solute integral and solid fraction within the
-1e-12 relative tolerance of the other observe tests.  Collected last so that
+1e-12 relative tolerance of the other observe tests, for one grain, for
+every cell (grain -1) and for the pulling axis (grain -2).  Collected last so that
 a failure here does not hide any other test.
 """
 import numpy as np
@@ -48,7 +49,7 @@ def test_noalloc_observe_matches_pf_observe_twice(native, prec):
     for call in range(2):
         s.step(25 + 10 * call)
         psi_d, U_d, g_d = s.device_fields()
-        for g in (-1, 1):
+        for g in (-1, 1, -2):  # -2: every cell, +y as the growth axis (the pulling axis)
             gg = max(g, 0)
             ref = s.observe(g)
             got = native.observe_fields_noalloc(s.p, psi_d, U_d, g_d, w.rots[gg], w.centres[gg], g)
