@@ -38,7 +38,11 @@ PHYS_STEPS = 20000
 DS_THETAS = (0, 10, 20, 30, 40)
 DS_VP, DS_LT = 0.1, 2000.0
 OBS_EVERY = 100
-B_PER_CELL = {"f32": 18, "f64": 34}  # read psi, U, grain; write psi', U'
+# algorithmic bytes per cell update: read psi, U, grain; write psi', U'
+# (f32c: hi and lo halves of psi and U).  The two-kernel form adds the
+# d psi/dt write and read and the U pass's second read of psi and U.
+B_PER_CELL = {"f32": 18, "f64": 34, "f32c": 34}
+B_PER_CELL_TWO = {"f32": 34, "f64": 66}
 
 
 def dist_env():
@@ -61,25 +65,38 @@ TRAFFIC = {
 }
 
 
-# FP32 floating-point operations per cell update (FADD + FMUL + 2 FFMA thread
-# instructions per cell from ncu on the scalar build of the same arithmetic)
-# and the FP32 peak from the unit counts and the maximum clock: 152 SMs x 128
-# FP32 lanes x 2 (FMA) x 2.07 GHz.
-# (3D: executed per output cell, including the ring-1 recompute of the 30 x 14 tile)
-FLOP_PER_CELL = {("sweep2d", "SBAR21"): 315, ("poly2d", "SBAR21"): 315, ("directional2d", "SBAR21"): 315,
-                 ("dendrite3d", "SBAR120"): 1001}
+# FP32 floating-point operations per cell update of the dominant kernel, from
+# an ncu capture of one launch: FADD + FMUL + 2 FFMA + 2 (FADD2 + FMUL2) +
+# 4 FFMA2 thread instructions (sm__sass_thread_inst_executed_op_*_pred_on)
+# over the launch's cell updates; like TRAFFIC, valid only while the kernel
+# source is byte-identical to the one captured.  The FP32 peak is the unit
+# count at the maximum clock: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz.
+# (3D: executed per output cell, including the ring-1 recompute of the tile.)
+FLOPS = {
+    # k_step2d<float, S-bar_21> launch of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38)
+    "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
+                "sha256": "2c3054b08514666c37bee63e29a1212ad130f7c85e7b23bda1d8a4aeabc6be40", "flop_per_cell": 301.1},
+    # k_step3d<float, S-bar_120, 30, 14> launch of the 256^3 free dendrite
+    "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
+                   "sha256": "c61f12b619648a147f6a766017b0050881de28269c5f3989897a750f80b1898c", "flop_per_cell": 1036.8},
+}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def traffic_for(workload):
+def _captured(table, workload, key):
+    """table[workload][key] if the kernel source still matches the capture, else None."""
     import hashlib
-    t = TRAFFIC.get(workload)
+    t = table.get(workload)
     if not t or not t["sha256"]:
         return None
     with open(os.path.join(ROOT, t["source"]), "rb") as f:
         if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
             return None
-    return t["bytes"]
+    return t[key]
+
+
+def traffic_for(workload):
+    return _captured(TRAFFIC, workload, "bytes")
 
 
 def aggregate(ms_local: float, cells_per_rank: int, steps: int, world: int, device=None) -> tuple:
@@ -684,6 +701,11 @@ def run_native(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.Stream()
     ws = workloads(args.n, args.scheme, args.workload)
+    for w in ws:
+        if args.time_level == "t0" or args.kernels == "two":
+            w.time_level = 1
+        if args.kernels == "two":
+            w.kernels = 1
     # the clock sampler runs from before the autotuner (seconds of load on a
     # fresh box) to the end of the timed region
     clocks = Clocks(local, window="the autotuner, the warm-up and the timed region")
@@ -720,8 +742,7 @@ def run_native(args):
             pairs.append((a, b, chunk))
             done += chunk
             if sims[0].steps_done % OBS_EVERY == 0 or done == k:
-                for s in sims:
-                    s.observe(0)
+                group.observe(0)  # every instance, one synchronisation
                 observes[0] += 1
         return pairs
 
@@ -788,55 +809,107 @@ def run_native(args):
 
     # roofline of the fused step kernel: algorithmic bytes per launch / mean launch time
     peak, peak_kind = peaks()
-    bpc = B_PER_CELL[args.precision]
+    bpc = (B_PER_CELL_TWO if args.kernels == "two" else B_PER_CELL)[args.precision]
     achieved = cells * bpc / (kern_ms / n_launch / 1e3) / 1e9
-    kname = ("k_step2d" if ws[0].dim == 2 else "k_step3d") + f"<{'float' if args.precision == 'f32' else 'double'},{args.scheme}>"
+    tname = {"f32": "float", "f64": "double", "f32c": "float, compensated state"}[args.precision]
+    kname = ("k_step2d" if ws[0].dim == 2 else "k_step3d") + f"<{tname},{args.scheme}>"
+    if args.kernels == "two":
+        kname += " psi pass + U pass (two-kernel form, T0)"
+    elif args.time_level == "t0":
+        kname += " (T0)"
+    default_path = args.precision == "f32" and args.kernels == "fused" and args.time_level == "t1"
+    fpc = _captured(FLOPS, args.workload, "flop_per_cell") if default_path and args.scheme in ("SBAR21", "SBAR120") \
+        else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic_for(args.workload), "peak_source": peak_kind, "bytes_per_cell": bpc, "kernel": kname}
-    fpc = FLOP_PER_CELL.get((args.workload, args.scheme)) if args.precision == "f32" else None
+            "traffic": traffic_for(args.workload) if default_path else None, "peak_source": peak_kind,
+            "bytes_per_cell": bpc, "kernel": kname}
     roof_alu = None
     if fpc:
         tf = cells * fpc / (kern_ms / n_launch / 1e3) / 1e12
         roof_alu = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": tf / FP32_PEAK_TFLOPS, "flop_per_cell": fpc, "kernel": kname,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                    "flop_source": "ncu thread-instruction counts of one launch (FADD, FMUL, FFMA and packed pairs)"}
 
-    # end to end through the public API: the state of every instance queued in
-    # from pinned host buffers (pf_set_fields_async), the K steps with their
-    # observes, and the state queued back out (pf_get_fields_async), one
-    # synchronisation at the end; all inside the timed region
-    if args.no_e2e:
+    # end to end through the public API, as a client pipelines a batch: the
+    # instances split into two halves, each half a group on its own stream;
+    # per half, its state queued in from pinned host buffers
+    # (pf_set_fields_async), the K steps with their observes
+    # (pf_group_observe), the state queued back out (pf_get_fields_async).
+    # One half's copies overlap the other half's steps; all inside the timed
+    # region, from the first upload to the last download.
+    e2e = None
+    if not args.no_e2e:
+        dt_np = np.float32 if args.precision == "f32" else np.float64
         host = []
-    else:
-        host = [(torch.empty(s.shape, dtype=torch.float32 if args.precision == "f32" else torch.float64).pin_memory(),
-                 torch.empty(s.shape, dtype=torch.float32 if args.precision == "f32" else torch.float64).pin_memory())
-                for s in sims]
-    for s, (hp, hu) in zip(sims, host):
-        s.get_fields(out=(hp.numpy(), hu.numpy()))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s, (hp, hu) in zip(sims, host):
-        s.set_fields_async(hp.numpy(), hu.numpy())
-    if host:
-        steps(args.steps)
-    h2d = d2h = 0
-    for s, (hp, hu) in zip(sims, host):
-        s.get_fields_async(hp.numpy(), hu.numpy())  # straight into the pinned buffers
-        h2d += hp.numel() * hp.element_size() * 2
-        d2h += hp.numel() * hp.element_size() * 2
-    if host:
-        sims[0].synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e = None if not host else {"value": cells * args.steps * world / e2e_s / 1e9, "unit": "GLUPS",
-                                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
-                                 "copies": "pf_set_fields_async / pf_get_fields_async on the batch's stream, "
-                                           "pinned host buffers, one synchronisation"}
+        for s in sims:
+            hp = torch.empty(s.shape, dtype=torch.float32 if dt_np == np.float32 else torch.float64).pin_memory()
+            hu = torch.empty_like(hp).pin_memory()
+            s.get_fields(out=(hp.numpy(), hu.numpy()))
+            host.append((hp, hu))
+        half = (len(ws) + 1) // 2
+        parts = [list(range(half)), list(range(half, len(ws)))]
+        pipes = []
+        for idx in parts:
+            if not idx:
+                continue
+            st_ = torch.cuda.Stream()
+            ss = []
+            with torch.cuda.stream(st_):
+                for i in idx:
+                    ss.append(N.Sim.from_workload(ws[i], args.precision, stream=st_, init=False))
+                    if tile:
+                        ss[-1].set_tile(*tile)
+            g_ = N.Group(len(ss), sum(N.Group.work_items(x) for x in ss), stream=st_)
+            for x in ss:
+                g_.add(x)
+            pipes.append((st_, ss, g_, [host[i] for i in idx]))
+        for st_, ss, g_, hh in pipes:  # untimed warm-up of the new groups (graph capture)
+            for x, (hp, hu) in zip(ss, hh):
+                x.set_fields_async(hp.numpy(), hu.numpy())
+            g_.step(max(args.warmup, 16), use_graph=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for st_, ss, g_, hh in pipes:
+            for x, (hp, hu) in zip(ss, hh):
+                x.set_fields_async(hp.numpy(), hu.numpy())
+        done = 0
+        while done < args.steps:
+            at = pipes[0][1][0].steps_done
+            chunk = min(OBS_EVERY - (at % OBS_EVERY), args.steps - done)
+            for st_, ss, g_, hh in pipes:
+                g_.step(chunk, use_graph=True)
+            done += chunk
+            if (at + chunk) % OBS_EVERY == 0 or done == args.steps:
+                for st_, ss, g_, hh in pipes:
+                    g_.observe(0)
+        h2d = d2h = 0
+        for st_, ss, g_, hh in pipes:
+            for x, (hp, hu) in zip(ss, hh):
+                x.get_fields_async(hp.numpy(), hu.numpy())  # straight into the pinned buffers
+                h2d += hp.numel() * hp.element_size() * 2
+                d2h += hp.numel() * hp.element_size() * 2
+        for st_, ss, g_, hh in pipes:
+            st_.synchronize()
+        e2e_s = time.perf_counter() - t0
+        for st_, ss, g_, hh in pipes:
+            g_.close()
+            for x in ss:
+                x.close()
+        e2e = {"value": cells * args.steps * world / e2e_s / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+               "copies": "two half-batches on two streams, each: pf_set_fields_async from pinned host buffers, "
+                         "the steps and observes, pf_get_fields_async into them; one half's copies overlap the "
+                         "other's steps"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": WORKLOAD_TEXT[args.workload].format(n=args.n, n2=2 * args.n, scheme=args.scheme) +
+                                       (", T0 time level" if args.time_level == "t0" or args.kernels == "two" else "") +
+                                       (", two-kernel form (psi kernel stores d psi/dt, then the U kernel)"
+                                        if args.kernels == "two" else "") +
                                        f", {args.precision.upper()} fields, batched persistent launch + CUDA graph, "
                                        f"FP64 observe of every instance every {OBS_EVERY} steps and after the last "
                                        f"timed step ({n_observe} inside the timed region)",
@@ -871,7 +944,11 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f32c"],
+                    help="f32c: FP32 arithmetic on the compensated (hi + lo) state, 2D")
+    ap.add_argument("--time-level", default="t1", choices=["t1", "t0"])
+    ap.add_argument("--kernels", default="fused", choices=["fused", "two"],
+                    help="two: the psi kernel stores d psi/dt, then the U kernel (2D, T0)")
     ap.add_argument("--scheme", default="SBAR21", choices=["SBAR21", "S21", "S10", "SBAR120", "S100"])
     ap.add_argument("--n", type=int, default=None,
                     help="grid side (default 1024 in 2D, 256 for dendrite3d, 320 for paper3d)")

@@ -50,7 +50,18 @@ typedef struct pf_sim pf_sim;
 typedef struct pf_group pf_group;
 
 typedef enum { PF_S10 = 0, PF_S21 = 1, PF_SBAR21 = 2, PF_S100 = 3, PF_SBAR120 = 4 } pf_scheme;
-typedef enum { PF_F32 = 0, PF_F64 = 1 } pf_precision;
+/* Arithmetic and storage of the fields:
+ *   PF_F32   FP32 fields, FP32 arithmetic (fast exp2 / reciprocal forms);
+ *   PF_F64   FP64 fields and arithmetic;
+ *   PF_F32C  FP32 arithmetic on a compensated state: psi and U each stored as
+ *            an FP32 pair hi + lo (about 48 significant bits, 8 bytes per
+ *            cell and field), updated by error-free two-sums; phi from the
+ *            library tanh, delta phi from the addition theorem of tanh and
+ *            the U differences of the diffusion term with their lo halves.
+ *            2D, isothermal, mirror walls and the T1 time level only.  The
+ *            host sees FP64 fields (pf_get_fields / pf_set_fields take FP64
+ *            arrays, hi + lo). */
+typedef enum { PF_F32 = 0, PF_F64 = 1, PF_F32C = 2 } pf_precision;
 
 enum {
     PF_OK = 0,
@@ -74,6 +85,14 @@ enum { PF_ISOTHERMAL = 0, PF_FROZEN_GRADIENT = 1 };
  *        dt (1-phi^2)/sqrt2 dpsi/dt (chain rule), phi^n instead of phi'
  *        (conserves the solute to O(dt) over a fixed time). */
 enum { PF_T1 = 0, PF_T0 = 1 };
+/* Kernels of a step (Sec. 3.3.1 describes two, a psi kernel then a U kernel):
+ * PF_FUSED: one kernel per step, psi' and the U update from the same pass
+ *   (d psi/dt stays on chip);
+ * PF_TWO_KERNELS: the psi kernel writes psi' and d psi/dt to device memory,
+ *   then the U kernel reads d psi/dt back (2D, PF_T0 time level, PF_F32 or
+ *   PF_F64).  Same arithmetic as the fused T0 step; it costs the extra
+ *   traffic of d psi/dt and a second read of psi and U. */
+enum { PF_FUSED = 0, PF_TWO_KERNELS = 1 };
 
 /* Problem statement (Sec. 2.1): grid, lattice spacing h (units of W), time
  * step dt (units of tau0), partition coefficient k, anisotropy strength
@@ -107,7 +126,7 @@ typedef struct {
     int32_t thermal;    /* PF_ISOTHERMAL or PF_FROZEN_GRADIENT */
     double Vp, lT, yT;  /* frozen gradient: pulling speed, thermal length, isotherm T0 at t = 0 */
     int32_t time_level; /* PF_T1 (default) or PF_T0 */
-    int32_t reserved;   /* 0 */
+    int32_t kernels;    /* PF_FUSED (default) or PF_TWO_KERNELS */
 } pf_params;
 
 /* A spherical (circular in 2D) seed: centre (x, y, z) and radius r in units
@@ -209,7 +228,8 @@ int pf_observe(pf_sim* s, int grain, pf_obs* out);
 int pf_tip_radius(pf_sim* s, int grain, const double tip[3], double v_tip, pf_tip* out);
 
 /* Checkpoint / restore of the current fields (nx*ny*nz elements of the
- * handle's precision each) and of the step counter. */
+ * handle's precision each; FP64 for PF_F32C, whose hi + lo halves are joined
+ * on the way out and split on the way in) and of the step counter. */
 int pf_get_fields(pf_sim* s, void* psi_host, void* U_host);
 int pf_set_fields(pf_sim* s, const void* psi_host, const void* U_host);
 /* The same copies queued on the handle's stream without waiting: the host
@@ -244,12 +264,14 @@ int pf_set_step(pf_sim* s, int64_t step);
  * Synchronises the stream.  Errors: PF_ERR_INVALID (rows out of range, or a
  * frozen temperature that the moved frame would put where pf_create refuses
  * it: F1 = 1 - (1-k) zeta below 0.05 on the grid, or the explicit step
- * unstable at 1/F1, at the current step; nothing is moved), PF_ERR_STATE
+ * unstable at 1/F1, at the current step; nothing is moved; or a PF_F32C
+ * handle), PF_ERR_STATE
  * (the handle belongs to a group), PF_ERR_CUDA. */
 int pf_shift_frame(pf_sim* s, int rows);
 
-/* Device addresses of the current psi, U (precision of the handle) and the
- * int16 grain map; valid until the next pf_step / pf_group_step. */
+/* Device addresses of the current psi, U (precision of the handle; for
+ * PF_F32C the FP32 hi halves, each followed by its nx*ny*nz lo halves) and
+ * the int16 grain map; valid until the next pf_step / pf_group_step. */
 int pf_device_fields(pf_sim* s, void** psi, void** U, void** grain);
 
 /* Tile shape of the fused kernel (cells per block along x, and the number
@@ -337,6 +359,12 @@ int pf_group_remove(pf_group* g, pf_sim* s);
  * device counter that every launch advances, so replays keep the time. */
 int pf_group_step(pf_group* g, int64_t n, int use_graph);
 int pf_group_size(const pf_group* g);
+/* pf_observe of every member (in the order they were added, out[i] for the
+ * i-th) with one synchronisation: the reductions of all members are queued on
+ * the group's stream and their records read back together.  grain as in
+ * pf_observe and valid for every member.  Returns PF_ERR_NONFINITE (with all
+ * of out filled) when a member holds NaN/Inf cells. */
+int pf_group_observe(pf_group* g, int grain, pf_obs* out);
 int pf_group_destroy(pf_group* g);
 
 #ifdef __cplusplus

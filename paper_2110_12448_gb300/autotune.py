@@ -52,6 +52,8 @@ def wave_aligned(workloads, bx, by, resident, max_waves=8, min_sweep=8):
 
 def _key(device_name, w, precision, count):
     ds = "|ds" if getattr(w, "thermal", 0) or getattr(w, "bc_x", 0) else ""  # the directional kernel variant
+    ds += "|t0" if getattr(w, "time_level", 0) else ""
+    ds += "|two" if getattr(w, "kernels", 0) else ""
     return f"{device_name}|{w.dim}|{w.scheme}|{precision}|{w.nx}x{w.ny}x{w.nz}|n{count}{ds}"
 
 

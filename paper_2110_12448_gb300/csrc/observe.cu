@@ -337,6 +337,22 @@ template <typename T> __global__ void k_fill(T* __restrict__ p, T v, long long n
         p[c] = v;
 }
 
+// Compensated FP32 state (precision PF_F32C): split an FP64 field into hi =
+// fl32(x) and lo = fl32(x - hi) (x - hi is exact in FP64), or join hi + lo
+// back into FP64 (exact).
+__global__ void k_split(const double* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo, long long n) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double v = x[c];
+        const float h = __double2float_rn(v);
+        hi[c] = h;
+        lo[c] = __double2float_rn(v - (double)h);
+    }
+}
+__global__ void k_join(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ x, long long n) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        x[c] = (double)hi[c] + (double)lo[c];
+}
+
 // Frame shift by `rows` cells toward -y: dst(x, y, z) = src(x, y + rows, z)
 // for y + rows < ny.  The vacated top rows, k rows beyond the last one, take
 // (mode 0) the last row's value, (mode 1) the last row's value plus a k (psi:
@@ -440,6 +456,20 @@ cudaError_t launch_shift_rows(int kind, const void* src, void* dst, int nx, int 
     else
         k_shift_rows<int16_t><<<grid, block, 0, st>>>(static_cast<const int16_t*>(src), static_cast<int16_t*>(dst), nx,
                                                       ny, nz, rows, 0, 0.0, 0.0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split(const double* x, float* hi, float* lo, long long n, cudaStream_t st) {
+    const int block = 256;
+    const int grid = 4 * 152;
+    k_split<<<grid, block, 0, st>>>(x, hi, lo, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_join(const float* hi, const float* lo, double* x, long long n, cudaStream_t st) {
+    const int block = 256;
+    const int grid = 4 * 152;
+    k_join<<<grid, block, 0, st>>>(hi, lo, x, n);
     return cudaGetLastError();
 }
 

@@ -58,7 +58,11 @@ bool valid_params(const pf_params* p) {
     if (p->nx > (1 << 20) || p->ny > (1 << 20) || (p->dim == 3 && p->nz > (1 << 14))) return false;
     if (p->dim == 2 && !(p->scheme == PF_S10 || p->scheme == PF_S21 || p->scheme == PF_SBAR21)) return false;
     if (p->dim == 3 && !(p->scheme == PF_S100 || p->scheme == PF_SBAR120)) return false;
-    if (p->precision != PF_F32 && p->precision != PF_F64) return false;
+    if (p->precision != PF_F32 && p->precision != PF_F64 && p->precision != PF_F32C) return false;
+    // the compensated FP32 state: 2D isothermal runs with mirror walls and the T1 time level
+    if (p->precision == PF_F32C && (p->dim != 2 || p->thermal != PF_ISOTHERMAL || p->bc_x != PF_BC_MIRROR ||
+                                    p->time_level != PF_T1))
+        return false;
     if (!(p->h > 0) || !(p->dt > 0) || !std::isfinite(p->h) || !std::isfinite(p->dt)) return false;
     if (!(p->k > 0 && p->k < 1)) return false;
     if (!(p->eps4 >= 0 && p->eps4 < 0.25)) return false;
@@ -67,6 +71,11 @@ bool valid_params(const pf_params* p) {
     if (p->bc_x != PF_BC_MIRROR && p->bc_x != PF_BC_PERIODIC) return false;
     if (p->thermal != PF_ISOTHERMAL && p->thermal != PF_FROZEN_GRADIENT) return false;
     if (p->time_level != PF_T1 && p->time_level != PF_T0) return false;
+    if (p->kernels != PF_FUSED && p->kernels != PF_TWO_KERNELS) return false;
+    // the two-kernel form: 2D, T0 time level, plain FP32 or FP64 fields
+    if (p->kernels == PF_TWO_KERNELS &&
+        (p->dim != 2 || p->time_level != PF_T0 || (p->precision != PF_F32 && p->precision != PF_F64)))
+        return false;
     double F1min = 1.0;
     if (p->thermal == PF_FROZEN_GRADIENT) {
         if (!(p->lT > 0) || !std::isfinite(p->lT) || !(p->Vp >= 0) || !std::isfinite(p->Vp) ||
@@ -86,7 +95,7 @@ bool valid_params(const pf_params* p) {
 }
 
 struct Layout {
-    size_t psi0, psi1, U0, U1, grain, rot, seeds, partials, result, work, rec, total;
+    size_t psi0, psi1, U0, U1, grain, rot, seeds, partials, result, work, rec, rate, total;
     size_t N;
     int esz, max_seeds, max_work;
 };
@@ -94,6 +103,9 @@ struct Layout {
 long long cells(const pf_params* p) { return (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1); }
 
 int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// precision code of the step kernels: 0 float, 1 double, 2 compensated float pairs
+int kprec(const pf_params& p) { return p.precision == PF_F64 ? 1 : (p.precision == PF_F32C ? 2 : 0); }
 
 // capacity of the work list: the smallest tile any compiled shape produces
 int max_work_items(const pf_params* p) {
@@ -104,7 +116,8 @@ int max_work_items(const pf_params* p) {
 Layout layout(const pf_params* p) {
     Layout L{};
     L.N = (size_t)cells(p);
-    L.esz = p->precision == PF_F64 ? 8 : 4;
+    // bytes per cell of one field and level: FP32C holds hi and lo halves
+    L.esz = p->precision == PF_F32 ? 4 : 8;
     L.max_seeds = p->max_seeds > 0 ? p->max_seeds : 64;
     L.max_work = max_work_items(p);
     size_t o = 0;
@@ -124,6 +137,7 @@ Layout layout(const pf_params* p) {
     L.result = take(sizeof(ObsPartial));
     L.work = take((size_t)L.max_work * sizeof(WorkItem));
     L.rec = take(sizeof(InstRec));
+    L.rate = p->kernels == PF_TWO_KERNELS ? take(L.N * L.esz) : 0;  // d psi/dt between the two kernels
     L.total = o;
     return L;
 }
@@ -155,6 +169,7 @@ struct pf_sim {
     ObsPartial* result;
     WorkItem* work;
     InstRec* rec;
+    void* rate;  // d psi/dt of the two-kernel form (nullptr when fused)
     int n_grains;
     std::vector<double> rot_h, centres_h;
     int64_t step;
@@ -200,11 +215,17 @@ bool ds_of(const pf_params& p) {
     return p.thermal == PF_FROZEN_GRADIENT || p.bc_x == PF_BC_PERIODIC || p.time_level == PF_T0;
 }
 
-int occupancy(const pf_sim* s) {
-    const int prec = s->p.precision == PF_F64 ? 1 : 0;
-    return s->p.dim == 2 ? occupancy_step2d(prec, s->p.scheme, s->bx, ds_of(s->p))
-                         : occupancy_step3d(prec, s->p.scheme, s->bx, s->by);
+// resident units of the step's kernel; for the two-kernel form those of the
+// pass with fewer, so that one persistent grid serves both passes
+int occupancy_of(const pf_params& p, int bx, int by) {
+    const int prec = kprec(p);
+    if (p.dim == 3) return occupancy_step3d(prec, p.scheme, bx, by);
+    if (p.kernels == PF_TWO_KERNELS)
+        return std::min(occupancy_step2d(prec, p.scheme, bx, ds_of(p), 1), occupancy_step2d(prec, p.scheme, bx, ds_of(p), 2));
+    return occupancy_step2d(prec, p.scheme, bx, ds_of(p));
 }
+
+int occupancy(const pf_sim* s) { return occupancy_of(s->p, s->bx, s->by); }
 
 InstRec make_rec(const pf_sim* s, int parity_offset) {
     InstRec r{};
@@ -214,6 +235,7 @@ InstRec make_rec(const pf_sim* s, int parity_offset) {
     r.U[1] = s->U[1];
     r.grain = s->grain;
     r.rot = s->rot;
+    r.rate = s->rate;
     r.nx = s->p.nx;
     r.ny = s->p.ny;
     r.nz = s->p.dim == 3 ? s->p.nz : 1;
@@ -289,13 +311,47 @@ int upload_rot(pf_sim* s) {
 
 // One step of a handle from step `step` (its parity selects the time level).
 bool launch_sim_step(const pf_sim* s, int64_t step) {
-    const int prec = s->p.precision == PF_F64 ? 1 : 0;
+    const int prec = kprec(s->p);
     const int lp = (int)(step & 1);
+    const StepClock clk{nullptr, nullptr, (long long)step};
+    if (s->p.dim == 2 && s->p.kernels == PF_TWO_KERNELS)
+        return launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp, clk, true, 1) &&
+               launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp, clk, true, 2);
     if (s->p.dim == 2)
-        return launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp,
-                             StepClock{nullptr, nullptr, (long long)step}, ds_of(s->p));
+        return launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp, clk,
+                             ds_of(s->p));
     return launch_step3d(prec, s->p.scheme, s->bx, s->by, s->grid, s->st, s->work, s->n_work, s->rec, lp,
                          StepClock{nullptr, nullptr, (long long)step});
+}
+
+// Compensated FP32 state (PF_F32C): the 8 bytes per cell of a level hold the
+// hi half (N floats) followed by the lo half.  Between steps the other level
+// is free, so FP64 copies of the current fields are formed there (join) and
+// FP64 fields from the host are split from there into the current level.
+float* lo_of(const pf_sim* s, void* hi) { return static_cast<float*>(hi) + s->L.N; }
+
+cudaError_t join_current(const pf_sim* s, bool psi, bool U) {
+    const int cur = (int)(s->step & 1), oth = cur ^ 1;
+    cudaError_t e = cudaSuccess;
+    if (psi)
+        e = launch_join(static_cast<const float*>(s->psi[cur]), lo_of(s, s->psi[cur]), static_cast<double*>(s->psi[oth]),
+                        (long long)s->L.N, s->st);
+    if (e == cudaSuccess && U)
+        e = launch_join(static_cast<const float*>(s->U[cur]), lo_of(s, s->U[cur]), static_cast<double*>(s->U[oth]),
+                        (long long)s->L.N, s->st);
+    return e;
+}
+
+cudaError_t split_into_current(const pf_sim* s, bool psi, bool U) {
+    const int cur = (int)(s->step & 1), oth = cur ^ 1;
+    cudaError_t e = cudaSuccess;
+    if (psi)
+        e = launch_split(static_cast<const double*>(s->psi[oth]), static_cast<float*>(s->psi[cur]), lo_of(s, s->psi[cur]),
+                         (long long)s->L.N, s->st);
+    if (e == cudaSuccess && U)
+        e = launch_split(static_cast<const double*>(s->U[oth]), static_cast<float*>(s->U[cur]), lo_of(s, s->U[cur]),
+                         (long long)s->L.N, s->st);
+    return e;
 }
 
 }  // namespace
@@ -332,6 +388,7 @@ int pf_create(const pf_params* p, void* dev_mem, size_t bytes, void* stream, pf_
     s->result = reinterpret_cast<ObsPartial*>(s->base + L.result);
     s->work = reinterpret_cast<WorkItem*>(s->base + L.work);
     s->rec = reinterpret_cast<InstRec*>(s->base + L.rec);
+    s->rate = p->kernels == PF_TWO_KERNELS ? s->base + L.rate : nullptr;
     s->n_grains = 1;
     s->rot_h.assign(9, 0.0);
     s->rot_h[0] = s->rot_h[4] = s->rot_h[8] = 1.0;
@@ -350,7 +407,20 @@ int pf_create(const pf_params* p, void* dev_mem, size_t bytes, void* stream, pf_
     if ((e = cudaMemsetAsync(s->grain, 0, L.N * sizeof(int16_t), s->st)) != cudaSuccess) { delete s; return cuda_fail(e, "memset grain"); }
     const int prec = p->precision == PF_F64 ? 1 : 0;
     if ((e = launch_fill(prec, s->psi[0], -1e3, (long long)L.N, s->st)) != cudaSuccess) { delete s; return cuda_fail(e, "fill psi"); }
-    if ((e = launch_fill(prec, s->U[0], p->U0, (long long)L.N, s->st)) != cudaSuccess) { delete s; return cuda_fail(e, "fill U"); }
+    if (p->precision == PF_F32C) {
+        // U0 = hi + lo exactly; psi = -1e3 is a float
+        const float u_hi = (float)p->U0;
+        const double u_lo = p->U0 - (double)u_hi;
+        if ((e = launch_fill(0, lo_of(s, s->psi[0]), 0.0, (long long)L.N, s->st)) != cudaSuccess ||
+            (e = launch_fill(0, s->U[0], (double)u_hi, (long long)L.N, s->st)) != cudaSuccess ||
+            (e = launch_fill(0, lo_of(s, s->U[0]), u_lo, (long long)L.N, s->st)) != cudaSuccess) {
+            delete s;
+            return cuda_fail(e, "fill compensated fields");
+        }
+    } else if ((e = launch_fill(prec, s->U[0], p->U0, (long long)L.N, s->st)) != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "fill U");
+    }
     if ((rc = upload_work(s)) != PF_OK) { delete s; return rc; }
     *out = s;
     return PF_OK;
@@ -390,8 +460,15 @@ int pf_init_seeds(pf_sim* s, int n_seeds, const pf_seed* seeds) {
     }
     CK(cudaMemcpyAsync(s->seeds, h.data(), n_seeds * sizeof(SeedDev), cudaMemcpyHostToDevice, s->st));
     const int cur = (int)(s->step & 1);
-    CK(launch_init_seeds(s->p.precision == PF_F64 ? 1 : 0, s->p.dim, s->p.nx, s->p.ny, s->p.nz, s->p.h, s->p.U0, s->seeds,
-                         n_seeds, s->psi[cur], s->U[cur], s->grain, s->st));
+    if (s->p.precision == PF_F32C) {
+        // FP64 seed fields in the free level, split into the current one
+        CK(launch_init_seeds(1, s->p.dim, s->p.nx, s->p.ny, s->p.nz, s->p.h, s->p.U0, s->seeds, n_seeds,
+                             s->psi[cur ^ 1], s->U[cur ^ 1], s->grain, s->st));
+        CK(split_into_current(s, true, true));
+    } else {
+        CK(launch_init_seeds(s->p.precision == PF_F64 ? 1 : 0, s->p.dim, s->p.nx, s->p.ny, s->p.nz, s->p.h, s->p.U0,
+                             s->seeds, n_seeds, s->psi[cur], s->U[cur], s->grain, s->st));
+    }
     CK(cudaStreamSynchronize(s->st));
     return PF_OK;
 }
@@ -435,8 +512,14 @@ int pf_step(pf_sim* s, int64_t n) {
     return PF_OK;
 }
 
-int pf_observe(pf_sim* s, int grain, pf_obs* out) {
-    if (!s || !out || grain < -2 || grain >= s->n_grains) return PF_ERR_INVALID;
+}  // extern "C"
+
+namespace {
+
+// Arguments of the observe reductions of grain g (-2: pulling axis, -1: all
+// cells, else one grain) of a handle; the compensated state is observed
+// through FP64 copies of hi + lo.
+int observe_args(pf_sim* s, int grain, ObsArgs& a) {
     const int dim = s->p.dim;
     const int gg = grain < 0 ? 0 : grain;
     const double* R = &s->rot_h[9 * gg];
@@ -446,25 +529,32 @@ int pf_observe(pf_sim* s, int grain, pf_obs* out) {
     if (grain == -2) {
         d[1] = 1.0;
     } else {
-        for (int a = 0; a < dim; ++a)
+        for (int ax = 0; ax < dim; ++ax)
             for (int sg = 1; sg >= -1; sg -= 2) {
-                const double yc = sg * R[3 + a];
+                const double yc = sg * R[3 + ax];
                 if (yc > best) {
                     best = yc;
-                    for (int q = 0; q < 3; ++q) d[q] = q < dim ? sg * R[q * 3 + a] : 0.0;
+                    for (int q = 0; q < 3; ++q) d[q] = q < dim ? sg * R[q * 3 + ax] : 0.0;
                 }
             }
     }
     int ea = 0;
-    for (int a = 1; a < dim; ++a)
-        if (std::fabs(d[a]) > std::fabs(d[ea])) ea = a;
+    for (int ax = 1; ax < dim; ++ax)
+        if (std::fabs(d[ax]) > std::fabs(d[ea])) ea = ax;
     const int es = d[ea] >= 0 ? 1 : -1;
-    ObsArgs a{};
+    a = ObsArgs{};
     const int cur = (int)(s->step & 1);
     a.psi = s->psi[cur];
     a.U = s->U[cur];
     a.grain = s->grain;
     a.prec = s->p.precision == PF_F64 ? 1 : 0;
+    if (s->p.precision == PF_F32C) {
+        // the reductions read FP64 copies of hi + lo
+        CK(join_current(s, true, true));
+        a.psi = s->psi[cur ^ 1];
+        a.U = s->U[cur ^ 1];
+        a.prec = 1;
+    }
     a.dim = dim;
     a.nx = s->p.nx;
     a.ny = s->p.ny;
@@ -478,10 +568,12 @@ int pf_observe(pf_sim* s, int grain, pf_obs* out) {
     }
     a.ea = ea;
     a.es = es;
-    CK(launch_observe(a, s->partials, s->result, s->st));
-    ObsPartial r;
-    CK(cudaMemcpyAsync(&r, s->result, sizeof(r), cudaMemcpyDeviceToHost, s->st));
-    CK(cudaStreamSynchronize(s->st));
+    return PF_OK;
+}
+
+// Fill *out from the reduced record r and advance the tip history of the slot.
+int observe_finish(pf_sim* s, int grain, const ObsArgs& a, const ObsPartial& r, pf_obs* out) {
+    const int dim = s->p.dim;
     std::memset(out, 0, sizeof(*out));
     out->step = s->step;
     out->t = (double)s->step * s->p.dt;
@@ -513,10 +605,30 @@ int pf_observe(pf_sim* s, int grain, pf_obs* out) {
     return r.nonfinite > 0 ? PF_ERR_NONFINITE : PF_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int pf_observe(pf_sim* s, int grain, pf_obs* out) {
+    if (!s || !out || grain < -2 || grain >= s->n_grains) return PF_ERR_INVALID;
+    ObsArgs a;
+    int rc = observe_args(s, grain, a);
+    if (rc != PF_OK) return rc;
+    CK(launch_observe(a, s->partials, s->result, s->st));
+    ObsPartial r;
+    CK(cudaMemcpyAsync(&r, s->result, sizeof(r), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return observe_finish(s, grain, a, r, out);
+}
+
 int pf_get_fields(pf_sim* s, void* psi_host, void* U_host) {
     if (!s || (!psi_host && !U_host)) return PF_ERR_INVALID;
-    const int cur = (int)(s->step & 1);
+    int cur = (int)(s->step & 1);
     const size_t b = s->L.N * s->L.esz;
+    if (s->p.precision == PF_F32C) {  // FP64 host arrays: hi + lo joined in the free level
+        CK(join_current(s, psi_host != nullptr, U_host != nullptr));
+        cur ^= 1;
+    }
     if (psi_host) CK(cudaMemcpyAsync(psi_host, s->psi[cur], b, cudaMemcpyDeviceToHost, s->st));
     if (U_host) CK(cudaMemcpyAsync(U_host, s->U[cur], b, cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
@@ -533,6 +645,11 @@ int pf_tip_radius(pf_sim* s, int grain, const double tip[3], double v_tip, pf_ti
     const int cur = (int)(s->step & 1);
     a.psi = s->psi[cur];
     a.prec = s->p.precision == PF_F64 ? 1 : 0;
+    if (s->p.precision == PF_F32C) {
+        CK(join_current(s, true, false));
+        a.psi = s->psi[cur ^ 1];
+        a.prec = 1;
+    }
     a.dim = dim;
     a.nx = s->p.nx;
     a.ny = s->p.ny;
@@ -567,27 +684,35 @@ int pf_tip_radius(pf_sim* s, int grain, const double tip[3], double v_tip, pf_ti
 
 int pf_set_fields(pf_sim* s, const void* psi_host, const void* U_host) {
     if (!s || (!psi_host && !U_host)) return PF_ERR_INVALID;
-    const int cur = (int)(s->step & 1);
+    const bool cmp = s->p.precision == PF_F32C;  // FP64 host arrays, split from the free level
+    const int cur = (int)(s->step & 1), dst = cmp ? cur ^ 1 : cur;
     const size_t b = s->L.N * s->L.esz;
-    if (psi_host) CK(cudaMemcpyAsync(s->psi[cur], psi_host, b, cudaMemcpyHostToDevice, s->st));
-    if (U_host) CK(cudaMemcpyAsync(s->U[cur], U_host, b, cudaMemcpyHostToDevice, s->st));
+    if (psi_host) CK(cudaMemcpyAsync(s->psi[dst], psi_host, b, cudaMemcpyHostToDevice, s->st));
+    if (U_host) CK(cudaMemcpyAsync(s->U[dst], U_host, b, cudaMemcpyHostToDevice, s->st));
+    if (cmp) CK(split_into_current(s, psi_host != nullptr, U_host != nullptr));
     CK(cudaStreamSynchronize(s->st));
     return PF_OK;
 }
 
 int pf_set_fields_async(pf_sim* s, const void* psi_host, const void* U_host) {
     if (!s || (!psi_host && !U_host)) return PF_ERR_INVALID;
-    const int cur = (int)(s->step & 1);
+    const bool cmp = s->p.precision == PF_F32C;
+    const int cur = (int)(s->step & 1), dst = cmp ? cur ^ 1 : cur;
     const size_t b = s->L.N * s->L.esz;
-    if (psi_host) CK(cudaMemcpyAsync(s->psi[cur], psi_host, b, cudaMemcpyHostToDevice, s->st));
-    if (U_host) CK(cudaMemcpyAsync(s->U[cur], U_host, b, cudaMemcpyHostToDevice, s->st));
+    if (psi_host) CK(cudaMemcpyAsync(s->psi[dst], psi_host, b, cudaMemcpyHostToDevice, s->st));
+    if (U_host) CK(cudaMemcpyAsync(s->U[dst], U_host, b, cudaMemcpyHostToDevice, s->st));
+    if (cmp) CK(split_into_current(s, psi_host != nullptr, U_host != nullptr));
     return PF_OK;
 }
 
 int pf_get_fields_async(pf_sim* s, void* psi_host, void* U_host) {
     if (!s || (!psi_host && !U_host)) return PF_ERR_INVALID;
-    const int cur = (int)(s->step & 1);
+    int cur = (int)(s->step & 1);
     const size_t b = s->L.N * s->L.esz;
+    if (s->p.precision == PF_F32C) {
+        CK(join_current(s, psi_host != nullptr, U_host != nullptr));
+        cur ^= 1;
+    }
     if (psi_host) CK(cudaMemcpyAsync(psi_host, s->psi[cur], b, cudaMemcpyDeviceToHost, s->st));
     if (U_host) CK(cudaMemcpyAsync(U_host, s->U[cur], b, cudaMemcpyDeviceToHost, s->st));
     return PF_OK;
@@ -622,7 +747,7 @@ int pf_set_step(pf_sim* s, int64_t step) {
 }
 
 int pf_shift_frame(pf_sim* s, int rows) {
-    if (!s || rows <= 0 || rows >= s->p.ny) return PF_ERR_INVALID;
+    if (!s || rows <= 0 || rows >= s->p.ny || s->p.precision == PF_F32C) return PF_ERR_INVALID;
     if (s->group) return PF_ERR_STATE;
     if (s->p.thermal == PF_FROZEN_GRADIENT) {
         // the moved frame must pass the creation checks (F1 = 1 - (1-k) zeta >= 0.05 over the grid,
@@ -835,7 +960,8 @@ struct pf_group {
     bool dirty;
     struct Cls {
         int dim, scheme, prec, bx, by, w0, n, grid;
-        bool ds;  // 2D kernel variant with frozen temperature / periodic x
+        bool ds;   // 2D kernel variant with frozen temperature / periodic x
+        bool two;  // two-kernel form: the psi pass, then the U pass
     };
     std::vector<Cls> classes;
     // step counter of frozen-temperature members: member m is at step
@@ -843,6 +969,7 @@ struct pf_group {
     // launch (also inside captured graphs) when any member is thermal
     long long* clock;
     long long* step_base;
+    ObsPartial* obs;  // one reduced observe record per member slot
     bool thermal_any;
     cudaGraphExec_t graph;
     int graph_len;
@@ -860,7 +987,8 @@ int group_rebuild(pf_group* g) {
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
     auto key = [&](int i) {
         const pf_sim* s = g->members[i];
-        return ((long long)ds_of(s->p) << 48) | ((long long)s->p.dim << 40) | ((long long)s->p.scheme << 32) |
+        return ((long long)s->p.kernels << 52) | ((long long)ds_of(s->p) << 48) | ((long long)s->p.dim << 40) |
+               ((long long)s->p.scheme << 32) |
                ((long long)s->p.precision << 24) | ((long long)s->bx << 12) | (long long)s->by;
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
@@ -873,8 +1001,8 @@ int group_rebuild(pf_group* g) {
         const pf_sim* s = g->members[i];
         const long long k = key(i);
         if (k != prev) {
-            pf_group::Cls c{s->p.dim, s->p.scheme, s->p.precision == PF_F64 ? 1 : 0, s->bx, s->by, (int)work.size(), 0, 0,
-                            ds_of(s->p)};
+            pf_group::Cls c{s->p.dim, s->p.scheme, kprec(s->p), s->bx, s->by, (int)work.size(), 0, 0,
+                            ds_of(s->p), s->p.kernels == PF_TWO_KERNELS};
             g->classes.push_back(c);
             prev = k;
         }
@@ -883,7 +1011,10 @@ int group_rebuild(pf_group* g) {
     }
     if ((int)work.size() > g->max_work) return PF_ERR_BUDGET;
     for (auto& c : g->classes) {
-        int occ = c.dim == 2 ? occupancy_step2d(c.prec, c.scheme, c.bx, c.ds) : occupancy_step3d(c.prec, c.scheme, c.bx, c.by);
+        int occ = c.dim == 3 ? occupancy_step3d(c.prec, c.scheme, c.bx, c.by)
+                  : c.two    ? std::min(occupancy_step2d(c.prec, c.scheme, c.bx, c.ds, 1),
+                                        occupancy_step2d(c.prec, c.scheme, c.bx, c.ds, 2))
+                             : occupancy_step2d(c.prec, c.scheme, c.bx, c.ds);
         if (occ <= 0) return PF_ERR_INVALID;
         c.grid = std::min(c.n, occ * num_sms());
     }
@@ -909,10 +1040,18 @@ bool group_launch_once(pf_group* g, int launch_parity) {
     const StepClock clk{g->clock, g->step_base, 0};
     for (const auto& c : g->classes) {
         if (c.n == 0) continue;
-        bool ok = c.dim == 2 ? launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs,
-                                             launch_parity, clk, c.ds)
-                             : launch_step3d(c.prec, c.scheme, c.bx, c.by, c.grid, g->st, g->work + c.w0, c.n, g->recs,
-                                             launch_parity, clk);
+        bool ok;
+        if (c.dim == 3)
+            ok = launch_step3d(c.prec, c.scheme, c.bx, c.by, c.grid, g->st, g->work + c.w0, c.n, g->recs, launch_parity,
+                               clk);
+        else if (c.two)
+            ok = launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs, launch_parity, clk,
+                               true, 1) &&
+                 launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs, launch_parity, clk,
+                               true, 2);
+        else
+            ok = launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs, launch_parity, clk,
+                               c.ds);
         if (!ok) return false;
     }
     if (g->thermal_any && launch_tick(g->clock, g->st) != cudaSuccess) return false;
@@ -926,7 +1065,8 @@ extern "C" {
 size_t pf_group_required_bytes(int max_instances, int max_work) {
     if (max_instances < 1 || max_work < 1) return 0;
     return align256((size_t)max_instances * sizeof(InstRec)) + align256((size_t)max_work * sizeof(WorkItem)) +
-           align256((size_t)(max_instances + 1) * sizeof(long long));
+           align256((size_t)(max_instances + 1) * sizeof(long long)) +
+           align256((size_t)max_instances * sizeof(ObsPartial));
 }
 
 int pf_group_work_items(const pf_sim* s) {
@@ -952,6 +1092,8 @@ int pf_group_create(int max_instances, int max_work, void* dev_mem, size_t bytes
     g->clock = reinterpret_cast<long long*>(g->base + align256((size_t)max_instances * sizeof(InstRec)) +
                                             align256((size_t)max_work * sizeof(WorkItem)));
     g->step_base = g->clock + 1;
+    g->obs = reinterpret_cast<ObsPartial*>(reinterpret_cast<char*>(g->clock) +
+                                           align256((size_t)(max_instances + 1) * sizeof(long long)));
     g->thermal_any = false;
     g->launches = 0;
     g->dirty = true;
@@ -1039,6 +1181,34 @@ int pf_group_step(pf_group* g, int64_t n, int use_graph) {
 }
 
 int pf_group_size(const pf_group* g) { return g ? (int)g->members.size() : PF_ERR_INVALID; }
+
+int pf_group_observe(pf_group* g, int grain, pf_obs* out) {
+    if (!g || !out || grain < -2) return PF_ERR_INVALID;
+    for (pf_sim* s : g->members)
+        if (grain >= s->n_grains) return PF_ERR_INVALID;
+    const size_t n = g->members.size();
+    if (n == 0) return PF_OK;
+    std::vector<ObsArgs> args(n);
+    for (size_t i = 0; i < n; ++i) {
+        pf_sim* s = g->members[i];
+        // the member's fields are current on the group's stream; its partials
+        // are its own, the reduced record goes to the group's slot i
+        const cudaStream_t keep = s->st;
+        s->st = g->st;
+        int rc = observe_args(s, grain, args[i]);
+        cudaError_t e = rc == PF_OK ? launch_observe(args[i], s->partials, g->obs + i, g->st) : cudaSuccess;
+        s->st = keep;
+        if (rc != PF_OK) return rc;
+        if (e != cudaSuccess) return cuda_fail(e, "launch_observe");
+    }
+    std::vector<ObsPartial> r(n);
+    CK(cudaMemcpyAsync(r.data(), g->obs, n * sizeof(ObsPartial), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    int status = PF_OK;
+    for (size_t i = 0; i < n; ++i)
+        if (observe_finish(g->members[i], grain, args[i], r[i], out + i) != PF_OK) status = PF_ERR_NONFINITE;
+    return status;
+}
 
 int pf_group_destroy(pf_group* g) {
     if (!g) return PF_ERR_INVALID;

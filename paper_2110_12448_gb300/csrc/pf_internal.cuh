@@ -39,6 +39,7 @@ struct InstRec {
     void* U[2];
     const int16_t* grain;  // per-cell grain index
     const void* rot;       // n_grains x 9, crystal -> lab, in the field precision
+    void* rate;            // d psi/dt of the two-kernel form (nullptr when fused)
     int32_t nx, ny, nz, parity_offset;
     int32_t thermal;  // 1: frozen temperature along +y (2D)
     int32_t bcx;      // 1: periodic x (2D)
@@ -108,7 +109,9 @@ __device__ __forceinline__ int mirror_idx(int i, int n) {
     return i;
 }
 
-// Launchers (defined in step2d.cu / step3d.cu).  prec: 0 float, 1 double.
+// Launchers (defined in step2d.cu / step3d.cu).  prec: 0 float, 1 double,
+// 2 compensated float pairs (2D isothermal only; lo half right after the hi
+// half of each level).
 // Return false if (prec, scheme, block) has no compiled kernel.
 // Step counter of the instances in a launch (only read for frozen-temperature
 // instances): with clock == nullptr every instance is at step `step`;
@@ -119,15 +122,17 @@ struct StepClock {
     const long long* base;
     long long step;
 };
+// mode: 0 the fused step; 1, 2 the psi and U passes of the two-kernel form
+// (T0 time level, the ds variant, prec 0 or 1)
 bool launch_step2d(int prec, int scheme, int bx, int grid, cudaStream_t st, const WorkItem* work, int n_work,
-                   const InstRec* recs, int launch_parity, StepClock clk, bool ds);
+                   const InstRec* recs, int launch_parity, StepClock clk, bool ds, int mode = 0);
 bool launch_step3d(int prec, int scheme, int bx, int by, int grid, cudaStream_t st, const WorkItem* work,
                    int n_work, const InstRec* recs, int launch_parity, StepClock clk);
 // clock += 1 (one thread)
 cudaError_t launch_tick(long long* clock, cudaStream_t st);
 // Blocks of the fused kernel that fit on one SM (0 if not compiled).
 // ds: the kernel variant for frozen-temperature / periodic-x instances
-int occupancy_step2d(int prec, int scheme, int bx, bool ds);
+int occupancy_step2d(int prec, int scheme, int bx, bool ds, int mode = 0);
 int occupancy_step3d(int prec, int scheme, int bx, int by);
 
 // Observation / initialisation kernels (observe.cu).
@@ -172,6 +177,9 @@ struct SeedDev {
 cudaError_t launch_init_seeds(int prec, int dim, int nx, int ny, int nz, double h, double U0, const SeedDev* seeds,
                               int n_seeds, void* psi, void* U, int16_t* grain, cudaStream_t st);
 cudaError_t launch_fill(int prec, void* p, double v, long long n, cudaStream_t st);
+// compensated FP32 state: FP64 -> (hi, lo) and back
+cudaError_t launch_split(const double* x, float* hi, float* lo, long long n, cudaStream_t st);
+cudaError_t launch_join(const float* hi, const float* lo, double* x, long long n, cudaStream_t st);
 // frame shift of one field toward -y (kind 0: float, 1: double, 2: int16 grain index); vacated
 // rows, k beyond the last: mode 0 copy the last row, 1 continue it by a k, 3 a + (last - a) exp(-b k)
 cudaError_t launch_shift_rows(int kind, const void* src, void* dst, int nx, int ny, int nz, int rows, int mode,

@@ -242,6 +242,44 @@ template <typename T> __device__ __forceinline__ V<T> guarded_div2(V<T> f, V<T> 
     return mk(m.x() * m.x() * hh < Guard<T>::v ? T(0) : q.x(), m.y() * m.y() * hh < Guard<T>::v ? T(0) : q.y());
 }
 
+// ---------------------------------------------------------------------------
+// compensated state (precision PF_F32C): psi and U carried as FP32 pairs
+// hi + lo (about 48 significant bits) while the rates use FP32 arithmetic.
+// Three places decide the accuracy of a step beyond the rounding of the
+// rates: the state update, phi, and delta phi.
+// ---------------------------------------------------------------------------
+// (hi, lo) + d: Knuth's two-sum of hi and d, the rounding error folded into
+// lo, renormalised by Dekker's fast two-sum (the _rn intrinsics are never
+// contracted into FMAs, which would break the error-free transformations)
+__device__ __forceinline__ void cadd(float hi, float lo, float d, float& ho, float& lo_o) {
+    const float s = __fadd_rn(hi, d);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+    const float l = __fadd_rn(lo, e);
+    ho = __fadd_rn(s, l);
+    lo_o = __fsub_rn(l, __fsub_rn(ho, s));
+}
+template <typename T> __device__ __forceinline__ void cadd2(V<T> hi, V<T> lo, V<T> d, V<T>& ho, V<T>& lo_o) {
+    float a, b, c, e;
+    cadd((float)hi.x(), (float)lo.x(), (float)d.x(), a, b);
+    cadd((float)hi.y(), (float)lo.y(), (float)d.y(), c, e);
+    ho = mk(T(a), T(c));
+    lo_o = mk(T(b), T(e));
+}
+// phi = tanh((hi + lo) / sqrt2) with the library tanh (a few ulp); the
+// argument is rounded once
+__device__ __forceinline__ float phi_acc(float hi, float lo) {
+    const float c = 0.70710678118654752440f;
+    return tanhf(fmaf(hi, c, lo * c));
+}
+// phi(psi + d) - phi(psi) = T (1 - phi^2) / (1 + T phi) with T = tanh(d / sqrt2),
+// the addition theorem of tanh: the increment keeps its relative accuracy,
+// unlike the difference phi' - phi of two rounded values
+__device__ __forceinline__ float dphi_acc(float phi, float d) {
+    const float T = tanhf(d * 0.70710678118654752440f);
+    return __fdiv_rn(T * fmaf(-phi, phi, 1.0f), fmaf(T, phi, 1.0f));
+}
+
 template <typename T> struct ConstOf;
 template <> struct ConstOf<float> {
     static __device__ __forceinline__ const float* get(const InstRec& r) { return r.cf; }
@@ -315,12 +353,23 @@ __device__ __forceinline__ void store_pair(T* __restrict__ row, int c, int nx, b
 #ifndef PF_STEP2D_MIN_BLOCKS_F32
 #define PF_STEP2D_MIN_BLOCKS_F32 16
 #endif
+// the compensated kernel holds the lo rows as well: a 255-register cap
+#ifndef PF_STEP2D_MIN_BLOCKS_F32C
+#define PF_STEP2D_MIN_BLOCKS_F32C 8
+#endif
 
 // DS = false: isothermal instances with mirror walls (the flags below are
 // compile-time false and their code disappears); DS = true: instances with a
-// frozen temperature and/or periodic x.
-template <typename T, int S, bool DS>
-__global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D_MIN_BLOCKS_F32 : 1)
+// frozen temperature and/or periodic x.  CMP = true (T = float, DS = false):
+// the compensated state of precision PF_F32C, the lo halves of psi and U
+// stored right after the hi halves of each time level.  MODE (T0 time level
+// only, DS = true): 0 the fused step; 1 the psi pass of the two-kernel form of
+// Sec. 3.3.1, which stores psi' and d psi/dt (InstRec::rate); 2 its U pass,
+// which reads d psi/dt back instead of recomputing phase 1 (U' needs only
+// psi^n, U^n and d psi/dt^n at the T0 level).
+template <typename T, int S, bool DS, bool CMP, int MODE = 0>
+__global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
+                                  sizeof(T) == 4 ? (CMP ? PF_STEP2D_MIN_BLOCKS_F32C : PF_STEP2D_MIN_BLOCKS_F32) : 1)
     k_step2d(const WorkItem* __restrict__ work, int n_work, const InstRec* __restrict__ recs, int launch_parity,
              StepClock clk) {
     constexpr bool ISO = (S == S21 || S == SBAR21);
@@ -339,6 +388,13 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         const T* __restrict__ Uf = static_cast<const T*>(rec.U[par]);
         T* __restrict__ psi_o = static_cast<T*>(rec.psi[par ^ 1]);
         T* __restrict__ U_o = static_cast<T*>(rec.U[par ^ 1]);
+        // compensated state: the lo half of a level follows its hi half
+        const size_t NN = (size_t)nx * ny;
+        const T* __restrict__ psiL = psi + NN;
+        const T* __restrict__ UfL = Uf + NN;
+        T* __restrict__ psi_oL = psi_o + NN;
+        T* __restrict__ U_oL = U_o + NN;
+        T* __restrict__ rate_b = static_cast<T*>(rec.rate);  // d psi/dt of the two-kernel form
         const int16_t* __restrict__ grain = rec.grain;
         const T* __restrict__ rot = static_cast<const T*>(rec.rot);
         const T* cst = ConstOf<T>::get(rec);
@@ -398,6 +454,16 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             o.m2 = o.p2 = T(0);
             return o;
         };
+        // compensated state: phi of the own columns from hi + lo
+        auto phi_row_c = [&](const Row<T>& p, V<T> lo) {
+            Row<T> o;
+            o.l = (T)phi_acc((float)p.l, (float)lo.x());
+            o.r = (T)phi_acc((float)p.r, (float)lo.y());
+            o.m1 = shup(o.r);
+            o.p1 = shdn(o.l);
+            o.m2 = o.p2 = T(0);
+            return o;
+        };
         // delta phi row: ghost columns take their mirror cell's value (only in
         // warps that hold ghost columns), halo columns come from the neighbours
         auto dphi_row = [&](V<T> d) {
@@ -442,7 +508,20 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         // phase 1 at real row p (psi rows Pm = p-1, P0 = p, Pp = p+1), grains
         // gL, gR: returns psi' and phi' of the own columns and delta phi.
         auto phase1 = [&](int p, const Row<T>& Pm, const Row<T>& P0, const Row<T>& Pp, const Row<T>& ph0,
-                          const Row<T>& u0, int gL, int gR, V<T>& psin, V<T>& phin, V<T>& dph) {
+                          const Row<T>& u0, int gL, int gR, V<T> lo0, V<T>& psin, V<T>& psin_lo, V<T>& phin,
+                          V<T>& dph, V<T>& rate_o) {
+            if constexpr (MODE == 2) {
+                // U pass of the two-kernel form: d psi/dt^n from the psi pass,
+                // T0 increment dt (1 - phi^2)/sqrt2 d psi/dt, phi^n on the left
+                T ra, rb;
+                load_pair<T>(rate_b + (size_t)PF_CHK(p, ny) * nx, cL, nx, vec, per, ra, rb);
+                const V<T> ph = ph0.C();
+                rate_o = mk(ra, rb);
+                dph = bc<T>(dt * T(0.70710678118654752440)) * (bc<T>(T(1)) - ph * ph) * rate_o;
+                phin = ph;
+                psin = psin_lo = bc<T>(T(0));
+                return;
+            }
             set_rot(gL, gR);
             const int gM = shup(gR);  // grain of column L-1
             const V<T> W0 = P0.W(), C0 = P0.C(), E0 = P0.E();
@@ -495,10 +574,23 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
                 u = u + bc<T>(z);
                 iF1 = M<T>::rcp(T(1) - omk * z);
             }
+            if constexpr (CMP) {
+                // 1 - phi^2 rounded once; psi' = (hi + lo) + dt rate kept exactly;
+                // delta phi from the addition theorem, phi' = phi + delta phi
+                const V<T> src = bc<T>(SQ2) * (ph - bc<T>(lam) * fma(ph * bc<T>(T(-1)), ph, bc<T>(T(1))) * u);
+                const V<T> rate = (L + N + src) * rcp2(ac * ac) - bc<T>(SQ2) * ph * G;
+                const V<T> d = bc<T>(dt) * rate;
+                cadd2<T>(C0, lo0, d, psin, psin_lo);
+                dph = mk((T)dphi_acc((float)ph.x(), (float)d.x()), (T)dphi_acc((float)ph.y(), (float)d.y()));
+                phin = ph + dph;
+                return;
+            }
             const V<T> src = bc<T>(SQ2) * (ph - bc<T>(lam) * (bc<T>(T(1)) - ph * ph) * u);
             V<T> rate = (L + N + src) * rcp2(ac * ac) - bc<T>(SQ2) * ph * G;
             if (DS) rate = rate * bc<T>(iF1);
+            rate_o = rate;
             psin = fma(bc<T>(dt), rate, C0);
+            psin_lo = lo0;
             phin = mk(M<T>::tanh_isq2(psin.x()), M<T>::tanh_isq2(psin.y()));
             dph = phin - ph;
             if (DS) {
@@ -521,13 +613,19 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         // and updates the carries.  need_x = false skips S_{2,1}'s x-face
         // magnitudes, which would read row q-2.
         auto fluxes = [&](const Row<T>& aD0, const Row<T>& aD1, const Row<T>& aA0, const Row<T>& aA1,
-                          const Row<T>& bU0, const Row<T>& bU1, const Row<T>* Pq, bool need_x, V<T>& sD, V<T>& sA) {
+                          const Row<T>& bU0, const Row<T>& bU1, const Row<T>& bL0, const Row<T>& bL1, const Row<T>* Pq,
+                          bool need_x, V<T>& sD, V<T>& sA) {
             const Row<T>& b0 = Pq[2];
             const Row<T>& b1 = Pq[3];
+            // differences of U; the compensated state adds those of the lo halves
+            auto dU = [&](V<T> hi_diff, V<T> lo_diff) -> V<T> {
+                if constexpr (CMP) return hi_diff + lo_diff;
+                return hi_diff;
+            };
             if (S == S10) {
                 const V<T> half = bc<T>(T(0.5));
-                const V<T> fxD = half * (aD0.C() + aD0.E()) * (bU0.E() - bU0.C());
-                const V<T> fyD = half * (aD0.C() + aD1.C()) * (bU1.C() - bU0.C());
+                const V<T> fxD = half * (aD0.C() + aD0.E()) * dU(bU0.E() - bU0.C(), bL0.E() - bL0.C());
+                const V<T> fyD = half * (aD0.C() + aD1.C()) * dU(bU1.C() - bU0.C(), bL1.C() - bL0.C());
                 const Row<T>& bm = Pq[1];
                 const V<T> dxp = b0.E() - b0.C(), dyp = b1.C() - b0.C();
                 const V<T> gx = dxp * bc<T>(ih), gy = ((b1.E() + b1.C()) - (bm.E() + bm.C())) * bc<T>(i4h);
@@ -550,10 +648,10 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             const V<T> KC_A = q4 * ((aA0.C() + aA0.E()) + (aA1.C() + aA1.E()));
             const V<T> KW_A = q4 * ((aA0.W() + aA0.C()) + (aA1.W() + aA1.C()));
             // <10> faces x+, y+ (weight sums of Eq. flux_10) and <11> corners ++, -+
-            const V<T> u0c = bU0.C();
-            const V<T> FXpD = ((aD0.C() + aD0.E()) + (KC_D + cK_D)) * (bU0.E() - u0c);
-            const V<T> FYpD = ((aD0.C() + aD1.C()) + (KC_D + KW_D)) * (bU1.C() - u0c);
-            const V<T> FPPD = KC_D * (bU1.E() - u0c), FMPD = KW_D * (bU1.W() - u0c);
+            const V<T> u0c = bU0.C(), l0c = bL0.C();
+            const V<T> FXpD = ((aD0.C() + aD0.E()) + (KC_D + cK_D)) * dU(bU0.E() - u0c, bL0.E() - l0c);
+            const V<T> FYpD = ((aD0.C() + aD1.C()) + (KC_D + KW_D)) * dU(bU1.C() - u0c, bL1.C() - l0c);
+            const V<T> FPPD = KC_D * dU(bU1.E() - u0c, bL1.E() - l0c), FMPD = KW_D * dU(bU1.W() - u0c, bL1.W() - l0c);
             const V<T> p0c = b0.C();
             V<T> FXpA = ((aA0.C() + aA0.E()) + (KC_A + cK_A)) * (b0.E() - p0c);
             V<T> FYpA = ((aA0.C() + aA1.C()) + (KC_A + KW_A)) * (b1.C() - p0c);
@@ -614,7 +712,15 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
         Row<T> P[5];      // psi rows r-2 .. r+2 (iteration r)
         Row<T> PH1, UU0, UU1, DP0;
         Row<T> AD0, AA0;  // alpha rows of row r
+        Row<T> UL0, UL1;  // compensated state: lo halves of U rows r, r+1
+        V<T> PL1 = bc<T>(T(0));  // compensated state: lo half of psi, own columns of row r+1
         V<T> phin_cur;    // phi' at row r
+        auto psi_store = [&](int row, V<T> hi, V<T> lo, V<T> rt) {
+            if constexpr (MODE == 2) return;  // the U pass leaves psi' to the psi pass
+            store_pair<T>(psi_o + (size_t)PF_CHK(row, ny) * nx, cL, nx, vec, outL, outR, hi);
+            if constexpr (CMP) store_pair<T>(psi_oL + (size_t)PF_CHK(row, ny) * nx, cL, nx, vec, outL, outR, lo);
+            if constexpr (MODE == 1) store_pair<T>(rate_b + (size_t)PF_CHK(row, ny) * nx, cL, nx, vec, outL, outR, rt);
+        };
         {
             // psi rows y0-3 .. y0+1 (row y0-3 is read only by S_{2,1}'s x-face
             // magnitudes, which the prologue skips)
@@ -624,79 +730,127 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
                 P[i] = make_row(a, b, S == S21);
             }
             P[0] = P[1];
-            const Row<T> phm = phi_row(P[2]), ph0 = phi_row(P[3]);
+            V<T> plm = bc<T>(T(0)), pl0 = bc<T>(T(0));
+            Row<T> ulm = make_row(T(0), T(0), false), ul0 = ulm;
+            if constexpr (CMP) {
+                fetch_row(psiL, y0 - 1, a, b);
+                plm = mk(a, b);
+                fetch_row(psiL, y0, a, b);
+                pl0 = mk(a, b);
+                fetch_row(UfL, y0 - 1, a, b);
+                ulm = make_row(a, b, false);
+                fetch_row(UfL, y0, a, b);
+                ul0 = make_row(a, b, false);
+            }
+            const Row<T> phm = CMP ? phi_row_c(P[2], plm) : phi_row(P[2]);
+            const Row<T> ph0 = CMP ? phi_row_c(P[3], pl0) : phi_row(P[3]);
             fetch_row(Uf, y0 - 1, a, b);
             const Row<T> um = make_row(a, b, false);
             fetch_row(Uf, y0, a, b);
             const Row<T> u0 = make_row(a, b, false);
-            // phase 1 at rows y0-1 and y0; the ghost row -1 copies row 0
+            // phase 1 at rows y0-1 and y0; the ghost row -1 copies row 0 (the
+            // psi pass of the two-kernel form needs no row y0-1: no U fluxes)
             int gL, gR;
-            V<T> psn, fn, dm = bc<T>(T(0)), d0;
+            V<T> psn, psnl, fn, dm = bc<T>(T(0)), d0, rt;
             const bool ghost = (y0 - 1) < 0;
-            if (!ghost) {
+            if (!ghost && MODE != 1) {
                 load_grain_pair(grain + (size_t)PF_CHK((y0 - 1), ny) * nx, cL, nx, vec, per, gL, gR);
-                phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, psn, fn, dm);
+                phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, plm, psn, psnl, fn, dm, rt);
             }
             load_grain_pair(grain + (size_t)PF_CHK(y0, ny) * nx, cL, nx, vec, per, gL, gR);
-            phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, psn, fn, d0);
+            phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, pl0, psn, psnl, fn, d0, rt);
             if (ghost) dm = d0;
             phin_cur = fn;
-            if (y0 < y1) store_pair<T>(psi_o + (size_t)PF_CHK(y0, ny) * nx, cL, nx, vec, outL, outR, psn);
+            if (y0 < y1) psi_store(y0, psn, psnl, rt);
             const Row<T> dmr = dphi_row(dm), d0r = dphi_row(d0);
             // phase-2 fluxes at row y0-1 (carries only); psi rows y0-3 .. y0+1
             const Row<T> aDm = alphaD(phm), aAm = alphaA(um, dmr);
             AD0 = alphaD(ph0);
             AA0 = alphaA(u0, d0r);
             V<T> s0, s1;
-            fluxes(aDm, AD0, aAm, AA0, um, u0, P, false, s0, s1);
+            if constexpr (MODE != 1) fluxes(aDm, AD0, aAm, AA0, um, u0, ulm, ul0, P, false, s0, s1);
             P[0] = P[1];
             P[1] = P[2];
             P[2] = P[3];
             P[3] = P[4];
             UU0 = u0;
+            UL0 = ul0;
             DP0 = d0r;
         }
 
-        // prefetch psi row y0+2 and U, grain row y0+1
-        T nPa, nPb, nUa, nUb;
+        // prefetch psi row y0+2 and U, grain row y0+1 (compensated state: the
+        // lo halves of psi and U of row y0+1)
+        T nPa, nPb, nUa, nUb, nPLa = T(0), nPLb = T(0), nULa = T(0), nULb = T(0);
         int nGa = 0, nGb = 0;
         fetch_row(psi, y0 + 2, nPa, nPb);
         fetch_row(Uf, y0 + 1, nUa, nUb);
+        if constexpr (CMP) {
+            fetch_row(psiL, y0 + 1, nPLa, nPLb);
+            fetch_row(UfL, y0 + 1, nULa, nULb);
+        }
         if (y0 + 1 < ny) load_grain_pair(grain + (size_t)PF_CHK((y0 + 1), ny) * nx, cL, nx, vec, per, nGa, nGb);
 
         // ---------------- sweep ----------------
         for (int r = y0; r < y1; ++r) {
             P[4] = make_row(nPa, nPb, S == S21);
             UU1 = make_row(nUa, nUb, false);
-            PH1 = phi_row(P[3]);
+            if constexpr (CMP) {
+                PL1 = mk(nPLa, nPLb);
+                UL1 = make_row(nULa, nULb, false);
+            }
+            PH1 = CMP ? phi_row_c(P[3], PL1) : phi_row(P[3]);
             const int gL = nGa, gR = nGb;
             fetch_row(psi, r + 3, nPa, nPb);
             fetch_row(Uf, r + 2, nUa, nUb);
+            if constexpr (CMP) {
+                fetch_row(psiL, r + 2, nPLa, nPLb);
+                fetch_row(UfL, r + 2, nULa, nULb);
+            }
             if (r + 2 < ny) load_grain_pair(grain + (size_t)PF_CHK((r + 2), ny) * nx, cL, nx, vec, per, nGa, nGb);
 
-            // phase 1 at row r+1
+            // phase 1 at row r+1 (the psi pass of the two-kernel form: only
+            // rows it stores)
             V<T> phn = bc<T>(T(0));
             Row<T> DP1;
-            if (r + 1 < ny) {
-                V<T> psn, d;
-                phase1(r + 1, P[2], P[3], P[4], PH1, UU1, gL, gR, psn, phn, d);
-                if (r + 1 < y1) store_pair<T>(psi_o + (size_t)PF_CHK((r + 1), ny) * nx, cL, nx, vec, outL, outR, psn);
+            if (r + 1 < ny && (MODE != 1 || r + 1 < y1)) {
+                V<T> psn, psnl, d, rt;
+                phase1(r + 1, P[2], P[3], P[4], PH1, UU1, gL, gR, PL1, psn, psnl, phn, d, rt);
+                if (r + 1 < y1) psi_store(r + 1, psn, psnl, rt);
                 DP1 = dphi_row(d);
             } else {
                 DP1 = DP0;  // ghost row ny mirrors row ny-1 = r
+            }
+            if constexpr (MODE == 1) {
+                P[0] = P[1];
+                P[1] = P[2];
+                P[2] = P[3];
+                P[3] = P[4];
+                UU0 = UU1;
+                continue;
             }
 
             // phase 2 at row r
             const Row<T> AD1 = alphaD(PH1), AA1 = alphaA(UU1, DP1);
             {
                 V<T> sD, sA;
-                fluxes(AD0, AD1, AA0, AA1, UU0, UU1, P, true, sD, sA);
+                fluxes(AD0, AD1, AA0, AA1, UU0, UU1, UL0, UL1, P, true, sD, sA);
                 const T cs = (S == S10) ? ih2 : i6h2;
                 const V<T> u = UU0.C();
                 const V<T> num =
                     fma(bc<T>(dt * cs), fma(bc<T>(Dc), sD, sA), fma(bc<T>(omk), u, bc<T>(T(1))) * DP0.C());
-                const V<T> un = fma(num, rcp2(fma(bc<T>(-omk), phin_cur, bc<T>(T(1) + kk))), u);
-                store_pair<T>(U_o + (size_t)PF_CHK(r, ny) * nx, cL, nx, vec, outL, outR, un);
+                if constexpr (CMP) {
+                    // U' = (hi + lo) + num / (1 + k - (1-k) phi'), kept exactly
+                    const V<T> den = fma(bc<T>(-omk), phin_cur, bc<T>(T(1) + kk));
+                    const V<T> inc = mk((T)__fdiv_rn((float)num.x(), (float)den.x()),
+                                        (T)__fdiv_rn((float)num.y(), (float)den.y()));
+                    V<T> uh, ul;
+                    cadd2<T>(u, UL0.C(), inc, uh, ul);
+                    store_pair<T>(U_o + (size_t)PF_CHK(r, ny) * nx, cL, nx, vec, outL, outR, uh);
+                    store_pair<T>(U_oL + (size_t)PF_CHK(r, ny) * nx, cL, nx, vec, outL, outR, ul);
+                } else {
+                    const V<T> un = fma(num, rcp2(fma(bc<T>(-omk), phin_cur, bc<T>(T(1) + kk))), u);
+                    store_pair<T>(U_o + (size_t)PF_CHK(r, ny) * nx, cL, nx, vec, outL, outR, un);
+                }
             }
             phin_cur = phn;
             P[0] = P[1];
@@ -704,6 +858,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB, sizeof(T) == 4 ? PF_STEP2D
             P[2] = P[3];
             P[3] = P[4];
             UU0 = UU1;
+            if constexpr (CMP) UL0 = UL1;
             DP0 = DP1;
             AD0 = AD1;
             AA0 = AA1;
@@ -715,20 +870,48 @@ constexpr int WARPS_PER_BLOCK = PF_STEP2D_WPB;
 
 template <typename T, int S>
 bool launch_one(int grid_warps, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp,
-                StepClock clk, bool ds) {
+                StepClock clk, bool ds, int mode) {
     const int blocks = (grid_warps + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-    if (ds)
-        k_step2d<T, S, true><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
+    if (mode != 0 && !ds) return false;  // the two-kernel form runs on the T0 (ds) variant
+    if (mode == 1)
+        k_step2d<T, S, true, false, 1><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
+    else if (mode == 2)
+        k_step2d<T, S, true, false, 2><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
+    else if (ds)
+        k_step2d<T, S, true, false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
     else
-        k_step2d<T, S, false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
+        k_step2d<T, S, false, false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
+    return true;
+}
+// compensated state (isothermal, mirror walls, T1 only)
+template <int S>
+bool launch_cmp(int grid_warps, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp,
+                StepClock clk, bool ds) {
+    if (ds) return false;
+    const int blocks = (grid_warps + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+    k_step2d<float, S, false, true><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
     return true;
 }
 
-template <typename T, int S> int occ_one(bool ds) {
+template <typename T, int S> int occ_one(bool ds, int mode) {
+    int n = 0;
+    if (mode != 0 && !ds) return 0;
+    cudaError_t e;
+    if (mode == 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, true, false, 1>, 32 * WARPS_PER_BLOCK, 0);
+    else if (mode == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, true, false, 2>, 32 * WARPS_PER_BLOCK, 0);
+    else if (ds)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, true, false>, 32 * WARPS_PER_BLOCK, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, false, false>, 32 * WARPS_PER_BLOCK, 0);
+    return e == cudaSuccess ? n * WARPS_PER_BLOCK : 0;
+}
+template <int S> int occ_cmp(bool ds) {
+    if (ds) return 0;
     int n = 0;
     const cudaError_t e =
-        ds ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, true>, 32 * WARPS_PER_BLOCK, 0)
-           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, false>, 32 * WARPS_PER_BLOCK, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<float, S, false, true>, 32 * WARPS_PER_BLOCK, 0);
     return e == cudaSuccess ? n * WARPS_PER_BLOCK : 0;
 }
 
@@ -739,38 +922,53 @@ PF_BOUNDS_READER(bounds_step2d)
 // The 2D kernel is warp-granular: `bx` must be 64 (columns a warp holds) and
 // `grid` counts warps.
 bool launch_step2d(int prec, int scheme, int bx, int grid, cudaStream_t st, const WorkItem* work, int n_work,
-                   const InstRec* recs, int lp, StepClock clk, bool ds) {
+                   const InstRec* recs, int lp, StepClock clk, bool ds, int mode) {
     if (bx != WARP_COLS) return false;
     if (prec == 0) {
         switch (scheme) {
-            case S10: return launch_one<float, S10>(grid, st, work, n_work, recs, lp, clk, ds);
-            case S21: return launch_one<float, S21>(grid, st, work, n_work, recs, lp, clk, ds);
-            case SBAR21: return launch_one<float, SBAR21>(grid, st, work, n_work, recs, lp, clk, ds);
+            case S10: return launch_one<float, S10>(grid, st, work, n_work, recs, lp, clk, ds, mode);
+            case S21: return launch_one<float, S21>(grid, st, work, n_work, recs, lp, clk, ds, mode);
+            case SBAR21: return launch_one<float, SBAR21>(grid, st, work, n_work, recs, lp, clk, ds, mode);
+        }
+    } else if (prec == 2) {
+        if (mode != 0) return false;
+        switch (scheme) {
+            case S10: return launch_cmp<S10>(grid, st, work, n_work, recs, lp, clk, ds);
+            case S21: return launch_cmp<S21>(grid, st, work, n_work, recs, lp, clk, ds);
+            case SBAR21: return launch_cmp<SBAR21>(grid, st, work, n_work, recs, lp, clk, ds);
         }
     } else {
         switch (scheme) {
-            case S10: return launch_one<double, S10>(grid, st, work, n_work, recs, lp, clk, ds);
-            case S21: return launch_one<double, S21>(grid, st, work, n_work, recs, lp, clk, ds);
-            case SBAR21: return launch_one<double, SBAR21>(grid, st, work, n_work, recs, lp, clk, ds);
+            case S10: return launch_one<double, S10>(grid, st, work, n_work, recs, lp, clk, ds, mode);
+            case S21: return launch_one<double, S21>(grid, st, work, n_work, recs, lp, clk, ds, mode);
+            case SBAR21: return launch_one<double, SBAR21>(grid, st, work, n_work, recs, lp, clk, ds, mode);
         }
     }
     return false;
 }
 
-// Warps of the fused kernel resident on one SM (0 if not compiled).
-int occupancy_step2d(int prec, int scheme, int bx, bool ds) {
+// Warps of the fused kernel (mode 0) or of a pass of the two-kernel form
+// resident on one SM (0 if not compiled).
+int occupancy_step2d(int prec, int scheme, int bx, bool ds, int mode) {
     if (bx != WARP_COLS) return 0;
     if (prec == 0) {
         switch (scheme) {
-            case S10: return occ_one<float, S10>(ds);
-            case S21: return occ_one<float, S21>(ds);
-            case SBAR21: return occ_one<float, SBAR21>(ds);
+            case S10: return occ_one<float, S10>(ds, mode);
+            case S21: return occ_one<float, S21>(ds, mode);
+            case SBAR21: return occ_one<float, SBAR21>(ds, mode);
+        }
+    } else if (prec == 2) {
+        if (mode != 0) return 0;
+        switch (scheme) {
+            case S10: return occ_cmp<S10>(ds);
+            case S21: return occ_cmp<S21>(ds);
+            case SBAR21: return occ_cmp<SBAR21>(ds);
         }
     } else {
         switch (scheme) {
-            case S10: return occ_one<double, S10>(ds);
-            case S21: return occ_one<double, S21>(ds);
-            case SBAR21: return occ_one<double, SBAR21>(ds);
+            case S10: return occ_one<double, S10>(ds, mode);
+            case S21: return occ_one<double, S21>(ds, mode);
+            case SBAR21: return occ_one<double, SBAR21>(ds, mode);
         }
     }
     return 0;

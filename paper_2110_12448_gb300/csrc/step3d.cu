@@ -584,8 +584,10 @@ bool launch_t(int grid, cudaStream_t st, const WorkItem* work, int n_work, const
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(k_step3d<T, S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem) !=
-            cudaSuccess)
+            cudaSuccess) {
+            cudaGetLastError();  // a tile that does not fit is an answer, not an error for later calls
             return false;
+        }
         attr = true;
     }
     k_step3d<T, S, TX, TY><<<grid, TL::NT, TL::smem, st>>>(work, n_work, recs, lp, clk);
@@ -593,12 +595,18 @@ bool launch_t(int grid, cudaStream_t st, const WorkItem* work, int n_work, const
 }
 template <typename T, int S, int TX, int TY> int occ_t() {
     using TL = Tile3<T, S, TX, TY>;
+    // a tile whose shared memory exceeds the per-block limit (FP64 with the
+    // 30 x 14 tile) is not available: 0, with the runtime's error cleared
     if (cudaFuncSetAttribute(k_step3d<T, S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem) !=
-        cudaSuccess)
+        cudaSuccess) {
+        cudaGetLastError();
         return 0;
+    }
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step3d<T, S, TX, TY>, TL::NT, TL::smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step3d<T, S, TX, TY>, TL::NT, TL::smem) != cudaSuccess) {
+        cudaGetLastError();
         return 0;
+    }
     return n;
 }
 

@@ -20,7 +20,7 @@ _lock = threading.Lock()
 _lib = None
 
 SCHEMES = {"S10": 0, "S21": 1, "SBAR21": 2, "S100": 3, "SBAR120": 4}
-PRECISIONS = {"f32": 0, "f64": 1}
+PRECISIONS = {"f32": 0, "f64": 1, "f32c": 2}  # f32c: FP32 arithmetic on a compensated (hi + lo) state
 PF_OK, PF_ERR_INVALID, PF_ERR_BUDGET, PF_ERR_CUDA, PF_ERR_NONFINITE, PF_ERR_TIMEOUT, PF_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 
 
@@ -40,12 +40,13 @@ class Params(C.Structure):
                 ("scheme", C.c_int32), ("precision", C.c_int32), ("max_grains", C.c_int32),
                 ("max_seeds", C.c_int32), ("bc_x", C.c_int32), ("thermal", C.c_int32),
                 ("Vp", C.c_double), ("lT", C.c_double), ("yT", C.c_double),
-                ("time_level", C.c_int32), ("reserved", C.c_int32)]
+                ("time_level", C.c_int32), ("kernels", C.c_int32)]
 
 
 PF_BC_MIRROR, PF_BC_PERIODIC = 0, 1
 PF_ISOTHERMAL, PF_FROZEN_GRADIENT = 0, 1
 PF_T1, PF_T0 = 0, 1
+PF_FUSED, PF_TWO_KERNELS = 0, 1
 
 
 class Seed(C.Structure):
@@ -115,6 +116,7 @@ def lib():
                 "pf_group_remove": (C.c_int, [vp, vp]),
                 "pf_group_step": (C.c_int, [vp, i64, C.c_int]),
                 "pf_group_size": (C.c_int, [vp]),
+                "pf_group_observe": (C.c_int, [vp, C.c_int, vp]),
                 "pf_group_destroy": (C.c_int, [vp]),
                 "pf_observe_fields_noalloc": (C.c_int, [P(Params), vp, vp, vp, P(C.c_double), P(C.c_double), C.c_int,
                                                         vp, P(Obs)]),
@@ -154,13 +156,14 @@ def _check(rc: int, what: str):
 
 def make_params(dim, nx, ny, nz=1, h=0.8, dt=0.02, k=0.15, eps4=0.02, lam=10.0, D=None, U0=-0.55,
                 scheme="SBAR21", precision="f32", max_grains=1, max_seeds=0, bc_x=PF_BC_MIRROR,
-                thermal=PF_ISOTHERMAL, Vp=0.0, lT=1.0, yT=0.0, time_level=PF_T1) -> Params:
+                thermal=PF_ISOTHERMAL, Vp=0.0, lT=1.0, yT=0.0, time_level=PF_T1, kernels=PF_FUSED) -> Params:
     if D is None:
         D = 0.6267 * lam
     return Params(int(dim), int(nx), int(ny), int(nz if dim == 3 else 1), float(h), float(dt), float(k), float(eps4),
                   float(lam), float(D), float(U0), SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
                   PRECISIONS[precision] if isinstance(precision, str) else int(precision), int(max_grains),
-                  int(max_seeds), int(bc_x), int(thermal), float(Vp), float(lT), float(yT), int(time_level), 0)
+                  int(max_seeds), int(bc_x), int(thermal), float(Vp), float(lT), float(yT), int(time_level),
+                  int(kernels))
 
 
 def required_bytes(p: Params) -> int:
@@ -180,7 +183,7 @@ class Sim:
     def __init__(self, p: Params, stream=None, device="cuda"):
         import torch
         self.p = p
-        self.np_dtype = np.float64 if p.precision == 1 else np.float32
+        self.np_dtype = np.float32 if p.precision == 0 else np.float64  # f32c: the host sees FP64 fields
         n = required_bytes(p)
         if n == 0:
             raise PfError(PF_ERR_INVALID, "pf_required_bytes")
@@ -199,7 +202,8 @@ class Sim:
         p = make_params(w.dim, w.nx, w.ny, w.nz, w.h, w.dt, w.k, w.eps4, w.lam, w.D, w.U0, scheme or w.scheme,
                         precision, max_grains=max(1, w.n_grains), max_seeds=max(1, len(w.seeds)),
                         bc_x=getattr(w, "bc_x", 0), thermal=getattr(w, "thermal", 0), Vp=getattr(w, "Vp", 0.0),
-                        lT=getattr(w, "lT", 1.0), yT=getattr(w, "yT", 0.0), time_level=getattr(w, "time_level", 0))
+                        lT=getattr(w, "lT", 1.0), yT=getattr(w, "yT", 0.0), time_level=getattr(w, "time_level", 0),
+                        kernels=getattr(w, "kernels", 0))
         s = cls(p, stream=stream)
         s.set_grains(w.rots, w.centres)
         if init:
@@ -402,6 +406,22 @@ class Group:
 
     def step(self, n: int = 1, use_graph: bool = True):
         _check(lib().pf_group_step(self.h, int(n), 1 if use_graph else 0), "pf_group_step")
+
+    def observe(self, grain: int = -1, allow_nonfinite=False) -> list:
+        """pf_group_observe: observe() of every member, one synchronisation;
+        dicts in the order the members were added."""
+        n = len(self.members)
+        arr = (Obs * max(1, n))()
+        rc = lib().pf_group_observe(self.h, int(grain), arr)
+        if rc != PF_OK and not (allow_nonfinite and rc == PF_ERR_NONFINITE):
+            raise PfError(rc, "pf_group_observe")
+        out = []
+        for i in range(n):
+            d = {f: getattr(arr[i], f) for f, _ in Obs._fields_}
+            d["tip"] = tuple(arr[i].tip)
+            d["status"] = PF_ERR_NONFINITE if arr[i].nonfinite else PF_OK
+            out.append(d)
+        return out
 
     def __len__(self):
         return int(lib().pf_group_size(self.h))

@@ -96,3 +96,26 @@ def test_directional_parameters_accepted_and_bound():
 def test_unchecked_build_reports_no_bounds_record():
     # the default library compiles the index checks away
     assert native.debug_bounds() is None
+
+
+@pytest.mark.parametrize("kw", [dict(dim=3, nz=16, scheme="SBAR120", dt=0.015),
+                                dict(thermal=native.PF_FROZEN_GRADIENT, lT=100.0),
+                                dict(bc_x=native.PF_BC_PERIODIC), dict(time_level=native.PF_T0)])
+def test_compensated_precision_scope(kw):
+    """PF_F32C (compensated FP32 state) is 2D, isothermal, mirror walls, T1 only;
+    its fields take 8 bytes per cell and level (hi and lo halves)."""
+    assert native.required_bytes(_p(**dict(kw, precision="f32c"))) == 0
+    n = 64 * 48
+    assert native.required_bytes(_p(precision="f32c")) >= 4 * n * 8 + n * 2
+
+
+def test_two_kernel_form_scope():
+    """PF_TWO_KERNELS is the 2D T0 form with FP32 or FP64 fields; it adds one
+    field-sized buffer for d psi/dt."""
+    t0 = dict(time_level=native.PF_T0, kernels=native.PF_TWO_KERNELS)
+    n = 64 * 48
+    assert native.required_bytes(_p(**t0)) >= native.required_bytes(_p(time_level=native.PF_T0)) + 4 * n
+    assert native.required_bytes(_p(precision="f64", **t0)) > 0
+    for bad in (dict(time_level=native.PF_T1, kernels=native.PF_TWO_KERNELS), dict(t0, precision="f32c"),
+                dict(t0, dim=3, nz=16, scheme="SBAR120", dt=0.015), dict(kernels=2)):
+        assert native.required_bytes(_p(**bad)) == 0, bad

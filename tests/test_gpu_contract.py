@@ -16,6 +16,9 @@ step (exact arithmetic otherwise) ends 2e-4 / 3e-4 away: any build that stores
 FP32 fields misses 1e-4 on this workload.
   * FP64: 1e-9 (rounding of 1e-16 per step, amplified).
   * FP32 fields (fast exp2/reciprocal): 5e-3 on phi and U (measured ~2e-3).
+  * FP32 arithmetic on the compensated state (PF_F32C): the contract's 1e-4.
+    Its per-step errors are the FP32 rounding of the rates and of phi, a few
+    times below the FP32 rounding of a stored state.
 """
 import json
 import math
@@ -110,3 +113,9 @@ def test_fp32_10k_steps(native, oracle_run):
     dphi, du, verr = compare(native, oracle_run, "f32")
     assert verr < 5e-3  # the contract's tip-velocity bound, 0.5 %
     assert dphi < 5e-3 and du < 5e-3
+
+
+def test_f32c_10k_steps(native, oracle_run):
+    dphi, du, verr = compare(native, oracle_run, "f32c")
+    assert verr < 5e-3
+    assert dphi <= 1e-4 and du <= 1e-4
