@@ -126,7 +126,7 @@ class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, index, window="the timed region"):
         self.index = index
@@ -141,7 +141,7 @@ class Clocks:
             r = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                 "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
             row = r.stdout.strip().splitlines()[0]
-            return row if row.count(",") >= 8 else None
+            return row if row.count(",") >= 9 else None
         except Exception:
             return None
 
@@ -178,7 +178,9 @@ class Clocks:
             mx = max(float(r[2]) for r in rows)
             names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
             reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+            util = [float(r[9]) for r in rows if len(r) > 9 and r[9].strip().replace(".", "", 1).isdigit()]
             return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
+                    "gpu_util_pct_median": statistics.median(util) if util else None,
                     "samples": len(sampled), "edge_samples": len(self.edges),
                     "edge_sm_mhz": [float(r.split(",")[1]) for r in self.edges],
                     "window": f"200 ms sampler over {self.window}, plus one sample right before and one right "
@@ -641,7 +643,10 @@ def run_serve(args):
                                        f"128..2048 and 3D 64..192 scaled by {args.serve_scale}, 1-16 seeds, U0 in "
                                        f"[-0.7,-0.4], 1000..20000 steps scaled by {args.serve_scale}, 80% HBM budget"},
                 "latency_s": {"p50": summ["p50_s"], "p99": summ["p99_s"], "of": "time to result"},
-                "requests": summ["requests"], "wall_s": summ["wall_s"], "clocks": clocks.summary()}
+                "requests": summ["requests"], "wall_s": summ["wall_s"], "clocks": clocks.summary(),
+                "cell_updates": {"2d": summ["cell_updates_2d"], "3d": summ["cell_updates_3d"]},
+                "max_running": summ["max_running"], "peak_bytes": summ["peak_bytes"],
+                "budget_bytes": summ["budget_bytes"]}
         print(json.dumps(line), flush=True)
     return 0
 

@@ -41,8 +41,11 @@ __device__ __forceinline__ void combine(ObsPartial& a, const ObsPartial& b) {
     }
 }
 
+// The partial of block `blk` of `nblk` walking the cells of one field pair;
+// sh: OBS_THREADS records of shared memory.
 template <typename T>
-__global__ void __launch_bounds__(OBS_THREADS) k_observe(ObsArgs a, ObsPartial* __restrict__ partials) {
+__device__ void observe_block(const ObsArgs& a, ObsPartial* __restrict__ partials, long long blk, long long nblk,
+                              ObsPartial* sh) {
     const T* __restrict__ psi = static_cast<const T*>(a.psi);
     const T* __restrict__ U = static_cast<const T*>(a.U);
     const long long nx = a.nx, ny = a.ny, nz = a.dim == 3 ? a.nz : 1;
@@ -56,59 +59,98 @@ __global__ void __launch_bounds__(OBS_THREADS) k_observe(ObsArgs a, ObsPartial* 
     acc.tip[0] = acc.tip[1] = acc.tip[2] = 0.0;
     acc.pad = 0.0;
     const double k = a.k, omk = 1.0 - a.k;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const T pst = psi[c];
-        const double ps = (double)pst, u = (double)U[c];
-        if (!isfinite(ps) || !isfinite(u)) {
-            acc.nonfinite += 1;
-            continue;
-        }
-        // Away from the interface |psi| / sqrt2 >= 22.6 and tanh is +-1 to FP64
-        // precision (both here and in C libraries that return +-1 from |x| = 22
-        // on); the test runs in the field precision and skips the FP64
-        // division and tanh for the bulk of the grid.
-        const double ph = fabs(pst) >= T(32) ? (pst > T(0) ? 1.0 : -1.0) : tanh(ps / SQ2);
-        acc.solute += (1.0 + k - omk * ph) * (1.0 + omk * u) / 2.0;
-        acc.solid += (1.0 + ph) / 2.0;
-        if (a.grain_filter >= 0 && a.grain[c] != a.grain_filter) continue;
-        if (!(ps >= 0.0)) continue;
-        const long long i = c % nx, j = (c / nx) % ny, kk = c / (nx * ny);
-        long long ii = i, jj = j, kq = kk;
-        if (a.ea == 0) ii += a.es;
-        else if (a.ea == 1) jj += a.es;
-        else kq += a.es;
-        if (ii < 0 || jj < 0 || kq < 0 || ii >= nx || jj >= ny || kq >= nz) continue;
-        const double pn = (double)psi[PF_CHK((kq * ny + jj) * nx + ii, N)];
-        if (!(pn < 0.0)) continue;
-        const double frac = __ddiv_rn(ps, __dsub_rn(ps, pn));
-        double p[3] = {__dmul_rn((double)i, a.h), __dmul_rn((double)j, a.h),
-                       a.dim == 3 ? __dmul_rn((double)kk, a.h) : 0.0};
-        p[a.ea] = __dadd_rn(p[a.ea], __dmul_rn((double)a.es * frac, a.h));
-        double sc = 0.0;
-        for (int q = 0; q < a.dim; ++q) sc = __dadd_rn(sc, __dmul_rn(__dsub_rn(p[q], a.cg[q]), a.d[q]));
-        if (better(sc, c, acc.score, acc.tip_index)) {
-            acc.score = sc;
-            acc.tip_index = c;
-            acc.tip[0] = p[0];
-            acc.tip[1] = p[1];
-            acc.tip[2] = p[2];
+    // Away from the interface |psi| / sqrt2 >= 22.6 and tanh is +-1 to FP64
+    // precision (both here and in C libraries that return +-1 from |x| = 22
+    // on).  Those bulk cells contribute 1 + (1-k) U (liquid) or k (1 + (1-k) U)
+    // (solid) to the solute sum and 0 or 1 to the solid sum: they are counted
+    // and their U summed in FP64, and the terms formed once per thread.  Rows
+    // are walked whole (one block per row, threads along x), so no cell index
+    // is divided.
+    long long n_liq = 0, n_sol = 0;
+    double u_liq = 0.0, u_sol = 0.0;
+    const long long rows = ny * nz;
+    for (long long row = blk; row < rows; row += nblk) {
+        const long long j = row % ny, kk = row / ny;
+        const long long base = row * nx;
+        for (long long i = threadIdx.x; i < nx; i += blockDim.x) {
+            const long long c = base + i;
+            const T pst = psi[c];
+            const T ut = U[c];
+            const double ps = (double)pst, u = (double)ut;
+            if (!isfinite(ps) || !isfinite(u)) {
+                acc.nonfinite += 1;
+                continue;
+            }
+            if (fabs(pst) >= T(32)) {
+                if (pst > T(0)) {
+                    n_sol += 1;
+                    u_sol += u;
+                } else {
+                    n_liq += 1;
+                    u_liq += u;
+                    continue;  // liquid: no tip candidate
+                }
+            } else {
+                const double ph = tanh(ps / SQ2);
+                acc.solute += (1.0 + k - omk * ph) * (1.0 + omk * u) / 2.0;
+                acc.solid += (1.0 + ph) / 2.0;
+            }
+            if (a.grain_filter >= 0 && a.grain[c] != a.grain_filter) continue;
+            if (!(ps >= 0.0)) continue;
+            long long ii = i, jj = j, kq = kk;
+            if (a.ea == 0) ii += a.es;
+            else if (a.ea == 1) jj += a.es;
+            else kq += a.es;
+            if (ii < 0 || jj < 0 || kq < 0 || ii >= nx || jj >= ny || kq >= nz) continue;
+            const double pn = (double)psi[PF_CHK((kq * ny + jj) * nx + ii, N)];
+            if (!(pn < 0.0)) continue;
+            const double frac = __ddiv_rn(ps, __dsub_rn(ps, pn));
+            double p[3] = {__dmul_rn((double)i, a.h), __dmul_rn((double)j, a.h),
+                           a.dim == 3 ? __dmul_rn((double)kk, a.h) : 0.0};
+            p[a.ea] = __dadd_rn(p[a.ea], __dmul_rn((double)a.es * frac, a.h));
+            double sc = 0.0;
+            for (int q = 0; q < a.dim; ++q) sc = __dadd_rn(sc, __dmul_rn(__dsub_rn(p[q], a.cg[q]), a.d[q]));
+            if (better(sc, c, acc.score, acc.tip_index)) {
+                acc.score = sc;
+                acc.tip_index = c;
+                acc.tip[0] = p[0];
+                acc.tip[1] = p[1];
+                acc.tip[2] = p[2];
+            }
         }
     }
-    __shared__ ObsPartial sh[OBS_THREADS];
+    acc.solute += ((double)n_liq + omk * u_liq) + k * ((double)n_sol + omk * u_sol);
+    acc.solid += (double)n_sol;
     sh[threadIdx.x] = acc;
     __syncthreads();
     for (int s = OBS_THREADS / 2; s > 0; s >>= 1) {
         if ((int)threadIdx.x < s) combine(sh[threadIdx.x], sh[threadIdx.x + s]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+    if (threadIdx.x == 0) partials[blk] = sh[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(OBS_THREADS) k_observe(ObsArgs a, ObsPartial* __restrict__ partials) {
+    __shared__ ObsPartial sh[OBS_THREADS];
+    observe_block<T>(a, partials, blockIdx.x, gridDim.x, sh);
+}
+
+// All members of a group in one launch: blocks (x, m) walk member m's cells
+// exactly as blocks x of k_observe would (same partials, same order).
+__global__ void __launch_bounds__(OBS_THREADS) k_observe_multi(const ObsJob* __restrict__ jobs) {
+    __shared__ ObsPartial sh[OBS_THREADS];
+    const ObsJob& j = jobs[blockIdx.y];
+    if (j.a.prec == 0)
+        observe_block<float>(j.a, j.partials, blockIdx.x, gridDim.x, sh);
+    else
+        observe_block<double>(j.a, j.partials, blockIdx.x, gridDim.x, sh);
 }
 
 // Combine the block partials: thread t folds partials t, t + 256, ... in
 // index order, then a fixed tree; deterministic for a fixed partial count.
-__global__ void __launch_bounds__(OBS_THREADS) k_observe_finish(const ObsPartial* __restrict__ partials, int n,
-                                                                ObsPartial* __restrict__ out) {
-    __shared__ ObsPartial sh[OBS_THREADS];
+__device__ void finish_block(const ObsPartial* __restrict__ partials, int n, ObsPartial* __restrict__ out,
+                             ObsPartial* sh) {
     ObsPartial acc;
     acc.solute = 0.0;
     acc.solid = 0.0;
@@ -125,6 +167,19 @@ __global__ void __launch_bounds__(OBS_THREADS) k_observe_finish(const ObsPartial
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = sh[0];
+}
+
+__global__ void __launch_bounds__(OBS_THREADS) k_observe_finish(const ObsPartial* __restrict__ partials, int n,
+                                                                ObsPartial* __restrict__ out) {
+    __shared__ ObsPartial sh[OBS_THREADS];
+    finish_block(partials, n, out, sh);
+}
+
+// Block m combines member m's partials into out[m].
+__global__ void __launch_bounds__(OBS_THREADS) k_observe_finish_multi(const ObsJob* __restrict__ jobs,
+                                                                      ObsPartial* __restrict__ out) {
+    __shared__ ObsPartial sh[OBS_THREADS];
+    finish_block(jobs[blockIdx.x].partials, OBS_BLOCKS, out + blockIdx.x, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -403,6 +458,13 @@ cudaError_t noalloc_scratch(ObsPartial** partials, ObsPartial** result) {
     *partials = static_cast<ObsPartial*>(p);
     *result = *partials + OBS_BLOCKS;
     return cudaSuccess;
+}
+
+cudaError_t launch_observe_multi(const ObsJob* jobs, int n, ObsPartial* results, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_observe_multi<<<dim3(OBS_BLOCKS, n), OBS_THREADS, 0, st>>>(jobs);
+    k_observe_finish_multi<<<n, OBS_THREADS, 0, st>>>(jobs, results);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* result, cudaStream_t st) {

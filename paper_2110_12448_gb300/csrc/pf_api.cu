@@ -970,6 +970,7 @@ struct pf_group {
     long long* clock;
     long long* step_base;
     ObsPartial* obs;  // one reduced observe record per member slot
+    ObsJob* jobs;     // observe arguments of every member (pf_group_observe)
     bool thermal_any;
     cudaGraphExec_t graph;
     int graph_len;
@@ -1066,7 +1067,7 @@ size_t pf_group_required_bytes(int max_instances, int max_work) {
     if (max_instances < 1 || max_work < 1) return 0;
     return align256((size_t)max_instances * sizeof(InstRec)) + align256((size_t)max_work * sizeof(WorkItem)) +
            align256((size_t)(max_instances + 1) * sizeof(long long)) +
-           align256((size_t)max_instances * sizeof(ObsPartial));
+           align256((size_t)max_instances * sizeof(ObsPartial)) + align256((size_t)max_instances * sizeof(ObsJob));
 }
 
 int pf_group_work_items(const pf_sim* s) {
@@ -1094,6 +1095,8 @@ int pf_group_create(int max_instances, int max_work, void* dev_mem, size_t bytes
     g->step_base = g->clock + 1;
     g->obs = reinterpret_cast<ObsPartial*>(reinterpret_cast<char*>(g->clock) +
                                            align256((size_t)(max_instances + 1) * sizeof(long long)));
+    g->jobs = reinterpret_cast<ObsJob*>(reinterpret_cast<char*>(g->obs) +
+                                        align256((size_t)max_instances * sizeof(ObsPartial)));
     g->thermal_any = false;
     g->launches = 0;
     g->dirty = true;
@@ -1188,19 +1191,23 @@ int pf_group_observe(pf_group* g, int grain, pf_obs* out) {
         if (grain >= s->n_grains) return PF_ERR_INVALID;
     const size_t n = g->members.size();
     if (n == 0) return PF_OK;
-    std::vector<ObsArgs> args(n);
+    std::vector<ObsJob> jobs(n);
     for (size_t i = 0; i < n; ++i) {
         pf_sim* s = g->members[i];
-        // the member's fields are current on the group's stream; its partials
-        // are its own, the reduced record goes to the group's slot i
+        // the member's fields are current on the group's stream (compensated
+        // members are joined there); its partials are its own, the reduced
+        // record goes to the group's slot i
         const cudaStream_t keep = s->st;
         s->st = g->st;
-        int rc = observe_args(s, grain, args[i]);
-        cudaError_t e = rc == PF_OK ? launch_observe(args[i], s->partials, g->obs + i, g->st) : cudaSuccess;
+        const int rc = observe_args(s, grain, jobs[i].a);
         s->st = keep;
         if (rc != PF_OK) return rc;
-        if (e != cudaSuccess) return cuda_fail(e, "launch_observe");
+        jobs[i].partials = s->partials;
     }
+    CK(cudaMemcpyAsync(g->jobs, jobs.data(), n * sizeof(ObsJob), cudaMemcpyHostToDevice, g->st));
+    CK(launch_observe_multi(g->jobs, (int)n, g->obs, g->st));
+    std::vector<ObsArgs> args(n);
+    for (size_t i = 0; i < n; ++i) args[i] = jobs[i].a;
     std::vector<ObsPartial> r(n);
     CK(cudaMemcpyAsync(r.data(), g->obs, n * sizeof(ObsPartial), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));

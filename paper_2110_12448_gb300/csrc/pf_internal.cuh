@@ -155,6 +155,13 @@ struct ObsArgs {
 constexpr int OBS_BLOCKS = 304;  // 2 x 152 SMs
 constexpr int OBS_THREADS = 256;
 cudaError_t launch_observe(const ObsArgs& a, ObsPartial* partials, ObsPartial* result, cudaStream_t st);
+// one observe job of a group: the arguments and the member's OBS_BLOCKS partials
+struct ObsJob {
+    ObsArgs a;
+    ObsPartial* partials;
+};
+// the jobs (in device memory) of n members in one launch; results[m] for job m
+cudaError_t launch_observe_multi(const ObsJob* jobs, int n, ObsPartial* results, cudaStream_t st);
 // Device address of the library's fixed observe scratch on the current device.
 cudaError_t noalloc_scratch(ObsPartial** partials, ObsPartial** result);
 

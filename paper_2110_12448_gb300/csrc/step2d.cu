@@ -188,6 +188,57 @@ template <typename T> __device__ __forceinline__ V<T> aniso_a2(V<T> gx, V<T> gy,
     const V<T> a = fma(bc<T>(T(4) * eps), fma(sx, sx, sy * sy), bc<T>(T(1) - T(3) * eps));
     return mk(r2.x() * hh < Guard<T>::v ? T(1) : a.x(), r2.y() * hh < Guard<T>::v ? T(1) : a.y());
 }
+// The same normal component of J - g without the cancellation in a^2 - 1
+// (the compensated state): with s_x + s_y = 1 in 2D, a - 1 = eps (4q - 3) =
+// eps (1 - 8 s_x s_y), a^2 - 1 = (a - 1)(a + 1), and s_x - q = s_y (s_x - s_y),
+// s_y - q = -s_x (s_x - s_y), so
+//   J'_x - c_x = c_x eps [b (2 + eps b) + 16 a s_y (s_x - s_y)],
+//   J'_y - c_y = c_y eps [b (2 + eps b) - 16 a s_x (s_x - s_y)],  b = 1 - 8 s_x s_y,
+// every term formed without subtracting nearly equal numbers.
+template <typename T>
+__device__ __forceinline__ V<T> aniso_qn2c(V<T> gx, V<T> gy, const Rot2<T>& R, T eps, T hh, bool xface) {
+    const V<T> cx = fma(R.a, gx, R.c * gy);
+    const V<T> cy = fma(R.b, gx, R.d * gy);
+    const V<T> r2 = fma(cx, cx, cy * cy);
+    const V<T> inv = rcp2(r2);
+    const V<T> sx = cx * cx * inv, sy = cy * cy * inv;
+    const V<T> dxy = (cx - cy) * (cx + cy) * inv;  // s_x - s_y
+    const V<T> b = fma(bc<T>(T(-8)) * sx, sy, bc<T>(T(1)));
+    const V<T> a = fma(bc<T>(eps), b, bc<T>(T(1)));
+    const V<T> B = b * fma(bc<T>(eps), b, bc<T>(T(2)));
+    const V<T> t = bc<T>(T(16)) * a * dxy;
+    const V<T> jx = cx * bc<T>(eps) * fma(t, sy, B), jy = cy * bc<T>(eps) * fma(t * bc<T>(T(-1)), sx, B);
+    const V<T> o = xface ? fma(R.a, jx, R.b * jy) : fma(R.c, jx, R.d * jy);
+    return mk(r2.x() * hh < Guard<T>::v ? T(0) : o.x(), r2.y() * hh < Guard<T>::v ? T(0) : o.y());
+}
+template <typename T>
+__device__ __forceinline__ T aniso_qn1c(T gx, T gy, T Ra, T Rb, T Rc, T Rd, T eps, T hh, bool xface) {
+    const T cx = Ra * gx + Rc * gy;
+    const T cy = Rb * gx + Rd * gy;
+    const T r2 = cx * cx + cy * cy;
+    if (r2 * hh < Guard<T>::v) return T(0);
+    const T inv = M<T>::rcp(r2);
+    const T sx = cx * cx * inv, sy = cy * cy * inv;
+    const T dxy = (cx - cy) * (cx + cy) * inv;
+    const T b = T(1) - T(8) * sx * sy;
+    const T a = T(1) + eps * b;
+    const T B = b * (T(2) + eps * b);
+    const T t = T(16) * a * dxy;
+    const T jx = cx * eps * (B + t * sy), jy = cy * eps * (B - t * sx);
+    return xface ? (Ra * jx + Rb * jy) : (Rc * jx + Rd * jy);
+}
+// the anisotropic part 4 eps q of a_s = (1 - 3 eps) + 4 eps q (3 eps where
+// the normal is undefined, so that a_s = 1): the compensated state forms
+// a_s in double-float from it
+template <typename T> __device__ __forceinline__ V<T> aniso_w2(V<T> gx, V<T> gy, const Rot2<T>& R, T eps, T hh) {
+    const V<T> cx = fma(R.a, gx, R.c * gy);
+    const V<T> cy = fma(R.b, gx, R.d * gy);
+    const V<T> r2 = fma(cx, cx, cy * cy);
+    const V<T> inv = rcp2(r2);
+    const V<T> sx = cx * cx * inv, sy = cy * cy * inv;
+    const V<T> w = bc<T>(T(4) * eps) * fma(sx, sx, sy * sy);
+    return mk(r2.x() * hh < Guard<T>::v ? T(3) * eps : w.x(), r2.y() * hh < Guard<T>::v ? T(3) * eps : w.y());
+}
 // scalar version for the rare faces between two grains
 template <typename T>
 __device__ __forceinline__ T aniso_qn1(T gx, T gy, T Ra, T Rb, T Rc, T Rd, T eps, T hh, bool xface) {
@@ -278,6 +329,85 @@ __device__ __forceinline__ float phi_acc(float hi, float lo) {
 __device__ __forceinline__ float dphi_acc(float phi, float d) {
     const float T = tanhf(d * 0.70710678118654752440f);
     return __fdiv_rn(T * fmaf(-phi, phi, 1.0f), fmaf(T, phi, 1.0f));
+}
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic on packed FP32 pairs (Dekker's double-length
+// arithmetic, 1971: values h + l with |l| <= ulp(h) / 2; error-free two-sum
+// and the FMA two-product).  The compensated state evaluates the psi rate this
+// way: its terms are O(1) while the rate must be accurate to ~1e-8 absolute
+// (a per-step perturbation of psi at the interface is amplified ~1e4-fold
+// over 1e4 steps of the free dendrite), beyond FP32's 2^-24.
+// ---------------------------------------------------------------------------
+struct D2 {
+    V<float> h, l;
+};
+__device__ __forceinline__ D2 d2(V<float> h, V<float> l) { return D2{h, l}; }
+__device__ __forceinline__ D2 d2f(V<float> h) { return D2{h, bc<float>(0.0f)}; }
+__device__ __forceinline__ D2 d2c(float h, float l) { return D2{bc<float>(h), bc<float>(l)}; }
+__device__ __forceinline__ V<float> vneg(V<float> a) { return a * bc<float>(-1.0f); }
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ D2 two_sum(V<float> a, V<float> b) {
+    const V<float> s = a + b;
+    const V<float> bb = s - a;
+    return D2{s, (a - (s - bb)) + (b - bb)};
+}
+// s + e = a + b exactly when |a| >= |b| (Dekker)
+__device__ __forceinline__ D2 fast_two_sum(V<float> a, V<float> b) {
+    const V<float> s = a + b;
+    return D2{s, b - (s - a)};
+}
+// p + e = a b exactly
+__device__ __forceinline__ D2 two_prod(V<float> a, V<float> b) {
+    const V<float> p = a * b;
+    return D2{p, fma(a, b, vneg(p))};
+}
+__device__ __forceinline__ D2 dadd(D2 x, D2 y) {
+    const D2 s = two_sum(x.h, y.h);
+    return fast_two_sum(s.h, s.l + (x.l + y.l));
+}
+__device__ __forceinline__ D2 dsub(D2 x, D2 y) { return dadd(x, D2{vneg(y.h), vneg(y.l)}); }
+__device__ __forceinline__ D2 dmul(D2 x, D2 y) {
+    const D2 p = two_prod(x.h, y.h);
+    return fast_two_sum(p.h, fma(x.h, y.l, fma(x.l, y.h, p.l)));
+}
+__device__ __forceinline__ D2 dscale(D2 x, float c) { return D2{x.h * bc<float>(c), x.l * bc<float>(c)}; }  // c a power of 2
+__device__ __forceinline__ D2 ddiv(D2 x, D2 y) {
+    const V<float> q1 = mk(__fdiv_rn(x.h.x(), y.h.x()), __fdiv_rn(x.h.y(), y.h.y()));
+    const D2 r = dsub(x, dmul(d2f(q1), y));
+    const V<float> q2 = mk(__fdiv_rn(r.h.x(), y.h.x()), __fdiv_rn(r.h.y(), y.h.y()));
+    return fast_two_sum(q1, q2);
+}
+// (hi_a + lo_a) - (hi_b + lo_b) with the hi difference exact
+__device__ __forceinline__ D2 ddiff(V<float> ha, V<float> la, V<float> hb, V<float> lb) {
+    const D2 s = two_sum(ha, vneg(hb));
+    return D2{s.h, s.l + (la - lb)};
+}
+// e^x for x <= 0 (|x| < 80) in double-float, relative error ~1e-11: Cody-Waite
+// reduction x = k ln2 + r, |r| <= ln2 / 2 (ln2 = L1 + L2 + L3, k L1 exact),
+// e^r by its Taylor series (r, r^2/2, r^3/6 in double-float, r^4/24 ..
+// r^9/9! in FP32, each below 1e-3 of the sum), then the exact scaling 2^k.
+__device__ __forceinline__ D2 dexp_neg(D2 x) {
+    const float L1 = 0.693115234375f, L2 = 3.194618329871446e-05f, L3 = 1.6465717678215697e-12f;
+    const float kx = rintf(x.h.x() * 1.4426950216293335f), ky = rintf(x.h.y() * 1.4426950216293335f);
+    const V<float> k = mk(kx, ky);
+    const D2 r0 = two_sum(fma(vneg(k), bc<float>(L1), x.h), vneg(k * bc<float>(L2)));
+    const D2 r = fast_two_sum(r0.h, r0.l + (x.l - k * bc<float>(L3)));
+    const D2 r2 = dmul(r, r);
+    const D2 r3 = dmul(r2, r);
+    const V<float> rh = r.h;
+    V<float> t = fma(rh, bc<float>(1.0f / 362880.0f), bc<float>(1.0f / 40320.0f));
+    t = fma(rh, t, bc<float>(1.0f / 5040.0f));
+    t = fma(rh, t, bc<float>(1.0f / 720.0f));
+    t = fma(rh, t, bc<float>(1.0f / 120.0f));
+    t = fma(rh, t, bc<float>(1.0f / 24.0f));
+    t = t * (r2.h * r2.h);
+    D2 e = dadd(dmul(r3, d2c(0.1666666716337204f, -4.967053879312289e-09f)), d2f(t));
+    e = dadd(e, dscale(r2, 0.5f));
+    e = dadd(e, r);
+    e = dadd(e, d2c(1.0f, 0.0f));
+    const V<float> p2 = mk(__int_as_float(((int)kx + 127) << 23), __int_as_float(((int)ky + 127) << 23));
+    return D2{e.h * p2, e.l * p2};
 }
 
 template <typename T> struct ConstOf;
@@ -507,9 +637,25 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
 
         // phase 1 at real row p (psi rows Pm = p-1, P0 = p, Pp = p+1), grains
         // gL, gR: returns psi' and phi' of the own columns and delta phi.
+        // double-float constants of the compensated state's psi rate
+        auto dfc = [&](double x) -> D2 {
+            const float h = (float)x;
+            return d2c(h, (float)(x - (double)h));
+        };
+        D2 kL = d2c(0.f, 0.f), kG1 = kL, kG2 = kL, kS2 = kL, kDT = kL, kA0 = kL;
+        if constexpr (CMP) {
+            const double hd = rec.h;
+            kL = dfc(ISO ? 1.0 / (6.0 * hd * hd) : 1.0 / (hd * hd));
+            kG1 = dfc(ISO ? 2.0 / 3.0 / (4.0 * hd * hd) : 0.25 / (hd * hd));
+            kG2 = dfc(ISO ? 1.0 / 3.0 / (8.0 * hd * hd) : 0.0);
+            kS2 = dfc(1.41421356237309504880);
+            kDT = dfc(rec.dt);
+            kA0 = dfc(1.0 - 3.0 * rec.eps4);
+        }
+
         auto phase1 = [&](int p, const Row<T>& Pm, const Row<T>& P0, const Row<T>& Pp, const Row<T>& ph0,
-                          const Row<T>& u0, int gL, int gR, V<T> lo0, V<T>& psin, V<T>& psin_lo, V<T>& phin,
-                          V<T>& dph, V<T>& rate_o) {
+                          const Row<T>& u0, int gL, int gR, const Row<T>& Lm, const Row<T>& L0, const Row<T>& Lp,
+                          V<T> ulo0, V<T>& psin, V<T>& psin_lo, V<T>& phin, V<T>& dph, V<T>& rate_o) {
             if constexpr (MODE == 2) {
                 // U pass of the two-kernel form: d psi/dt^n from the psi pass,
                 // T0 increment dt (1 - phi^2)/sqrt2 d psi/dt, phi^n on the left
@@ -528,24 +674,30 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             const V<T> Wm = Pm.W(), Cm = Pm.C(), Em = Pm.E();
             const V<T> Wp = Pp.W(), Cp = Pp.C(), Ep = Pp.E();
             // x+ faces: (L|R) in L's frame, (R|R+1) in R's frame
+            // face fluxes of J - g (the compensated state: the cancellation-free form)
+            auto aq2 = [&](V<T> gx, V<T> gy, bool xf) -> V<T> {
+                if constexpr (CMP) return aniso_qn2c<T>(gx, gy, RR, eps, hh, xf);
+                return aniso_qn2<T>(gx, gy, RR, eps, hh, xf);
+            };
+            auto aq1 = [&](T gx, T gy, T Ra, T Rb, T Rc, T Rd) -> T {
+                if constexpr (CMP) return aniso_qn1c<T>(gx, gy, Ra, Rb, Rc, Rd, eps, hh, true);
+                return aniso_qn1<T>(gx, gy, Ra, Rb, Rc, Rd, eps, hh, true);
+            };
             const V<T> gxX = (E0 - C0) * bc<T>(ih), gyX = ((Ep + Cp) - (Em + Cm)) * bc<T>(i4h);
-            const V<T> Xp = aniso_qn2<T>(gxX, gyX, RR, eps, hh, true);
+            const V<T> Xp = aq2(gxX, gyX, true);
             // x- faces: from the left column; recomputed across grain boundaries.
             // Lane 0 receives its own value: its column L (x0-2) feeds no output.
             T xmL = shup(Xp.y()), xmR = Xp.x();
             if (gM != gL)
-                xmL = aniso_qn1<T>((P0.l - P0.m1) * ih, ((Pp.l + Pp.m1) - (Pm.l + Pm.m1)) * i4h, RR.a.x(), RR.b.x(),
-                                   RR.c.x(), RR.d.x(), eps, hh, true);
-            if (gR != gL)
-                xmR = aniso_qn1<T>(gxX.x(), gyX.x(), RR.a.y(), RR.b.y(), RR.c.y(), RR.d.y(), eps, hh, true);
+                xmL = aq1((P0.l - P0.m1) * ih, ((Pp.l + Pp.m1) - (Pm.l + Pm.m1)) * i4h, RR.a.x(), RR.b.x(), RR.c.x(),
+                          RR.d.x());
+            if (gR != gL) xmR = aq1(gxX.x(), gyX.x(), RR.a.y(), RR.b.y(), RR.c.y(), RR.d.y());
             // y+ faces; y- faces carried from row p-1 when valid
-            const V<T> Yp =
-                aniso_qn2<T>(((Ep + E0) - (Wp + W0)) * bc<T>(i4h), (Cp - C0) * bc<T>(ih), RR, eps, hh, false);
+            const V<T> Yp = aq2(((Ep + E0) - (Wp + W0)) * bc<T>(i4h), (Cp - C0) * bc<T>(ih), false);
             V<T> Ym = qy_c;
             const bool okL = prow_c == p && gyL_c == gL, okR = prow_c == p && gyR_c == gR;
             if (!(okL && okR)) {
-                const V<T> Yc =
-                    aniso_qn2<T>(((E0 + Em) - (W0 + Wm)) * bc<T>(i4h), (C0 - Cm) * bc<T>(ih), RR, eps, hh, false);
+                const V<T> Yc = aq2(((E0 + Em) - (W0 + Wm)) * bc<T>(i4h), (C0 - Cm) * bc<T>(ih), false);
                 Ym = mk(okL ? Ym.x() : Yc.x(), okR ? Ym.y() : Yc.y());
             }
             qy_c = Yp;
@@ -575,14 +727,55 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                 iF1 = M<T>::rcp(T(1) - omk * z);
             }
             if constexpr (CMP) {
-                // 1 - phi^2 rounded once; psi' = (hi + lo) + dt rate kept exactly;
-                // delta phi from the addition theorem, phi' = phi + delta phi
-                const V<T> src = bc<T>(SQ2) * (ph - bc<T>(lam) * fma(ph * bc<T>(T(-1)), ph, bc<T>(T(1))) * u);
-                const V<T> rate = (L + N + src) * rcp2(ac * ac) - bc<T>(SQ2) * ph * G;
-                const V<T> d = bc<T>(dt) * rate;
-                cadd2<T>(C0, lo0, d, psin, psin_lo);
-                dph = mk((T)dphi_acc((float)ph.x(), (float)d.x()), (T)dphi_acc((float)ph.y(), (float)d.y()));
-                phin = ph + dph;
+                // The rate in double-float: psi differences to the centre exact
+                // (hi differences by two-sum plus the lo differences); L and G
+                // from them; phi and 1 - phi^2 from e = exp(-sqrt2 |psi|) as
+                // sign (1 - e) / (1 + e) and 4 e / (1 + e)^2; a_s = (1 - 3 eps)
+                // + 4 eps q with the FP32 anisotropic part; U with its lo
+                // half; the O(eps4) face terms N in FP32.  psi' = (hi + lo) +
+                // dt rate kept exactly; delta phi from the addition theorem.
+                const V<T> cl = L0.C();
+                auto dd = [&](V<T> hn, V<T> ln) { return ddiff(hn, ln, C0, cl); };
+                const D2 dW = dd(W0, L0.W()), dE = dd(E0, L0.E()), dS = dd(Cm, Lm.C()), dN = dd(Cp, Lp.C());
+                const D2 faces = dadd(dadd(dW, dE), dadd(dS, dN));
+                const D2 gx = dsub(dE, dW), gy = dsub(dN, dS);
+                D2 Ld, Gd;
+                if (ISO) {
+                    const D2 dWm = dd(Wm, Lm.W()), dEm = dd(Em, Lm.E()), dWp = dd(Wp, Lp.W()), dEp = dd(Ep, Lp.E());
+                    Ld = dmul(dadd(dscale(faces, 4.0f), dadd(dadd(dWm, dEm), dadd(dWp, dEp))), kL);
+                    const D2 gp = dsub(dEp, dWm), gm = dsub(dEm, dWp);
+                    Gd = dadd(dmul(dadd(dmul(gx, gx), dmul(gy, gy)), kG1), dmul(dadd(dmul(gp, gp), dmul(gm, gm)), kG2));
+                } else {
+                    Ld = dmul(faces, kL);
+                    Gd = dmul(dadd(dmul(gx, gx), dmul(gy, gy)), kG1);
+                }
+                // |psi| (clamped at 40: e < 1e-24 there) and its sign
+                const bool nL = C0.x() < T(0), nR = C0.y() < T(0);
+                const bool cLx = fabsf(C0.x()) > 40.0f, cRx = fabsf(C0.y()) > 40.0f;
+                const D2 ap = d2(mk(cLx ? 40.0f : fabsf(C0.x()), cRx ? 40.0f : fabsf(C0.y())),
+                                 mk(cLx ? 0.0f : (nL ? -cl.x() : cl.x()), cRx ? 0.0f : (nR ? -cl.y() : cl.y())));
+                const D2 e = dexp_neg(dmul(ap, D2{vneg(kS2.h), vneg(kS2.l)}));
+                const D2 one = d2c(1.0f, 0.0f);
+                const D2 ep1 = dadd(one, e);
+                const D2 pa = ddiv(dsub(one, e), ep1);
+                const D2 phd = d2(mk(nL ? -pa.h.x() : pa.h.x(), nR ? -pa.h.y() : pa.h.y()),
+                                  mk(nL ? -pa.l.x() : pa.l.x(), nR ? -pa.l.y() : pa.l.y()));
+                const D2 omp = ddiv(dscale(e, 4.0f), dmul(ep1, ep1));  // 1 - phi^2
+                const D2 cpl = dmul(dmul(omp, d2f(bc<T>(lam))), d2(u, ulo0));
+                const D2 srcd = dmul(dsub(phd, cpl), kS2);
+                const V<T> w = aniso_w2<T>(ex * bc<T>(ih_half), ey * bc<T>(ih_half), RR, eps, hh);
+                const D2 ad = dadd(kA0, d2f(w));
+                const D2 E = dadd(dadd(Ld, d2f(N)), srcd);
+                const D2 rate = dsub(ddiv(E, dmul(ad, ad)), dmul(dmul(phd, kS2), Gd));
+                const D2 d = dmul(rate, kDT);
+                const D2 s1 = two_sum(C0, d.h);
+                const D2 s2 = fast_two_sum(s1.h, s1.l + (cl + d.l));
+                psin = s2.h;
+                psin_lo = s2.l;
+                const V<T> phh = phd.h;
+                dph = mk((T)dphi_acc((float)phh.x(), (float)d.h.x()), (T)dphi_acc((float)phh.y(), (float)d.h.y()));
+                phin = phh + dph;
+                rate_o = rate.h;
                 return;
             }
             const V<T> src = bc<T>(SQ2) * (ph - bc<T>(lam) * (bc<T>(T(1)) - ph * ph) * u);
@@ -590,7 +783,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             if (DS) rate = rate * bc<T>(iF1);
             rate_o = rate;
             psin = fma(bc<T>(dt), rate, C0);
-            psin_lo = lo0;
+            psin_lo = L0.C();
             phin = mk(M<T>::tanh_isq2(psin.x()), M<T>::tanh_isq2(psin.y()));
             dph = phin - ph;
             if (DS) {
@@ -713,7 +906,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
         Row<T> PH1, UU0, UU1, DP0;
         Row<T> AD0, AA0;  // alpha rows of row r
         Row<T> UL0, UL1;  // compensated state: lo halves of U rows r, r+1
-        V<T> PL1 = bc<T>(T(0));  // compensated state: lo half of psi, own columns of row r+1
+        Row<T> LP[3];     // compensated state: lo halves of psi rows r .. r+2
         V<T> phin_cur;    // phi' at row r
         auto psi_store = [&](int row, V<T> hi, V<T> lo, V<T> rt) {
             if constexpr (MODE == 2) return;  // the U pass leaves psi' to the psi pass
@@ -730,20 +923,22 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                 P[i] = make_row(a, b, S == S21);
             }
             P[0] = P[1];
-            V<T> plm = bc<T>(T(0)), pl0 = bc<T>(T(0));
+            // compensated state: psi lo rows y0-2 .. y0+1, U lo rows y0-1, y0
+            Row<T> lq[4];
             Row<T> ulm = make_row(T(0), T(0), false), ul0 = ulm;
+            for (int i = 0; i < 4; ++i) lq[i] = ulm;
             if constexpr (CMP) {
-                fetch_row(psiL, y0 - 1, a, b);
-                plm = mk(a, b);
-                fetch_row(psiL, y0, a, b);
-                pl0 = mk(a, b);
+                for (int i = 0; i < 4; ++i) {
+                    fetch_row(psiL, y0 - 2 + i, a, b);
+                    lq[i] = make_row(a, b, false);
+                }
                 fetch_row(UfL, y0 - 1, a, b);
                 ulm = make_row(a, b, false);
                 fetch_row(UfL, y0, a, b);
                 ul0 = make_row(a, b, false);
             }
-            const Row<T> phm = CMP ? phi_row_c(P[2], plm) : phi_row(P[2]);
-            const Row<T> ph0 = CMP ? phi_row_c(P[3], pl0) : phi_row(P[3]);
+            const Row<T> phm = CMP ? phi_row_c(P[2], lq[1].C()) : phi_row(P[2]);
+            const Row<T> ph0 = CMP ? phi_row_c(P[3], lq[2].C()) : phi_row(P[3]);
             fetch_row(Uf, y0 - 1, a, b);
             const Row<T> um = make_row(a, b, false);
             fetch_row(Uf, y0, a, b);
@@ -755,10 +950,10 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             const bool ghost = (y0 - 1) < 0;
             if (!ghost && MODE != 1) {
                 load_grain_pair(grain + (size_t)PF_CHK((y0 - 1), ny) * nx, cL, nx, vec, per, gL, gR);
-                phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, plm, psn, psnl, fn, dm, rt);
+                phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, lq[0], lq[1], lq[2], ulm.C(), psn, psnl, fn, dm, rt);
             }
             load_grain_pair(grain + (size_t)PF_CHK(y0, ny) * nx, cL, nx, vec, per, gL, gR);
-            phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, pl0, psn, psnl, fn, d0, rt);
+            phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, lq[1], lq[2], lq[3], ul0.C(), psn, psnl, fn, d0, rt);
             if (ghost) dm = d0;
             phin_cur = fn;
             if (y0 < y1) psi_store(y0, psn, psnl, rt);
@@ -775,6 +970,8 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             P[3] = P[4];
             UU0 = u0;
             UL0 = ul0;
+            LP[0] = lq[2];
+            LP[1] = lq[3];
             DP0 = d0r;
         }
 
@@ -785,7 +982,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
         fetch_row(psi, y0 + 2, nPa, nPb);
         fetch_row(Uf, y0 + 1, nUa, nUb);
         if constexpr (CMP) {
-            fetch_row(psiL, y0 + 1, nPLa, nPLb);
+            fetch_row(psiL, y0 + 2, nPLa, nPLb);
             fetch_row(UfL, y0 + 1, nULa, nULb);
         }
         if (y0 + 1 < ny) load_grain_pair(grain + (size_t)PF_CHK((y0 + 1), ny) * nx, cL, nx, vec, per, nGa, nGb);
@@ -795,15 +992,15 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             P[4] = make_row(nPa, nPb, S == S21);
             UU1 = make_row(nUa, nUb, false);
             if constexpr (CMP) {
-                PL1 = mk(nPLa, nPLb);
+                LP[2] = make_row(nPLa, nPLb, false);
                 UL1 = make_row(nULa, nULb, false);
             }
-            PH1 = CMP ? phi_row_c(P[3], PL1) : phi_row(P[3]);
+            PH1 = CMP ? phi_row_c(P[3], LP[1].C()) : phi_row(P[3]);
             const int gL = nGa, gR = nGb;
             fetch_row(psi, r + 3, nPa, nPb);
             fetch_row(Uf, r + 2, nUa, nUb);
             if constexpr (CMP) {
-                fetch_row(psiL, r + 2, nPLa, nPLb);
+                fetch_row(psiL, r + 3, nPLa, nPLb);
                 fetch_row(UfL, r + 2, nULa, nULb);
             }
             if (r + 2 < ny) load_grain_pair(grain + (size_t)PF_CHK((r + 2), ny) * nx, cL, nx, vec, per, nGa, nGb);
@@ -814,7 +1011,8 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             Row<T> DP1;
             if (r + 1 < ny && (MODE != 1 || r + 1 < y1)) {
                 V<T> psn, psnl, d, rt;
-                phase1(r + 1, P[2], P[3], P[4], PH1, UU1, gL, gR, PL1, psn, psnl, phn, d, rt);
+                phase1(r + 1, P[2], P[3], P[4], PH1, UU1, gL, gR, LP[0], LP[1], LP[2], UL1.C(), psn, psnl, phn, d,
+                       rt);
                 if (r + 1 < y1) psi_store(r + 1, psn, psnl, rt);
                 DP1 = dphi_row(d);
             } else {
@@ -858,7 +1056,11 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             P[2] = P[3];
             P[3] = P[4];
             UU0 = UU1;
-            if constexpr (CMP) UL0 = UL1;
+            if constexpr (CMP) {
+                UL0 = UL1;
+                LP[0] = LP[1];
+                LP[1] = LP[2];
+            }
             DP0 = DP1;
             AD0 = AD1;
             AA0 = AA1;

@@ -137,6 +137,9 @@ class Server:
         self.admit_t: Dict[int, float] = {}
         self.results: List[Result] = []
         self.cell_steps = 0
+        self.cell_steps_by_dim = {2: 0, 3: 0}
+        self.max_running_seen = 0
+        self.peak_bytes = 0
 
     def _params(self, r: Request):
         w = r.workload
@@ -193,6 +196,10 @@ class Server:
             if n > 0:
                 self.group.step(n, use_graph=self.use_graph)
                 self.cell_steps += n * sum(s.n_cells for s in self.sims.values())
+                for s in self.sims.values():
+                    self.cell_steps_by_dim[s.p.dim] += n * s.n_cells
+                self.max_running_seen = max(self.max_running_seen, len(self.sims))
+                self.peak_bytes = max(self.peak_bytes, self.sched.used)
             self.stream.synchronize()  # bound the queue depth: times below are device-complete
             for rid in [rid for rid in self.sims if self.sims[rid].steps_done >= self.target[rid]]:
                 self._retire(rid, now)
@@ -202,7 +209,9 @@ class Server:
     def summary(self) -> dict:
         ttr = [r.time_to_result for r in self.results]
         return {"requests": len(self.results), "p50_s": percentile(ttr, 50), "p99_s": percentile(ttr, 99),
-                "wall_s": self.wall_s, "glups": self.cell_steps / self.wall_s / 1e9 if self.wall_s > 0 else 0.0}
+                "wall_s": self.wall_s, "glups": self.cell_steps / self.wall_s / 1e9 if self.wall_s > 0 else 0.0,
+                "cell_updates_2d": self.cell_steps_by_dim[2], "cell_updates_3d": self.cell_steps_by_dim[3],
+                "max_running": self.max_running_seen, "peak_bytes": self.peak_bytes, "budget_bytes": self.budget}
 
     def close(self):
         for rid in list(self.sims):

@@ -7,7 +7,10 @@ d psi/dt back and applies the T0 update of Eq. PF_b.  Checks:
     schemes, ragged grids with several grains, and over several steps;
   * the same values as the fused T0 step: the rate is the same arithmetic,
     stored and reloaded at the field precision, so the two forms agree bit for
-    bit in FP32 and FP64, alone and in a group replayed from CUDA graphs;
+    bit in FP32 (explicitly rounded packed operations), alone and in a group
+    replayed from CUDA graphs, and to round-off in FP64 (where the compiler
+    may contract a product and a sum into an FMA in one kernel and not in the
+    other: 1e-15 relative per step);
   * frozen temperature with periodic x (the same kernel variant) against the
     oracle.
 """
@@ -80,7 +83,10 @@ def test_equals_fused_t0_bit_for_bit(native, scheme, prec):
         out[kernels] = s.get_fields()
         s.close()
     for a, b in zip(out[native.PF_FUSED], out[native.PF_TWO_KERNELS]):
-        assert np.array_equal(a, b)
+        if prec == "f32":
+            assert np.array_equal(a, b)  # explicitly rounded FP32 operations: bit for bit
+        else:  # the compiler may contract a FP64 product and sum differently in the two kernels
+            assert rel_err(a, b) < 6e-15
 
 
 def test_group_graph_equals_alone(native):
