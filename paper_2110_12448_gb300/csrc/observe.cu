@@ -63,62 +63,92 @@ __device__ void observe_block(const ObsArgs& a, ObsPartial* __restrict__ partial
     // precision (both here and in C libraries that return +-1 from |x| = 22
     // on).  Those bulk cells contribute 1 + (1-k) U (liquid) or k (1 + (1-k) U)
     // (solid) to the solute sum and 0 or 1 to the solid sum: they are counted
-    // and their U summed in FP64, and the terms formed once per thread.  Rows
+    // and their U summed, and the terms formed once per thread.  Rows
     // are walked whole (one block per row, threads along x), so no cell index
-    // is divided.
+    // is divided.  The bulk U is summed exactly in FP32 pairs (Knuth's
+    // two-sum: hi + lo carries ~48 bits, more than the FP64 sum of these FP32
+    // values keeps) rather than in FP64, whose conversions and adds run at
+    // GB300's low FP64 rate; the non-finite test also runs in the field
+    // precision.
     long long n_liq = 0, n_sol = 0;
-    double u_liq = 0.0, u_sol = 0.0;
+    T sl_hi = T(0), sl_lo = T(0), ss_hi = T(0), ss_lo = T(0);
+    auto acc2 = [](T& hi, T& lo, T v) {
+        if constexpr (sizeof(T) == 4) {
+            const T sm = hi + v, bb = sm - hi;
+            lo += (hi - (sm - bb)) + (v - bb);
+            hi = sm;
+        } else {
+            hi += v;  // FP64 fields: the plain FP64 sum
+        }
+    };
     const long long rows = ny * nz;
+    // one cell: returns after the tip test (the bulk liquid returns early)
+    auto cell = [&](long long i, long long j, long long kk, long long c, T pst, T ut) {
+        if (!isfinite(pst) || !isfinite(ut)) {
+            acc.nonfinite += 1;
+            return;
+        }
+        if (fabs(pst) >= T(32)) {
+            if (pst > T(0)) {
+                n_sol += 1;
+                acc2(ss_hi, ss_lo, ut);
+            } else {
+                n_liq += 1;
+                acc2(sl_hi, sl_lo, ut);
+                return;  // liquid: no tip candidate
+            }
+        } else {
+            const double u = (double)ut;
+            const double ph = tanh((double)pst / SQ2);
+            acc.solute += (1.0 + k - omk * ph) * (1.0 + omk * u) / 2.0;
+            acc.solid += (1.0 + ph) / 2.0;
+        }
+        if (a.grain_filter >= 0 && a.grain[c] != a.grain_filter) return;
+        if (!(pst >= T(0))) return;
+        long long ii = i, jj = j, kq = kk;
+        if (a.ea == 0) ii += a.es;
+        else if (a.ea == 1) jj += a.es;
+        else kq += a.es;
+        if (ii < 0 || jj < 0 || kq < 0 || ii >= nx || jj >= ny || kq >= nz) return;
+        const T pnt = psi[PF_CHK((kq * ny + jj) * nx + ii, N)];
+        if (!(pnt < T(0))) return;
+        const double ps = (double)pst, pn = (double)pnt;
+        const double frac = __ddiv_rn(ps, __dsub_rn(ps, pn));
+        double p[3] = {__dmul_rn((double)i, a.h), __dmul_rn((double)j, a.h),
+                       a.dim == 3 ? __dmul_rn((double)kk, a.h) : 0.0};
+        p[a.ea] = __dadd_rn(p[a.ea], __dmul_rn((double)a.es * frac, a.h));
+        double sc = 0.0;
+        for (int q = 0; q < a.dim; ++q) sc = __dadd_rn(sc, __dmul_rn(__dsub_rn(p[q], a.cg[q]), a.d[q]));
+        if (better(sc, c, acc.score, acc.tip_index)) {
+            acc.score = sc;
+            acc.tip_index = c;
+            acc.tip[0] = p[0];
+            acc.tip[1] = p[1];
+            acc.tip[2] = p[2];
+        }
+    };
+    // FP32 rows whose length is a multiple of 4 are read four cells at a time
+    // (16-byte vector loads: more bytes in flight per thread); other rows cell
+    // by cell.  The order of the per-thread sums differs between the two, not
+    // the cells each block covers.
+    const bool vec4 = sizeof(T) == 4 && (nx & 3) == 0 && ((uintptr_t)psi & 15) == 0 && ((uintptr_t)U & 15) == 0;
     for (long long row = blk; row < rows; row += nblk) {
         const long long j = row % ny, kk = row / ny;
         const long long base = row * nx;
-        for (long long i = threadIdx.x; i < nx; i += blockDim.x) {
-            const long long c = base + i;
-            const T pst = psi[c];
-            const T ut = U[c];
-            const double ps = (double)pst, u = (double)ut;
-            if (!isfinite(ps) || !isfinite(u)) {
-                acc.nonfinite += 1;
-                continue;
+        if (vec4) {
+            for (long long i = 4 * (long long)threadIdx.x; i < nx; i += 4 * (long long)blockDim.x) {
+                const float4 p4 = __ldg(reinterpret_cast<const float4*>(psi + PF_CHK(base + i, N)));
+                const float4 u4 = __ldg(reinterpret_cast<const float4*>(U + PF_CHK(base + i, N)));
+                cell(i, j, kk, base + i, (T)p4.x, (T)u4.x);
+                cell(i + 1, j, kk, base + i + 1, (T)p4.y, (T)u4.y);
+                cell(i + 2, j, kk, base + i + 2, (T)p4.z, (T)u4.z);
+                cell(i + 3, j, kk, base + i + 3, (T)p4.w, (T)u4.w);
             }
-            if (fabs(pst) >= T(32)) {
-                if (pst > T(0)) {
-                    n_sol += 1;
-                    u_sol += u;
-                } else {
-                    n_liq += 1;
-                    u_liq += u;
-                    continue;  // liquid: no tip candidate
-                }
-            } else {
-                const double ph = tanh(ps / SQ2);
-                acc.solute += (1.0 + k - omk * ph) * (1.0 + omk * u) / 2.0;
-                acc.solid += (1.0 + ph) / 2.0;
-            }
-            if (a.grain_filter >= 0 && a.grain[c] != a.grain_filter) continue;
-            if (!(ps >= 0.0)) continue;
-            long long ii = i, jj = j, kq = kk;
-            if (a.ea == 0) ii += a.es;
-            else if (a.ea == 1) jj += a.es;
-            else kq += a.es;
-            if (ii < 0 || jj < 0 || kq < 0 || ii >= nx || jj >= ny || kq >= nz) continue;
-            const double pn = (double)psi[PF_CHK((kq * ny + jj) * nx + ii, N)];
-            if (!(pn < 0.0)) continue;
-            const double frac = __ddiv_rn(ps, __dsub_rn(ps, pn));
-            double p[3] = {__dmul_rn((double)i, a.h), __dmul_rn((double)j, a.h),
-                           a.dim == 3 ? __dmul_rn((double)kk, a.h) : 0.0};
-            p[a.ea] = __dadd_rn(p[a.ea], __dmul_rn((double)a.es * frac, a.h));
-            double sc = 0.0;
-            for (int q = 0; q < a.dim; ++q) sc = __dadd_rn(sc, __dmul_rn(__dsub_rn(p[q], a.cg[q]), a.d[q]));
-            if (better(sc, c, acc.score, acc.tip_index)) {
-                acc.score = sc;
-                acc.tip_index = c;
-                acc.tip[0] = p[0];
-                acc.tip[1] = p[1];
-                acc.tip[2] = p[2];
-            }
+        } else {
+            for (long long i = threadIdx.x; i < nx; i += blockDim.x) cell(i, j, kk, base + i, psi[base + i], U[base + i]);
         }
     }
+    const double u_liq = (double)sl_hi + (double)sl_lo, u_sol = (double)ss_hi + (double)ss_lo;
     acc.solute += ((double)n_liq + omk * u_liq) + k * ((double)n_sol + omk * u_sol);
     acc.solid += (double)n_sol;
     sh[threadIdx.x] = acc;

@@ -805,9 +805,13 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
         // the own columns (x 6 h^2 for the D~_{2,1} forms, x h^2 for S_{1,0})
         // and updates the carries.  need_x = false skips S_{2,1}'s x-face
         // magnitudes, which would read row q-2.
+        // skipA (warp-uniform): delta phi is exactly 0 on the rows q-1 .. q+1 of
+        // the whole warp (bulk liquid or solid, where phi = +-1 exactly), so
+        // every anti-trapping flux these rows form or carry is exactly 0: sA = 0
+        // and the anti-trapping carries are 0, as the full evaluation gives.
         auto fluxes = [&](const Row<T>& aD0, const Row<T>& aD1, const Row<T>& aA0, const Row<T>& aA1,
                           const Row<T>& bU0, const Row<T>& bU1, const Row<T>& bL0, const Row<T>& bL1, const Row<T>* Pq,
-                          bool need_x, V<T>& sD, V<T>& sA) {
+                          bool need_x, bool skipA, V<T>& sD, V<T>& sA) {
             const Row<T>& b0 = Pq[2];
             const Row<T>& b1 = Pq[3];
             // differences of U; the compensated state adds those of the lo halves
@@ -819,6 +823,13 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                 const V<T> half = bc<T>(T(0.5));
                 const V<T> fxD = half * (aD0.C() + aD0.E()) * dU(bU0.E() - bU0.C(), bL0.E() - bL0.C());
                 const V<T> fyD = half * (aD0.C() + aD1.C()) * dU(bU1.C() - bU0.C(), bL1.C() - bL0.C());
+                sD = (fxD - mk(shup(fxD.y()), fxD.x())) + (fyD - cFYm_D);
+                cFYm_D = fyD;
+                if (skipA) {
+                    sA = bc<T>(T(0));
+                    cFYm_A = bc<T>(T(0));
+                    return;
+                }
                 const Row<T>& bm = Pq[1];
                 const V<T> dxp = b0.E() - b0.C(), dyp = b1.C() - b0.C();
                 const V<T> gx = dxp * bc<T>(ih), gy = ((b1.E() + b1.C()) - (bm.E() + bm.C())) * bc<T>(i4h);
@@ -828,9 +839,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                                                  mk(M<T>::sqrt_(mx.x()), M<T>::sqrt_(mx.y())), hh);
                 const V<T> fyA = guarded_div2<T>(half * (aA0.C() + aA1.C()) * dyp,
                                                  mk(M<T>::sqrt_(my.x()), M<T>::sqrt_(my.y())), hh);
-                sD = (fxD - mk(shup(fxD.y()), fxD.x())) + (fyD - cFYm_D);
                 sA = (fxA - mk(shup(fxA.y()), fxA.x())) + (fyA - cFYm_A);
-                cFYm_D = fyD;
                 cFYm_A = fyA;
                 return;
             }
@@ -838,13 +847,26 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             // corner means: the (+1/2, +1/2) corners of (L, R) and of (L-1, L)
             const V<T> KC_D = q4 * ((aD0.C() + aD0.E()) + (aD1.C() + aD1.E()));
             const V<T> KW_D = q4 * ((aD0.W() + aD0.C()) + (aD1.W() + aD1.C()));
-            const V<T> KC_A = q4 * ((aA0.C() + aA0.E()) + (aA1.C() + aA1.E()));
-            const V<T> KW_A = q4 * ((aA0.W() + aA0.C()) + (aA1.W() + aA1.C()));
             // <10> faces x+, y+ (weight sums of Eq. flux_10) and <11> corners ++, -+
             const V<T> u0c = bU0.C(), l0c = bL0.C();
             const V<T> FXpD = ((aD0.C() + aD0.E()) + (KC_D + cK_D)) * dU(bU0.E() - u0c, bL0.E() - l0c);
             const V<T> FYpD = ((aD0.C() + aD1.C()) + (KC_D + KW_D)) * dU(bU1.C() - u0c, bL1.C() - l0c);
             const V<T> FPPD = KC_D * dU(bU1.E() - u0c, bL1.E() - l0c), FMPD = KW_D * dU(bU1.W() - u0c, bL1.W() - l0c);
+            sD = ((FXpD - mk(shup(FXpD.y()), FXpD.x())) + (FYpD - cFYm_D)) + ((FPPD + FMPD) - (cFDmm_D + cFDpm_D));
+            // carries for row q+1: its y- face is this y+ face, its (-1/2,-1/2)
+            // corner the (+1/2,+1/2) corner of the column to the left, its
+            // (+1/2,-1/2) corner the (-1/2,+1/2) corner of the column to the right
+            cFYm_D = FYpD;
+            cFDmm_D = mk(shup(FPPD.y()), FPPD.x());
+            cFDpm_D = mk(FMPD.y(), shdn(FMPD.x()));
+            cK_D = KC_D;
+            if (skipA) {
+                sA = bc<T>(T(0));
+                cFYm_A = cFDmm_A = cFDpm_A = cK_A = bc<T>(T(0));
+                return;
+            }
+            const V<T> KC_A = q4 * ((aA0.C() + aA0.E()) + (aA1.C() + aA1.E()));
+            const V<T> KW_A = q4 * ((aA0.W() + aA0.C()) + (aA1.W() + aA1.C()));
             const V<T> p0c = b0.C();
             V<T> FXpA = ((aA0.C() + aA0.E()) + (KC_A + cK_A)) * (b0.E() - p0c);
             V<T> FYpA = ((aA0.C() + aA1.C()) + (KC_A + KW_A)) * (b1.C() - p0c);
@@ -868,19 +890,15 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                     appb_floor2<T>(appb_corner2<T>([&](int p, int t) { return ps(p - 1, t); }, ih), b1.W() - p0c, ihd),
                     hh);
             }
-            sD = ((FXpD - mk(shup(FXpD.y()), FXpD.x())) + (FYpD - cFYm_D)) + ((FPPD + FMPD) - (cFDmm_D + cFDpm_D));
             sA = ((FXpA - mk(shup(FXpA.y()), FXpA.x())) + (FYpA - cFYm_A)) + ((FPPA + FMPA) - (cFDmm_A + cFDpm_A));
-            // carries for row q+1: its y- face is this y+ face, its (-1/2,-1/2)
-            // corner the (+1/2,+1/2) corner of the column to the left, its
-            // (+1/2,-1/2) corner the (-1/2,+1/2) corner of the column to the right
-            cFYm_D = FYpD;
             cFYm_A = FYpA;
-            cFDmm_D = mk(shup(FPPD.y()), FPPD.x());
             cFDmm_A = mk(shup(FPPA.y()), FPPA.x());
-            cFDpm_D = mk(FMPD.y(), shdn(FMPD.x()));
             cFDpm_A = mk(FMPA.y(), shdn(FMPA.x()));
-            cK_D = KC_D;
             cK_A = KC_A;
+        };
+        // delta phi row exactly 0 over the whole warp (see skipA)
+        auto zero_row = [&](const Row<T>& d) -> bool {
+            return __all_sync(FULL, d.l == T(0) && d.r == T(0));
         };
         auto alphaD = [&](const Row<T>& ph) {
             Row<T> a;
@@ -907,6 +925,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
         Row<T> AD0, AA0;  // alpha rows of row r
         Row<T> UL0, UL1;  // compensated state: lo halves of U rows r, r+1
         Row<T> LP[3];     // compensated state: lo halves of psi rows r .. r+2
+        bool zA_prev = false, zA0 = false;  // delta phi rows r-1, r exactly 0 over the warp
         V<T> phin_cur;    // phi' at row r
         auto psi_store = [&](int row, V<T> hi, V<T> lo, V<T> rt) {
             if constexpr (MODE == 2) return;  // the U pass leaves psi' to the psi pass
@@ -963,7 +982,9 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             AD0 = alphaD(ph0);
             AA0 = alphaA(u0, d0r);
             V<T> s0, s1;
-            if constexpr (MODE != 1) fluxes(aDm, AD0, aAm, AA0, um, u0, ulm, ul0, P, false, s0, s1);
+            zA_prev = zero_row(dmr);
+            zA0 = zero_row(d0r);
+            if constexpr (MODE != 1) fluxes(aDm, AD0, aAm, AA0, um, u0, ulm, ul0, P, false, zA_prev && zA0, s0, s1);
             P[0] = P[1];
             P[1] = P[2];
             P[2] = P[3];
@@ -1028,10 +1049,12 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             }
 
             // phase 2 at row r
+            const bool zA1 = zero_row(DP1);
+            const bool skipA = zA_prev && zA0 && zA1;
             const Row<T> AD1 = alphaD(PH1), AA1 = alphaA(UU1, DP1);
             {
                 V<T> sD, sA;
-                fluxes(AD0, AD1, AA0, AA1, UU0, UU1, UL0, UL1, P, true, sD, sA);
+                fluxes(AD0, AD1, AA0, AA1, UU0, UU1, UL0, UL1, P, true, skipA, sD, sA);
                 const T cs = (S == S10) ? ih2 : i6h2;
                 const V<T> u = UU0.C();
                 const V<T> num =
@@ -1064,6 +1087,8 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             DP0 = DP1;
             AD0 = AD1;
             AA0 = AA1;
+            zA_prev = zA0;
+            zA0 = zA1;
         }
     }
 }

@@ -135,6 +135,23 @@ __device__ __forceinline__ P2<double> fma2(P2<double> a, P2<double> b, P2<double
 }
 template <typename T> __device__ __forceinline__ P2<T> bc2(T c) { return p2(c, c); }
 
+// shared-memory element of a (D, anti-trapping) pair: one 8- or 16-byte load
+template <typename T> struct Pair3;
+template <> struct Pair3<float> {
+    using t = float2;
+    static __device__ __forceinline__ P2<float> get(float2 v) {
+        P2<float> r;
+        r.v = v;
+        return r;
+    }
+    static __device__ __forceinline__ float2 put(float d, float a) { return make_float2(d, a); }
+};
+template <> struct Pair3<double> {
+    using t = double2;
+    static __device__ __forceinline__ P2<double> get(double2 v) { return p2(v.x, v.y); }
+    static __device__ __forceinline__ double2 put(double d, double a) { return make_double2(d, a); }
+};
+
 template <typename T> struct ConstOf3;
 template <> struct ConstOf3<float> {
     static __device__ __forceinline__ const float* get(const InstRec& r) { return r.cf; }
@@ -168,10 +185,11 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
     T* s_phi = s_psi + 8 * PX * PY;             // [8][AY][AX]
     T* s_U = s_phi + 8 * NT;                    // [4][AY][AX]
     T* s_dphi = s_U + 4 * NT;                   // [4][AY][AX]
-    T* s_aD = s_dphi + 4 * NT;                  // [4][AY][AX] alpha of D = 1 - phi
-    T* s_aA = s_aD + 4 * NT;                    // [4][AY][AX] alpha of the anti-trapping term
-    T* s_fi = s_aA + 4 * NT;                    // [2 fields][NFI][NT] owned in-plane fluxes
-    T* s_fz = s_fi + 2 * NFI * NT;              // [2 buffers][2 fields][NFZ][NT] owned fluxes to the next plane
+    // (D, anti-trapping) pairs, interleaved so that a packed pair is one load:
+    using T2 = typename Pair3<T>::t;
+    T2* s_al = reinterpret_cast<T2*>(s_dphi + 4 * NT);  // [4][AY][AX] alphas: 1 - phi and the anti-trapping alpha
+    T2* s_fi = s_al + 4 * NT;                            // [NFI][NT] owned in-plane fluxes
+    T2* s_fz = s_fi + NFI * NT;                          // [2 buffers][NFZ][NT] owned fluxes to the next plane
     const int tid = threadIdx.x;
     const int tx = tid % AX, ty = tid / AX;
     const T SQ2 = T(1.41421356237309504880);
@@ -229,6 +247,13 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
         auto RG = [&](T* base, int slots, int z, int y, int x) -> T& {
             return s_psi[PF_CHK((base - s_psi) + (((z & (slots - 1)) * AY + y) * AX + x), SM_ELEMS)];
         };
+        // pair arrays, indexed in pairs; the checked build bounds a pair by the
+        // whole allocation (two elements)
+        constexpr long long SM_PAIRS = SM_ELEMS / 2;
+        auto PR = [&](T2* base, long long i) -> T2& {
+            return reinterpret_cast<T2*>(s_psi)[PF_CHK((base - reinterpret_cast<T2*>(s_psi)) + i, SM_PAIRS)];
+        };
+        auto AL = [&](int z, int y, int x) -> T2& { return PR(s_al, ((z & 3) * AY + y) * AX + x); };
 
         // plane loads, split into a global fetch into registers (issued one
         // plane ahead) and a store into the shared-memory rings
@@ -345,15 +370,13 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             // T1: delta phi = phi' - phi; T0: chain-rule increment, phi^n on the left-hand side
             const T dph = t0 ? dt * (T(1) - ph * ph) * ISQ2 * rate : phn - ph;
             RG(s_dphi, 4, p, ty, tx) = dph;
-            RG(s_aD, 4, p, ty, tx) = T(1) - ph;
-            RG(s_aA, 4, p, ty, tx) = (T(1) + omk * u) * dph * isq2dt;
+            AL(p, ty, tx) = Pair3<T>::put(T(1) - ph, (T(1) + omk * u) * dph * isq2dt);
             return t0 ? ph : phn;
         };
         // ghost plane vz takes the slot values of plane mz
         auto copy_plane = [&](int vz, int mz) {
             RG(s_dphi, 4, vz, ty, tx) = RG(s_dphi, 4, mz, ty, tx);
-            RG(s_aD, 4, vz, ty, tx) = RG(s_aD, 4, mz, ty, tx);
-            RG(s_aA, 4, vz, ty, tx) = RG(s_aA, 4, mz, ty, tx);
+            AL(vz, ty, tx) = AL(mz, ty, tx);
         };
 
         // Owned phase-2 fluxes of this ring cell: in-plane at plane r (into
@@ -362,18 +385,14 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
         // for S_{1,0,0}; fluxes whose stencil leaves the ring region are set to
         // zero (no output cell uses them).
         auto owned_fluxes = [&](int r, int buf) {
-            auto aD = [&](int dx, int dy, int dz) -> T { return RG(s_aD, 4, r + dz, ty + dy, tx + dx); };
-            auto aA = [&](int dx, int dy, int dz) -> T { return RG(s_aA, 4, r + dz, ty + dy, tx + dx); };
+            auto aD = [&](int dx, int dy, int dz) -> T { return AL(r + dz, ty + dy, tx + dx).x; };
+            auto aA = [&](int dx, int dy, int dz) -> T { return AL(r + dz, ty + dy, tx + dx).y; };
             auto bU = [&](int dx, int dy, int dz) -> T { return RG(s_U, 4, r + dz, ty + dy, tx + dx); };
             auto bP = [&](int dx, int dy, int dz) -> T { return PS(r + dz, ty + 1 + dy, tx + 1 + dx); };
             const bool xm = tx >= 1, xp = tx + 1 < AX, ym = ty >= 1, yp = ty + 1 < AY;
-            T* fiD = s_fi + tid;
-            T* fiA = s_fi + NFI * NT + tid;
-            T* fzD = s_fz + (buf * 2 * NFZ) * NT + tid;
-            T* fzA = s_fz + (buf * 2 * NFZ + NFZ) * NT + tid;
             const T u0 = bU(0, 0, 0), p0 = bP(0, 0, 0);
-            // (D, A) pairs of alpha and beta
-            auto A2 = [&](int dx, int dy, int dz) -> P2<T> { return p2(aD(dx, dy, dz), aA(dx, dy, dz)); };
+            // (D, A) pairs of alpha (one load) and beta
+            auto A2 = [&](int dx, int dy, int dz) -> P2<T> { return Pair3<T>::get(AL(r + dz, ty + dy, tx + dx)); };
             auto B2 = [&](int dx, int dy, int dz) -> P2<T> { return p2(bU(dx, dy, dz), bP(dx, dy, dz)); };
             const P2<T> b00 = p2(u0, p0);
             // face toward e: returns (D, A) flux
@@ -475,27 +494,22 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                 ok[NFI + 4] = ym && xm && xp;
             }
 #pragma unroll
-            for (int q = 0; q < NFI; ++q) {
-                s_psi[PF_CHK((fiD - s_psi) + q * NT, SM_ELEMS)] = ok[q] ? oD[q] : T(0);
-                s_psi[PF_CHK((fiA - s_psi) + q * NT, SM_ELEMS)] = ok[q] ? oA[q] : T(0);
-            }
+            for (int q = 0; q < NFI; ++q)
+                PR(s_fi, (long long)q * NT + tid) = Pair3<T>::put(ok[q] ? oD[q] : T(0), ok[q] ? oA[q] : T(0));
 #pragma unroll
-            for (int q = 0; q < NFZ; ++q) {
-                s_psi[PF_CHK((fzD - s_psi) + q * NT, SM_ELEMS)] = ok[NFI + q] ? oD[NFI + q] : T(0);
-                s_psi[PF_CHK((fzA - s_psi) + q * NT, SM_ELEMS)] = ok[NFI + q] ? oA[NFI + q] : T(0);
-            }
+            for (int q = 0; q < NFZ; ++q)
+                PR(s_fz, (long long)(buf * NFZ + q) * NT + tid) =
+                    Pair3<T>::put(ok[NFI + q] ? oD[NFI + q] : T(0), ok[NFI + q] ? oA[NFI + q] : T(0));
         };
         // eight/eighteen-flux sums of an output cell at plane r: own fluxes
         // plus the negated owned fluxes of the neighbours that share them
         auto flux_sum = [&](int bufz_cur, int bufz_prev, T& sD, T& sA) {
-            auto FI = [&](int f, int k, int dx, int dy) -> T {
-                return s_fi[PF_CHK((f * NFI + k) * NT + tid + dy * AX + dx, 2 * NFI * NT)];
+            auto FI2 = [&](int k, int dx, int dy) -> P2<T> {
+                return Pair3<T>::get(s_fi[PF_CHK(k * NT + tid + dy * AX + dx, NFI * NT)]);
             };
-            auto FZ = [&](int b, int f, int k, int dx, int dy) -> T {
-                return s_fz[PF_CHK(((b * 2 + f) * NFZ + k) * NT + tid + dy * AX + dx, 2 * 2 * NFZ * NT)];
+            auto FZ2 = [&](int b, int k, int dx, int dy) -> P2<T> {
+                return Pair3<T>::get(s_fz[PF_CHK((b * NFZ + k) * NT + tid + dy * AX + dx, 2 * NFZ * NT)]);
             };
-            auto FI2 = [&](int k, int dx, int dy) -> P2<T> { return p2(FI(0, k, dx, dy), FI(1, k, dx, dy)); };
-            auto FZ2 = [&](int b, int k, int dx, int dy) -> P2<T> { return p2(FZ(b, 0, k, dx, dy), FZ(b, 1, k, dx, dy)); };
             P2<T> a = (FI2(0, 0, 0) - FI2(0, -1, 0)) + (FI2(1, 0, 0) - FI2(1, 0, -1));
             a = a + (FZ2(bufz_cur, 0, 0, 0) - FZ2(bufz_prev, 0, 0, 0));
             if (ISO) {
