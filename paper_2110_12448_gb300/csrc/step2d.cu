@@ -410,6 +410,13 @@ __device__ __forceinline__ D2 dexp_neg(D2 x) {
     return D2{e.h * p2, e.l * p2};
 }
 
+// |psi| beyond which the FP64 library tanh of psi / sqrt2 returns exactly
+// +-1 (from |psi / sqrt2| ~ 19 on).  FP64 rows beyond it take phi = sign(psi)
+// without the tanh, which is expensive at GB300's FP64 rate (+31% for the FP64
+// sweep); the FP32 exp2/reciprocal form costs less than the warp vote.
+template <typename T> struct Bulk;
+template <> struct Bulk<double> { static constexpr double psi = 32.0; };
+
 template <typename T> struct ConstOf;
 template <> struct ConstOf<float> {
     static __device__ __forceinline__ const float* get(const InstRec& r) { return r.cf; }
@@ -575,8 +582,23 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             }
             return row;
         };
+        // phi of a row; FP64: where |psi| exceeds the saturation bound on the
+        // whole row of the warp, phi = sign(psi) exactly (what tanh returns),
+        // taken without the tanh and, since the row's neighbours are already in
+        // place, without the shuffles
         auto phi_row = [&](const Row<T>& p) {
             Row<T> o;
+            if constexpr (sizeof(T) == 8) {
+                const T B = Bulk<T>::psi;
+                if (__all_sync(FULL, fabs(p.l) > B && fabs(p.r) > B)) {
+                    o.l = p.l > T(0) ? T(1) : T(-1);
+                    o.r = p.r > T(0) ? T(1) : T(-1);
+                    o.m1 = p.m1 > T(0) ? T(1) : T(-1);
+                    o.p1 = p.p1 > T(0) ? T(1) : T(-1);
+                    o.m2 = o.p2 = T(0);
+                    return o;
+                }
+            }
             o.l = M<T>::tanh_isq2(p.l);
             o.r = M<T>::tanh_isq2(p.r);
             o.m1 = shup(o.r);
@@ -784,7 +806,15 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             rate_o = rate;
             psin = fma(bc<T>(dt), rate, C0);
             psin_lo = L0.C();
-            phin = mk(M<T>::tanh_isq2(psin.x()), M<T>::tanh_isq2(psin.y()));
+            if constexpr (sizeof(T) == 8) {
+                const T B = Bulk<T>::psi;
+                if (__all_sync(FULL, fabs(psin.x()) > B && fabs(psin.y()) > B))
+                    phin = mk(psin.x() > T(0) ? T(1) : T(-1), psin.y() > T(0) ? T(1) : T(-1));
+                else
+                    phin = mk(M<T>::tanh_isq2(psin.x()), M<T>::tanh_isq2(psin.y()));
+            } else {
+                phin = mk(M<T>::tanh_isq2(psin.x()), M<T>::tanh_isq2(psin.y()));
+            }
             dph = phin - ph;
             if (DS) {
                 // T0: chain-rule increment dt (1 - phi^2)/sqrt2 dpsi/dt and phi^n on the left-hand side

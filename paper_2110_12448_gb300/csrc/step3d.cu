@@ -37,7 +37,9 @@ template <> struct M3<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 };
 template <> struct M3<double> {
-    static __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
+    // tanh is exactly +-1 beyond |x| = 22.6 (|psi| = 32); the FP64 library
+    // tanh is expensive at GB300's FP64 rate, and most cells are that far
+    static __device__ __forceinline__ double tanh_(double x) { return fabs(x) > 22.6 ? copysign(1.0, x) : tanh(x); }
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 };

@@ -2,8 +2,9 @@
 subprocess with PF_LIBRARY pointing at the -DPF_BOUNDS_CHECK library): tiny,
 odd and ragged grids for every scheme, precision and variant (isothermal with
 mirror walls, frozen gradient with periodic x, T0), single handles and
-graph-replayed groups, both 3D tiles, observe and the tip radius.  Prints the
-failure count and the first failing source line."""
+graph-replayed groups (with the group observe), both 3D tiles, observe and
+the tip radius; the compensated FP32 state and the two-kernel form in 2D.
+Prints the failure count and the first failing source line."""
 import json
 import os
 import sys
@@ -17,6 +18,7 @@ from paper_2110_12448_gb300 import native as N  # noqa: E402
 from paper_2110_12448_gb300 import synth  # noqa: E402
 
 VARIANTS = [dict(), dict(bc_x=1, thermal=1, Vp=0.3, lT=60.0), dict(time_level=1)]
+TWO_KERNELS = dict(time_level=1, kernels=1)
 
 
 def run_case(dim, scheme, prec, shape, var, tile=None, group=False, stream=None):
@@ -34,7 +36,8 @@ def run_case(dim, scheme, prec, shape, var, tile=None, group=False, stream=None)
     g, rots = synth.random_grains(rng, w, 2)
     p = N.make_params(dim, w.nx, w.ny, w.nz, w.h, w.dt, w.k, w.eps4, w.lam, w.D, w.U0, scheme, prec,
                       max_grains=2, bc_x=var.get("bc_x", 0), thermal=var.get("thermal", 0), Vp=var.get("Vp", 0.0),
-                      lT=var.get("lT", 1.0), yT=w.yT, time_level=var.get("time_level", 0))
+                      lT=var.get("lT", 1.0), yT=w.yT, time_level=var.get("time_level", 0),
+                      kernels=var.get("kernels", 0))
     s = N.Sim(p, stream=stream)
     s.set_grains(rots)
     s.set_grain_index(g)
@@ -45,6 +48,7 @@ def run_case(dim, scheme, prec, shape, var, tile=None, group=False, stream=None)
         grp = N.Group(1, N.Group.work_items(s), stream=stream)
         grp.add(s)
         grp.step(18, use_graph=True)
+        grp.observe(0, allow_nonfinite=True)
         grp.close()
     else:
         s.step(3)
@@ -69,6 +73,11 @@ def main():
                     cases += 1
             run_case(2, scheme, prec, (70, 21), VARIANTS[1], group=True, stream=st)
             cases += 1
+            for shape in [(4, 4), (5, 9), (61, 7), (131, 47)]:
+                run_case(2, scheme, prec, shape, TWO_KERNELS, stream=st)
+                cases += 1
+            run_case(2, scheme, prec, (70, 21), TWO_KERNELS, group=True, stream=st)
+            cases += 1
         for scheme in ("SBAR120", "S100"):
             for shape in [(4, 4, 4), (5, 9, 4), (31, 15, 7), (37, 29, 17)]:
                 for var in VARIANTS:
@@ -77,6 +86,12 @@ def main():
                         cases += 1
             run_case(3, scheme, prec, (33, 17, 9), VARIANTS[1], group=True, stream=st)
             cases += 1
+    for scheme in ("SBAR21", "S21", "S10"):  # the compensated FP32 state
+        for shape in [(4, 4), (5, 9), (61, 7), (64, 5), (131, 47)]:
+            run_case(2, scheme, "f32c", shape, VARIANTS[0], stream=st)
+            cases += 1
+        run_case(2, scheme, "f32c", (70, 21), VARIANTS[0], group=True, stream=st)
+        cases += 1
     torch.cuda.synchronize()
     res = N.debug_bounds()
     print(json.dumps({"cases": cases, "checked": res is not None, "failures": None if res is None else res[0],
