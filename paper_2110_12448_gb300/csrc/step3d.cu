@@ -137,6 +137,30 @@ __device__ __forceinline__ P2<double> fma2(P2<double> a, P2<double> b, P2<double
 }
 template <typename T> __device__ __forceinline__ P2<T> bc2(T c) { return p2(c, c); }
 
+// Component `ax` of (J - g) for the two opposite faces of a cell along ax
+// (lab-frame face gradients g[p] = (g_p of the + face, g_p of the - face)),
+// both in the cell's crystal frame R: aniso_q3 on a packed pair.
+template <typename T>
+__device__ __forceinline__ P2<T> aniso_q3p(const P2<T> g[3], const T R[9], T eps, T hh, int ax) {
+    P2<T> c[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) c[p] = fma2(bc2<T>(R[p]), g[0], fma2(bc2<T>(R[3 + p]), g[1], bc2<T>(R[6 + p]) * g[2]));
+    const P2<T> r2 = fma2(c[0], c[0], fma2(c[1], c[1], c[2] * c[2]));
+    const bool zd = r2.d() * hh < Guard<T>::v, za = r2.a() * hh < Guard<T>::v;
+    const P2<T> inv = p2(M3<T>::rcp(r2.d()), M3<T>::rcp(r2.a()));
+    P2<T> sp[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) sp[p] = c[p] * c[p] * inv;
+    const P2<T> q = fma2(sp[0], sp[0], fma2(sp[1], sp[1], sp[2] * sp[2]));
+    const P2<T> a = fma2(bc2<T>(T(4) * eps), q, bc2<T>(T(1) - T(3) * eps));
+    const P2<T> c1 = bc2<T>(T(16) * eps) * a;
+    const P2<T> c0 = fma2(a, a, bc2<T>(T(-1))) - c1 * q;
+    P2<T> out = bc2<T>(T(0));
+#pragma unroll
+    for (int p = 0; p < 3; ++p) out = fma2(bc2<T>(R[3 * ax + p]), c[p] * fma2(c1, sp[p], c0), out);
+    return p2(zd ? T(0) : out.d(), za ? T(0) : out.a());
+}
+
 // shared-memory element of a (D, anti-trapping) pair: one 8- or 16-byte load
 template <typename T> struct Pair3;
 template <> struct Pair3<float> {
@@ -354,12 +378,30 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                 }
                 return aniso_q3<T>(gf, R, eps, hh, ax);
             };
+            // the two faces along x (and along y) as one packed pair (+ face, - face)
+            auto face_pair = [&](int ax) -> P2<T> {
+                P2<T> gf[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const int e[3] = {ax == 0, ax == 1, ax == 2};
+                    if (q == ax) {
+                        gf[q] = p2((P(e[0], e[1], e[2]) - pc) * ih, (pc - P(-e[0], -e[1], -e[2])) * ih);
+                    } else {
+                        const int t[3] = {q == 0, q == 1, q == 2};
+                        const P2<T> up = p2(P(e[0] + t[0], e[1] + t[1], e[2] + t[2]), P(-e[0] + t[0], -e[1] + t[1], -e[2] + t[2]));
+                        const P2<T> dn = p2(P(e[0] - t[0], e[1] - t[1], e[2] - t[2]), P(-e[0] - t[0], -e[1] - t[1], -e[2] - t[2]));
+                        gf[q] = ((up + bc2<T>(P(t[0], t[1], t[2]))) - (dn + bc2<T>(P(-t[0], -t[1], -t[2])))) * bc2<T>(i4h);
+                    }
+                }
+                return aniso_q3p<T>(gf, R, eps, hh, ax);
+            };
             const T qzp = face(2, 1);
             const T qzm = (pz_c == p && gz_c == g) ? qz_c : face(2, -1);
             qz_c = qzp;
             gz_c = g;
             pz_c = p + 1;
-            const T N = ((face(0, 1) - face(0, -1)) + (face(1, 1) - face(1, -1)) + (qzp - qzm)) * ih;
+            const P2<T> fx = face_pair(0), fy = face_pair(1);
+            const T N = (((fx.d() - fx.a()) + (fy.d() - fy.a())) + (qzp - qzm)) * ih;
             T gc[3] = {(P(1, 0, 0) - P(-1, 0, 0)) * T(0.5) * ih, (P(0, 1, 0) - P(0, -1, 0)) * T(0.5) * ih,
                        (P(0, 0, 1) - P(0, 0, -1)) * T(0.5) * ih};
             const T ac = aniso_a3<T>(gc, R, eps, hh);
