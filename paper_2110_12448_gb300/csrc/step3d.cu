@@ -337,7 +337,11 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                 for (int q = 0; q < 9; ++q) R[q] = __ldg(rot + 9 * PF_CHK(g, rec.n_grains) + q);
                 gR = g;
             }
-            auto P = [&](int dx, int dy, int dz) -> T { return PS(p + dz, jy + dy, jx + dx); };
+            // element offsets of the cell in its three psi planes, formed once:
+            // the neighbour offsets then fold into the loads' immediates
+            const int pb[3] = {(((p - 1) & 7) * PY + jy) * PX + jx, ((p & 7) * PY + jy) * PX + jx,
+                               (((p + 1) & 7) * PY + jy) * PX + jx};
+            auto P = [&](int dx, int dy, int dz) -> T { return s_psi[PF_CHK(pb[dz + 1] + dy * PX + dx, 8 * PX * PY)]; };
             const T pc = P(0, 0, 0);
             const T s100 = P(1, 0, 0) + P(-1, 0, 0) + P(0, 1, 0) + P(0, -1, 0) + P(0, 0, 1) + P(0, 0, -1);
             T L, G;
@@ -429,14 +433,26 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
         // for S_{1,0,0}; fluxes whose stencil leaves the ring region are set to
         // zero (no output cell uses them).
         auto owned_fluxes = [&](int r, int buf) {
-            auto aD = [&](int dx, int dy, int dz) -> T { return AL(r + dz, ty + dy, tx + dx).x; };
-            auto aA = [&](int dx, int dy, int dz) -> T { return AL(r + dz, ty + dy, tx + dx).y; };
-            auto bU = [&](int dx, int dy, int dz) -> T { return RG(s_U, 4, r + dz, ty + dy, tx + dx); };
-            auto bP = [&](int dx, int dy, int dz) -> T { return PS(r + dz, ty + 1 + dy, tx + 1 + dx); };
+            // ring-region offsets of the cell in planes r-1 .. r+1 and its
+            // psi-region offsets, formed once (neighbour offsets fold into
+            // the loads' immediates)
+            const int rb[3] = {(((r - 1) & 3) * AY + ty) * AX + tx, ((r & 3) * AY + ty) * AX + tx,
+                               (((r + 1) & 3) * AY + ty) * AX + tx};
+            const int qb[3] = {(((r - 1) & 7) * PY + ty + 1) * PX + tx + 1, ((r & 7) * PY + ty + 1) * PX + tx + 1,
+                               (((r + 1) & 7) * PY + ty + 1) * PX + tx + 1};
+            auto ALr = [&](int dx, int dy, int dz) -> T2& { return PR(s_al, rb[dz + 1] + dy * AX + dx); };
+            auto aD = [&](int dx, int dy, int dz) -> T { return ALr(dx, dy, dz).x; };
+            auto aA = [&](int dx, int dy, int dz) -> T { return ALr(dx, dy, dz).y; };
+            auto bU = [&](int dx, int dy, int dz) -> T {
+                return s_psi[PF_CHK((s_U - s_psi) + rb[dz + 1] + dy * AX + dx, SM_ELEMS)];
+            };
+            auto bP = [&](int dx, int dy, int dz) -> T {
+                return s_psi[PF_CHK(qb[dz + 1] + dy * PX + dx, 8 * PX * PY)];
+            };
             const bool xm = tx >= 1, xp = tx + 1 < AX, ym = ty >= 1, yp = ty + 1 < AY;
             const T u0 = bU(0, 0, 0), p0 = bP(0, 0, 0);
             // (D, A) pairs of alpha (one load) and beta
-            auto A2 = [&](int dx, int dy, int dz) -> P2<T> { return Pair3<T>::get(AL(r + dz, ty + dy, tx + dx)); };
+            auto A2 = [&](int dx, int dy, int dz) -> P2<T> { return Pair3<T>::get(ALr(dx, dy, dz)); };
             auto B2 = [&](int dx, int dy, int dz) -> P2<T> { return p2(bU(dx, dy, dz), bP(dx, dy, dz)); };
             const P2<T> b00 = p2(u0, p0);
             // face toward e: returns (D, A) flux
