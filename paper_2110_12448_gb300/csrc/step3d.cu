@@ -53,8 +53,9 @@ __device__ __forceinline__ T aniso_q3(const T g[3], const T R[9], T eps, T hh, i
 #pragma unroll
     for (int p = 0; p < 3; ++p) c[p] = R[p] * g[0] + R[3 + p] * g[1] + R[6 + p] * g[2];
     const T r2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-    if (r2 * hh < Guard<T>::v) return T(0);
-    const T inv = M3<T>::rcp(r2);
+    // evaluated unconditionally and selected at the end (no divergent branch)
+    const bool guard = r2 * hh < Guard<T>::v;
+    const T inv = M3<T>::rcp(guard ? T(1) : r2);
     T s[3];
 #pragma unroll
     for (int p = 0; p < 3; ++p) s[p] = c[p] * c[p] * inv;
@@ -65,22 +66,22 @@ __device__ __forceinline__ T aniso_q3(const T g[3], const T R[9], T eps, T hh, i
     T out = T(0);
 #pragma unroll
     for (int p = 0; p < 3; ++p) out += R[3 * ax + p] * (c[p] * (c0 + c1 * s[p]));
-    return out;
+    return guard ? T(0) : out;
 }
 template <typename T> __device__ __forceinline__ T aniso_a3(const T g[3], const T R[9], T eps, T hh) {
     T c[3];
 #pragma unroll
     for (int p = 0; p < 3; ++p) c[p] = R[p] * g[0] + R[3 + p] * g[1] + R[6 + p] * g[2];
     const T r2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-    if (r2 * hh < Guard<T>::v) return T(1);
-    const T inv = M3<T>::rcp(r2);
+    const bool guard = r2 * hh < Guard<T>::v;
+    const T inv = M3<T>::rcp(guard ? T(1) : r2);
     T q = T(0);
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
         const T s = c[p] * c[p] * inv;
         q += s * s;
     }
-    return T(1) - T(3) * eps + T(4) * eps * q;
+    return guard ? T(1) : T(1) - T(3) * eps + T(4) * eps * q;
 }
 
 // The D~ fluxes of the D term (alpha = 1 - phi, beta = U) and of the
