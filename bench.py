@@ -58,10 +58,10 @@ def dist_env():
 TRAFFIC = {
     # ncu capture of one k_step2d<float, S-bar_21> launch of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38)
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
-                "sha256": "2c3054b08514666c37bee63e29a1212ad130f7c85e7b23bda1d8a4aeabc6be40", "bytes": 154640640},
+                "sha256": "16ca084cf48cd2c354d98a9f7e4e69a88f164ad104fd4dee28929024b6709c01", "bytes": 154524160},
     # ncu capture of one k_step3d<float, S-bar_120, 30, 14> launch of the 256^3 free dendrite
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
-                   "sha256": "c61f12b619648a147f6a766017b0050881de28269c5f3989897a750f80b1898c", "bytes": 262906368},
+                   "sha256": "32a7a9cc7b4a805bbd83f44faa23e23484268be88d2402b12490dd522e398f84", "bytes": 262227968},
 }
 
 
@@ -75,10 +75,10 @@ TRAFFIC = {
 FLOPS = {
     # k_step2d<float, S-bar_21> launch of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38)
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
-                "sha256": "2c3054b08514666c37bee63e29a1212ad130f7c85e7b23bda1d8a4aeabc6be40", "flop_per_cell": 301.1},
+                "sha256": "16ca084cf48cd2c354d98a9f7e4e69a88f164ad104fd4dee28929024b6709c01", "flop_per_cell": 261.2},
     # k_step3d<float, S-bar_120, 30, 14> launch of the 256^3 free dendrite
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
-                   "sha256": "c61f12b619648a147f6a766017b0050881de28269c5f3989897a750f80b1898c", "flop_per_cell": 1036.8},
+                   "sha256": "32a7a9cc7b4a805bbd83f44faa23e23484268be88d2402b12490dd522e398f84", "flop_per_cell": 1050.4},
 }
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
