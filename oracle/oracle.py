@@ -76,6 +76,8 @@ def lib():
             L.or_appb_grad.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp]
             L.or_dt_max.argtypes = [C.POINTER(Params)]
             L.or_dt_max.restype = C.c_double
+            L.or_set_at21_floor.argtypes = [C.c_int]
+            L.or_set_at21_floor.restype = C.c_int
             L.or_tip_radius.argtypes = [C.POINTER(Params), dp, dp, dp, dp]
             _lib = L
     return _lib
@@ -221,6 +223,13 @@ def appb_grad(field, i, j, kind, h=1.0):
 
 def dt_max(p: Params) -> float:
     return float(lib().or_dt_max(C.byref(p)))
+
+
+def set_at21_floor(on: bool) -> bool:
+    """Turn the magnitude floor of A_{2,1} (reading R-A21G) on or off; returns
+    the previous setting.  Off reproduces App. B's form without the floor, for
+    tests that show why the floor is there."""
+    return bool(lib().or_set_at21_floor(1 if on else 0))
 
 
 def tip_radius(p: Params, psi, tip, axis):

@@ -318,6 +318,15 @@ int or_appb_grad(const double* field, int nx, int ny, int i, int j, int kind, do
  * two-point slope |b_e - b_0| / |e| (a quotient above 2, which occurs only
  * where grad b has no direction, e.g. at a local extremum of psi inside the
  * interface) the magnitude is raised to that half (reading R-A21G). */
+/* The floor of reading R-A21G is on unless a test turns it off (to show
+ * what App. B's form does without it); or_set_at21_floor returns the
+ * previous setting. */
+static int g_at21_floor = 1;
+int or_set_at21_floor(int on) {
+    int old = g_at21_floor;
+    g_at21_floor = on != 0;
+    return old;
+}
 static double at_21(const pad_t* a, const pad_t* b, int i, int j, double h, double guard2) {
     double s10 = 0.0, s11 = 0.0;
     /* <10> fluxes: (dx,dy) and the face whose App. B origin gives that point */
@@ -329,7 +338,7 @@ static double at_21(const pad_t* a, const pad_t* b, int i, int j, double h, doub
             m = gradmag_face_2d(b, dx > 0 ? i : i - 1, j, 0, h);
         else
             m = gradmag_face_2d(b, i, dy > 0 ? j : j - 1, 1, h);
-        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);
+        if (g_at21_floor) m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);
         if (m * m * h * h < guard2) continue;
         s10 += flux_10(a, b, i, j, dx, dy, h) / m;
     }
@@ -337,7 +346,7 @@ static double at_21(const pad_t* a, const pad_t* b, int i, int j, double h, doub
     for (int q = 0; q < 4; ++q) {
         int dx = d11[q][0], dy = d11[q][1];
         double m = gradmag_corner_2d(b, dx > 0 ? i : i - 1, dy > 0 ? j : j - 1, h);
-        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / (SQ2 * h));
+        if (g_at21_floor) m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / (SQ2 * h));
         if (m * m * h * h < guard2) continue;
         s11 += flux_11(a, b, i, j, dx, dy, h) / m;
     }

@@ -93,11 +93,12 @@ MUTATIONS = [
      "Pdphi.v[c] = dt / SQ2 * Pnew.v[c];"),
     ("t0_uses_new_phi", "                Pnew.v[c] = ph; /* phi^n on the left-hand side */",
      "                Pnew.v[c] = tanh((Ppsi.v[c] + dt * Pnew.v[c]) / SQ2);"),
-    ("at21_floor_dropped_face", "        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);\n", ""),
+    ("at21_floor_dropped_face",
+     "        if (g_at21_floor) m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);\n", ""),
     ("at21_floor_dropped_corner",
-     "        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / (SQ2 * h));\n", ""),
-    ("at21_floor_factor", "        m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);",
-     "        m = fmax(m, 2.0 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);"),
+     "        if (g_at21_floor) m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / (SQ2 * h));\n", ""),
+    ("at21_floor_factor", "if (g_at21_floor) m = fmax(m, 0.5 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);",
+     "if (g_at21_floor) m = fmax(m, 2.0 * fabs(V2(b, i + dx, j + dy) - V2(b, i, j)) / h);"),
     ("observe_pulling_axis_as_x", "    if (g == -2) d[1] = 1.0;", "    if (g == -2) d[0] = 1.0;"),
     ("at_std2_no_normalisation", "((V2(b, i + dx, j + dy) - V2(b, i, j)) / h) / sqrt(m2);",
      "((V2(b, i + dx, j + dy) - V2(b, i, j)) / h);"),
