@@ -450,30 +450,14 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
             auto bP = [&](int dx, int dy, int dz) -> T {
                 return s_psi[PF_CHK(qb[dz + 1] + dy * PX + dx, 8 * PX * PY)];
             };
-            const bool xm = tx >= 1, xp = tx + 1 < AX, ym = ty >= 1, yp = ty + 1 < AY;
             const T u0 = bU(0, 0, 0), p0 = bP(0, 0, 0);
             // (D, A) pairs of alpha (one load) and beta
             auto A2 = [&](int dx, int dy, int dz) -> P2<T> { return Pair3<T>::get(ALr(dx, dy, dz)); };
             auto B2 = [&](int dx, int dy, int dz) -> P2<T> { return p2(bU(dx, dy, dz), bP(dx, dy, dz)); };
             const P2<T> b00 = p2(u0, p0);
-            // face toward e: returns (D, A) flux
+            // <100> face toward e (S_{1,0,0}): returns the (D, A) flux
             auto face = [&](const int e[3], T& fD, T& fA) {
-                if (ISO) {
-                    const P2<T> n = A2(0, 0, 0) + A2(e[0], e[1], e[2]);
-                    P2<T> m = bc2<T>(T(0));
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        if (e[q] != 0) continue;
-#pragma unroll
-                        for (int s2 = -1; s2 <= 1; s2 += 2) {
-                            const int t[3] = {q == 0 ? s2 : 0, q == 1 ? s2 : 0, q == 2 ? s2 : 0};
-                            m = m + (A2(t[0], t[1], t[2]) + A2(e[0] + t[0], e[1] + t[1], e[2] + t[2]));
-                        }
-                    }
-                    const P2<T> f = fma2(bc2<T>(T(0.5)), n, bc2<T>(T(1.0 / 8.0)) * m) * (B2(e[0], e[1], e[2]) - b00);
-                    fD = f.d();
-                    fA = f.a();
-                } else {
+                {
                     fD = T(0.5) * (aD(0, 0, 0) + aD(e[0], e[1], e[2])) * (bU(e[0], e[1], e[2]) - u0);
                     T gf[3];
                     int ax = e[0] != 0 ? 0 : (e[1] != 0 ? 1 : 2);
@@ -495,72 +479,68 @@ __global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* 
                                                         (bP(e[0], e[1], e[2]) - p0) * M3<T>::rcp(M3<T>::sqrt_(m2));
                 }
             };
-            // edge toward d = e1 + e2 (e3 the third axis)
-            auto edge = [&](const int e1[3], const int e2[3], int ax3, T& fD, T& fA) {
-                const int d[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
-                const P2<T> n = ((A2(0, 0, 0) + A2(e1[0], e1[1], e1[2])) + A2(e2[0], e2[1], e2[2])) + A2(d[0], d[1], d[2]);
-                P2<T> m = bc2<T>(T(0));
-#pragma unroll
-                for (int s3 = -1; s3 <= 1; s3 += 2) {
-                    int t[3] = {0, 0, 0};
-                    t[ax3] = s3;
-                    m = m + (((A2(t[0], t[1], t[2]) + A2(e1[0] + t[0], e1[1] + t[1], e1[2] + t[2])) +
-                              A2(e2[0] + t[0], e2[1] + t[1], e2[2] + t[2])) +
-                             A2(d[0] + t[0], d[1] + t[1], d[2] + t[2]));
-                }
-                const P2<T> f = fma2(bc2<T>(T(3.0 / 16.0)), n, bc2<T>(T(1.0 / 32.0)) * m) * (B2(d[0], d[1], d[2]) - b00);
-                fD = f.d();
-                fA = f.a();
-            };
-            // Every flux is evaluated unconditionally and zeroed afterwards where
-            // its stencil leaves the ring region, so that the compiler can share
-            // the neighbourhood loads between fluxes; all stores come last.
-            // Out-of-ring neighbours read the adjacent ring slot or array, always
-            // inside the block's shared memory (values discarded).
+            // Every owned flux is evaluated unconditionally, so that the
+            // compiler can share the neighbourhood loads between fluxes.  A
+            // flux whose stencil leaves the ring region reads the adjacent
+            // ring slot or array, always inside the block's shared memory; no
+            // output cell reads such a flux (each flux that flux_sum reads
+            // has its whole stencil inside the ring), so it is stored as it
+            // comes out.
             T oD[NFI + NFZ], oA[NFI + NFZ];
-            bool ok[NFI + NFZ];
-            {
-                const int e[3] = {1, 0, 0};
-                face(e, oD[0], oA[0]);
-                ok[0] = xp && ym && yp;
-            }
-            {
-                const int e[3] = {0, 1, 0};
-                face(e, oD[1], oA[1]);
-                ok[1] = yp && xm && xp;
-            }
-            if (ISO) {
-                const int ex[3] = {1, 0, 0}, eyp[3] = {0, 1, 0}, eym[3] = {0, -1, 0};
-                edge(ex, eyp, 2, oD[2], oA[2]);
-                ok[2] = xp && yp;
-                edge(ex, eym, 2, oD[3], oA[3]);
-                ok[3] = xp && ym;
-            }
-            // toward plane r+1: +z face [, +x+z, -x+z, +y+z, -y+z edges]
-            {
+            if constexpr (ISO) {
+                // D~_{1,2,0} fluxes from shared sums of the 27 (D, A) alpha
+                // pairs around the cell: a face toward e weighs 1/2 the mean
+                // pair (0, e) and 1/8 the eight tangential neighbours of the
+                // pair; an edge toward e1 + e2 weighs 3/16 the four cells of
+                // its square and 1/32 the eight cells beside it along the
+                // third axis.  Column sums along z, y and x (Kz, Jy, Ix) give
+                // the tangential terms of all nine fluxes.
+                auto Kz = [&](int dx, int dy) { return A2(dx, dy, -1) + A2(dx, dy, 1); };
+                auto Jy = [&](int dx, int dz) { return A2(dx, -1, dz) + A2(dx, 1, dz); };
+                auto Ix = [&](int dy, int dz) { return A2(-1, dy, dz) + A2(1, dy, dz); };
+                const P2<T> a0 = A2(0, 0, 0);
+                const P2<T> nX = a0 + A2(1, 0, 0), nY = a0 + A2(0, 1, 0), nZ = a0 + A2(0, 0, 1);
+                const P2<T> k00 = Kz(0, 0), k10 = Kz(1, 0), k01 = Kz(0, 1);
+                const P2<T> j00 = Jy(0, 0), j10 = Jy(1, 0), j01 = Jy(0, 1);
+                const P2<T> i00 = Ix(0, 0), i10 = Ix(1, 0), i01 = Ix(0, 1);
+                const P2<T> kx = k00 + k10, jx = j00 + j10, iy = i00 + i10, jz = j00 + j01;
+                const P2<T> hf = bc2<T>(T(0.5)), ef = bc2<T>(T(1.0 / 8.0));
+                const P2<T> he = bc2<T>(T(3.0 / 16.0)), ee = bc2<T>(T(1.0 / 32.0));
+                auto put = [&](int q, P2<T> n, P2<T> m, P2<T> h, P2<T> e, int dx, int dy, int dz) {
+                    const P2<T> f = fma2(h, n, e * m) * (B2(dx, dy, dz) - b00);
+                    oD[q] = f.d();
+                    oA[q] = f.a();
+                };
+                // in-plane: +x face, +y face, +x+y and +x-y edges
+                put(0, nX, jx + kx, hf, ef, 1, 0, 0);
+                put(1, nY, iy + (k00 + k01), hf, ef, 0, 1, 0);
+                put(2, nX + (A2(0, 1, 0) + A2(1, 1, 0)), kx + (k01 + Kz(1, 1)), he, ee, 1, 1, 0);
+                put(3, nX + (A2(0, -1, 0) + A2(1, -1, 0)), kx + (Kz(0, -1) + Kz(1, -1)), he, ee, 1, -1, 0);
+                // toward plane r+1: +z face, +x+z, -x+z, +y+z, -y+z edges
+                put(NFI, nZ, (i00 + i01) + jz, hf, ef, 0, 0, 1);
+                put(NFI + 1, nX + (A2(0, 0, 1) + A2(1, 0, 1)), jx + (j01 + Jy(1, 1)), he, ee, 1, 0, 1);
+                put(NFI + 2, nZ + (A2(-1, 0, 0) + A2(-1, 0, 1)), (j00 + Jy(-1, 0)) + (j01 + Jy(-1, 1)), he, ee, -1, 0,
+                    1);
+                put(NFI + 3, nY + (A2(0, 0, 1) + A2(0, 1, 1)), iy + (i01 + Ix(1, 1)), he, ee, 0, 1, 1);
+                put(NFI + 4, nZ + (A2(0, -1, 0) + A2(0, -1, 1)), (i00 + Ix(-1, 0)) + (i01 + Ix(-1, 1)), he, ee, 0, -1,
+                    1);
+            } else {
+                {
+                    const int e[3] = {1, 0, 0};
+                    face(e, oD[0], oA[0]);
+                }
+                {
+                    const int e[3] = {0, 1, 0};
+                    face(e, oD[1], oA[1]);
+                }
                 const int e[3] = {0, 0, 1};
                 face(e, oD[NFI], oA[NFI]);
-                ok[NFI] = xm && xp && ym && yp;
-            }
-            if (ISO) {
-                const int ez[3] = {0, 0, 1}, exp_[3] = {1, 0, 0}, exm[3] = {-1, 0, 0}, eyp[3] = {0, 1, 0},
-                          eym[3] = {0, -1, 0};
-                edge(exp_, ez, 1, oD[NFI + 1], oA[NFI + 1]);
-                ok[NFI + 1] = xp && ym && yp;
-                edge(exm, ez, 1, oD[NFI + 2], oA[NFI + 2]);
-                ok[NFI + 2] = xm && ym && yp;
-                edge(eyp, ez, 0, oD[NFI + 3], oA[NFI + 3]);
-                ok[NFI + 3] = yp && xm && xp;
-                edge(eym, ez, 0, oD[NFI + 4], oA[NFI + 4]);
-                ok[NFI + 4] = ym && xm && xp;
             }
 #pragma unroll
-            for (int q = 0; q < NFI; ++q)
-                PR(s_fi, (long long)q * NT + tid) = Pair3<T>::put(ok[q] ? oD[q] : T(0), ok[q] ? oA[q] : T(0));
+            for (int q = 0; q < NFI; ++q) PR(s_fi, (long long)q * NT + tid) = Pair3<T>::put(oD[q], oA[q]);
 #pragma unroll
             for (int q = 0; q < NFZ; ++q)
-                PR(s_fz, (long long)(buf * NFZ + q) * NT + tid) =
-                    Pair3<T>::put(ok[NFI + q] ? oD[NFI + q] : T(0), ok[NFI + q] ? oA[NFI + q] : T(0));
+                PR(s_fz, (long long)(buf * NFZ + q) * NT + tid) = Pair3<T>::put(oD[NFI + q], oA[NFI + q]);
         };
         // eight/eighteen-flux sums of an output cell at plane r: own fluxes
         // plus the negated owned fluxes of the neighbours that share them
