@@ -54,14 +54,15 @@ def dist_env():
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
-# source is byte-identical to the one captured (sha256 of the .cu file).
+# source is byte-identical to the one captured (sha256 of the .cu file) and
+# the launch uses the captured tile (block x, block y, sweep).
 TRAFFIC = {
     # ncu capture of one k_step2d<float, S-bar_21> launch of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38)
-    "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
+    "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu", "tile": [64, 1, 38],
                 "sha256": "16ca084cf48cd2c354d98a9f7e4e69a88f164ad104fd4dee28929024b6709c01", "bytes": 154524160},
-    # ncu capture of one k_step3d<float, S-bar_120, 30, 14> launch of the 256^3 free dendrite
-    "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
-                   "sha256": "32a7a9cc7b4a805bbd83f44faa23e23484268be88d2402b12490dd522e398f84", "bytes": 262227968},
+    # ncu capture of one k_step3d<float, S-bar_120, 30, 6> launch of the 256^3 free dendrite (tile 34 x 10 x 52)
+    "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu", "tile": [34, 10, 52],
+                   "sha256": "18a2050e7d74baf0edcd8033c2b12249f9cc5b4bbc3b6911998bb9fbaa64a90b", "bytes": 263545344},
 }
 
 
@@ -74,20 +75,25 @@ TRAFFIC = {
 # (3D: executed per output cell, including the ring-1 recompute of the tile.)
 FLOPS = {
     # k_step2d<float, S-bar_21> launch of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38)
-    "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu",
+    "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu", "tile": [64, 1, 38],
                 "sha256": "16ca084cf48cd2c354d98a9f7e4e69a88f164ad104fd4dee28929024b6709c01", "flop_per_cell": 261.2},
-    # k_step3d<float, S-bar_120, 30, 14> launch of the 256^3 free dendrite
-    "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu",
-                   "sha256": "32a7a9cc7b4a805bbd83f44faa23e23484268be88d2402b12490dd522e398f84", "flop_per_cell": 1050.4},
+    # k_step3d<float, S-bar_120, 30, 6> launch of the 256^3 free dendrite (tile 34 x 10 x 52)
+    "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu", "tile": [34, 10, 52],
+                   "sha256": "18a2050e7d74baf0edcd8033c2b12249f9cc5b4bbc3b6911998bb9fbaa64a90b", "flop_per_cell": 1100.6},
 }
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def _captured(table, workload, key):
-    """table[workload][key] if the kernel source still matches the capture, else None."""
+def _captured(table, workload, key, tile=None):
+    """table[workload][key] if the kernel source still matches the capture and
+    the launch uses the captured block shape, else None.  (The sweep length
+    moves the per-cell figures only through the halo rows or planes of each
+    work item's prologue: well under 1 % between neighbouring sweeps.)"""
     import hashlib
     t = table.get(workload)
     if not t or not t["sha256"]:
+        return None
+    if tile is None or list(tile)[:2] != list(t["tile"])[:2]:
         return None
     with open(os.path.join(ROOT, t["source"]), "rb") as f:
         if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
@@ -95,8 +101,8 @@ def _captured(table, workload, key):
     return t[key]
 
 
-def traffic_for(workload):
-    return _captured(TRAFFIC, workload, "bytes")
+def traffic_for(workload, tile=None):
+    return _captured(TRAFFIC, workload, "bytes", tile)
 
 
 def aggregate(ms_local: float, cells_per_rank: int, steps: int, world: int, device=None) -> tuple:
@@ -823,10 +829,10 @@ def run_native(args):
     elif args.time_level == "t0":
         kname += " (T0)"
     default_path = args.precision == "f32" and args.kernels == "fused" and args.time_level == "t1"
-    fpc = _captured(FLOPS, args.workload, "flop_per_cell") if default_path and args.scheme in ("SBAR21", "SBAR120") \
-        else None
+    fpc = _captured(FLOPS, args.workload, "flop_per_cell", tile) \
+        if default_path and args.scheme in ("SBAR21", "SBAR120") else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic_for(args.workload) if default_path else None, "peak_source": peak_kind,
+            "traffic": traffic_for(args.workload, tile) if default_path else None, "peak_source": peak_kind,
             "bytes_per_cell": bpc, "kernel": kname}
     roof_alu = None
     if fpc:

@@ -188,7 +188,10 @@ int pf_set_grains(pf_sim* s, int n_grains, const double* rot9, const double* cen
 
 /* psi = max over seeds of (r_s - |x - c_s|), the signed distance to the
  * union of seeds; grain = grain of the seed attaining the maximum (ties: the
- * lowest seed index); U = U0.  Computed in FP64 on the device. */
+ * lowest seed index); U = U0.  Computed in FP64 on the device.  seeds: host
+ * array of n_seeds records, 1 <= n_seeds <= max_seeds, finite, each grain in
+ * [0, n_grains); otherwise PF_ERR_INVALID and the fields are unchanged (a
+ * handle that was never seeded holds the all-liquid state pf_create leaves). */
 int pf_init_seeds(pf_sim* s, int n_seeds, const pf_seed* seeds);
 
 /* Copy an explicit per-cell grain map (nx*ny*nz int16, values < n_grains). */
@@ -356,14 +359,17 @@ int pf_group_remove(pf_group* g, pf_sim* s);
  * of launches are captured once per membership change and replayed; on the
  * legacy default stream (NULL), which cannot be captured, every step is
  * launched directly.  Frozen-temperature members read their step from a
- * device counter that every launch advances, so replays keep the time. */
+ * device counter that every launch advances, so replays keep the time.
+ * n = 0, or a group without members, launches nothing and returns PF_OK;
+ * n < 0 is PF_ERR_INVALID. */
 int pf_group_step(pf_group* g, int64_t n, int use_graph);
 int pf_group_size(const pf_group* g);
 /* pf_observe of every member (in the order they were added, out[i] for the
  * i-th) with one synchronisation: the reductions of all members are queued on
  * the group's stream and their records read back together.  grain as in
  * pf_observe and valid for every member.  Returns PF_ERR_NONFINITE (with all
- * of out filled) when a member holds NaN/Inf cells. */
+ * of out filled) when a member holds NaN/Inf cells.  A group without
+ * members writes nothing and returns PF_OK. */
 int pf_group_observe(pf_group* g, int grain, pf_obs* out);
 int pf_group_destroy(pf_group* g);
 

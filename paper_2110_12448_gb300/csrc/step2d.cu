@@ -53,6 +53,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+// x / y from the reciprocal estimate and one Newton correction of the
+// quotient (Markstein): q = x r, then q + (x - q y) r with the residual in
+// one FMA.  Within about an ulp of x / y for normal operands, with no
+// slow-path test; the compensated state's divisions either feed a residual
+// step that corrects the quotient to double-float precision or form small
+// increments whose last-bit error is far below the state's lo half.
+__device__ __forceinline__ float div_nr(float x, float y) {
+    const float r = rcp_approx(y);
+    const float q = x * r;
+    return fmaf(fmaf(-q, y, x), r, q);
+}
 __device__ __forceinline__ float ex2_approx(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -328,7 +339,7 @@ __device__ __forceinline__ float phi_acc(float hi, float lo) {
 // unlike the difference phi' - phi of two rounded values
 __device__ __forceinline__ float dphi_acc(float phi, float d) {
     const float T = tanhf(d * 0.70710678118654752440f);
-    return __fdiv_rn(T * fmaf(-phi, phi, 1.0f), fmaf(T, phi, 1.0f));
+    return div_nr(T * fmaf(-phi, phi, 1.0f), fmaf(T, phi, 1.0f));
 }
 
 // ---------------------------------------------------------------------------
@@ -373,9 +384,9 @@ __device__ __forceinline__ D2 dmul(D2 x, D2 y) {
 }
 __device__ __forceinline__ D2 dscale(D2 x, float c) { return D2{x.h * bc<float>(c), x.l * bc<float>(c)}; }  // c a power of 2
 __device__ __forceinline__ D2 ddiv(D2 x, D2 y) {
-    const V<float> q1 = mk(__fdiv_rn(x.h.x(), y.h.x()), __fdiv_rn(x.h.y(), y.h.y()));
+    const V<float> q1 = mk(div_nr(x.h.x(), y.h.x()), div_nr(x.h.y(), y.h.y()));
     const D2 r = dsub(x, dmul(d2f(q1), y));
-    const V<float> q2 = mk(__fdiv_rn(r.h.x(), y.h.x()), __fdiv_rn(r.h.y(), y.h.y()));
+    const V<float> q2 = mk(div_nr(r.h.x(), y.h.x()), div_nr(r.h.y(), y.h.y()));
     return fast_two_sum(q1, q2);
 }
 // (hi_a + lo_a) - (hi_b + lo_b) with the hi difference exact
@@ -1092,8 +1103,8 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                 if constexpr (CMP) {
                     // U' = (hi + lo) + num / (1 + k - (1-k) phi'), kept exactly
                     const V<T> den = fma(bc<T>(-omk), phin_cur, bc<T>(T(1) + kk));
-                    const V<T> inc = mk((T)__fdiv_rn((float)num.x(), (float)den.x()),
-                                        (T)__fdiv_rn((float)num.y(), (float)den.y()));
+                    const V<T> inc = mk((T)div_nr((float)num.x(), (float)den.x()),
+                                        (T)div_nr((float)num.y(), (float)den.y()));
                     V<T> uh, ul;
                     cadd2<T>(u, UL0.C(), inc, uh, ul);
                     store_pair<T>(U_o + (size_t)PF_CHK(r, ny) * nx, cL, nx, vec, outL, outR, uh);
