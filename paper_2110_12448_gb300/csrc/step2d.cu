@@ -688,7 +688,8 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
 
         auto phase1 = [&](int p, const Row<T>& Pm, const Row<T>& P0, const Row<T>& Pp, const Row<T>& ph0,
                           const Row<T>& u0, int gL, int gR, const Row<T>& Lm, const Row<T>& L0, const Row<T>& Lp,
-                          V<T> ulo0, V<T>& psin, V<T>& psin_lo, V<T>& phin, V<T>& dph, V<T>& rate_o) {
+                          V<T> ulo0, V<T>& psin, V<T>& psin_lo, V<T>& phin, V<T>& dph, V<T>& rate_o,
+                          V<T>& phc) {
             if constexpr (MODE == 2) {
                 // U pass of the two-kernel form: d psi/dt^n from the psi pass,
                 // T0 increment dt (1 - phi^2)/sqrt2 d psi/dt, phi^n on the left
@@ -698,6 +699,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                 rate_o = mk(ra, rb);
                 dph = bc<T>(dt * T(0.70710678118654752440)) * (bc<T>(T(1)) - ph * ph) * rate_o;
                 phin = ph;
+                phc = ph;
                 psin = psin_lo = bc<T>(T(0));
                 return;
             }
@@ -809,12 +811,14 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                 dph = mk((T)dphi_acc((float)phh.x(), (float)d.h.x()), (T)dphi_acc((float)phh.y(), (float)d.h.y()));
                 phin = phh + dph;
                 rate_o = rate.h;
+                phc = phh;  // phi^n of the own columns, rounded once from double-float
                 return;
             }
             const V<T> src = bc<T>(SQ2) * (ph - bc<T>(lam) * (bc<T>(T(1)) - ph * ph) * u);
             V<T> rate = (L + N + src) * rcp2(ac * ac) - bc<T>(SQ2) * ph * G;
             if (DS) rate = rate * bc<T>(iF1);
             rate_o = rate;
+            phc = ph;
             psin = fma(bc<T>(dt), rate, C0);
             psin_lo = L0.C();
             if constexpr (sizeof(T) == 8) {
@@ -1006,14 +1010,16 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             // phase 1 at rows y0-1 and y0; the ghost row -1 copies row 0 (the
             // psi pass of the two-kernel form needs no row y0-1: no U fluxes)
             int gL, gR;
-            V<T> psn, psnl, fn, dm = bc<T>(T(0)), d0, rt;
+            V<T> psn, psnl, fn, dm = bc<T>(T(0)), d0, rt, phc_unused;
             const bool ghost = (y0 - 1) < 0;
             if (!ghost && MODE != 1) {
                 load_grain_pair(grain + (size_t)PF_CHK((y0 - 1), ny) * nx, cL, nx, vec, per, gL, gR);
-                phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, lq[0], lq[1], lq[2], ulm.C(), psn, psnl, fn, dm, rt);
+                phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, lq[0], lq[1], lq[2], ulm.C(), psn, psnl, fn, dm, rt,
+                       phc_unused);
             }
             load_grain_pair(grain + (size_t)PF_CHK(y0, ny) * nx, cL, nx, vec, per, gL, gR);
-            phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, lq[1], lq[2], lq[3], ul0.C(), psn, psnl, fn, d0, rt);
+            phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, lq[1], lq[2], lq[3], ul0.C(), psn, psnl, fn, d0, rt,
+                   phc_unused);
             if (ghost) dm = d0;
             phin_cur = fn;
             if (y0 < y1) psi_store(y0, psn, psnl, rt);
@@ -1057,7 +1063,9 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                 LP[2] = make_row(nPLa, nPLb, false);
                 UL1 = make_row(nULa, nULb, false);
             }
-            PH1 = CMP ? phi_row_c(P[3], LP[1].C()) : phi_row(P[3]);
+            // phi of row r+1 (the compensated state takes it from phase 1,
+            // which forms it in double-float, below)
+            if constexpr (!CMP) PH1 = phi_row(P[3]);
             const int gL = nGa, gR = nGb;
             fetch_row(psi, r + 3, nPa, nPb);
             fetch_row(Uf, r + 2, nUa, nUb);
@@ -1072,12 +1080,20 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             V<T> phn = bc<T>(T(0));
             Row<T> DP1;
             if (r + 1 < ny && (MODE != 1 || r + 1 < y1)) {
-                V<T> psn, psnl, d, rt;
+                V<T> psn, psnl, d, rt, phc;
                 phase1(r + 1, P[2], P[3], P[4], PH1, UU1, gL, gR, LP[0], LP[1], LP[2], UL1.C(), psn, psnl, phn, d,
-                       rt);
+                       rt, phc);
                 if (r + 1 < y1) psi_store(r + 1, psn, psnl, rt);
                 DP1 = dphi_row(d);
+                if constexpr (CMP) {
+                    PH1.l = phc.x();
+                    PH1.r = phc.y();
+                    PH1.m1 = shup(PH1.r);
+                    PH1.p1 = shdn(PH1.l);
+                    PH1.m2 = PH1.p2 = T(0);
+                }
             } else {
+                if constexpr (CMP) PH1 = phi_row_c(P[3], LP[1].C());
                 DP1 = DP0;  // ghost row ny mirrors row ny-1 = r
             }
             if constexpr (MODE == 1) {

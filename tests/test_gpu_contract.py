@@ -25,7 +25,7 @@ FP32 fields misses 1e-4 on this workload.
     White noise of 3e-9 per step on psi alone already ends 2.4e-4 away in the
     oracle (the error grows linearly with the noise), so the psi rate is
     evaluated in double-float (FP32 pairs) and the O(eps4) face terms without
-    cancellation: its per-step error is ~1e-9 (measured 3e-5 / 2e-5).
+    cancellation: its per-step error is ~1e-9 (measured 3.7e-5 / 3.1e-5).
 """
 import json
 import math
