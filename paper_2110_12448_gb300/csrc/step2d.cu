@@ -501,9 +501,13 @@ __device__ __forceinline__ void store_pair(T* __restrict__ row, int c, int nx, b
 #ifndef PF_STEP2D_MIN_BLOCKS_F32
 #define PF_STEP2D_MIN_BLOCKS_F32 16
 #endif
-// the compensated kernel holds the lo rows as well: a 255-register cap
+// The compensated kernel holds the lo rows as well.  Capped at 168 registers
+// (eleven blocks asked for, twelve resident warps per SM) it spills ~100 bytes
+// of rarely used values and runs 13 % faster than uncapped at 246 registers
+// (eight warps): its dependency chains need the extra warps more than the
+// registers.
 #ifndef PF_STEP2D_MIN_BLOCKS_F32C
-#define PF_STEP2D_MIN_BLOCKS_F32C 8
+#define PF_STEP2D_MIN_BLOCKS_F32C 11
 #endif
 
 // DS = false: isothermal instances with mirror walls (the flags below are
