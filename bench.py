@@ -59,7 +59,7 @@ def dist_env():
 TRAFFIC = {
     # ncu capture of one k_step2d<float, S-bar_21> launch of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38)
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu", "tile": [64, 1, 38],
-                "sha256": "3c17694a2af1894e8cb83345e6e8dc1414080de52cf9d159fa1a1adffa6531eb", "bytes": 154500864},
+                "sha256": "1877ca685d040170505fea49fc6bc08f5bc8a916fe6c6ba9f2ebaf9a38d50b1d", "bytes": 154543104},
     # ncu capture of one k_step3d<float, S-bar_120, 30, 6> launch of the 256^3 free dendrite (tile 34 x 10 x 52)
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu", "tile": [34, 10, 52],
                    "sha256": "18a2050e7d74baf0edcd8033c2b12249f9cc5b4bbc3b6911998bb9fbaa64a90b", "bytes": 263545344},
@@ -76,7 +76,7 @@ TRAFFIC = {
 FLOPS = {
     # k_step2d<float, S-bar_21> launch of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38)
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu", "tile": [64, 1, 38],
-                "sha256": "3c17694a2af1894e8cb83345e6e8dc1414080de52cf9d159fa1a1adffa6531eb", "flop_per_cell": 261.2},
+                "sha256": "1877ca685d040170505fea49fc6bc08f5bc8a916fe6c6ba9f2ebaf9a38d50b1d", "flop_per_cell": 261.2},
     # k_step3d<float, S-bar_120, 30, 6> launch of the 256^3 free dendrite (tile 34 x 10 x 52)
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu", "tile": [34, 10, 52],
                    "sha256": "18a2050e7d74baf0edcd8033c2b12249f9cc5b4bbc3b6911998bb9fbaa64a90b", "flop_per_cell": 1100.6},
