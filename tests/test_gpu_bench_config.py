@@ -15,7 +15,8 @@ same tile in a ten-instance FP64 group on smaller random states and grains,
 wave-aligned odd sweep) one step against the oracle in FP64 (1e-12) and FP32
 (the one-step bounds 2e-6 on phi, 5e-6 on U) on a grid spanning several
 tiles with ragged edges; and the 256^3 free dendrite at its full size with
-the autotuned tile (34, 18, 32), one FP32 step from its state after 40 steps.
+the autotuner's two tied tiles (34, 18, 32) and (34, 10, 52), one FP32 step from
+its state after 40 steps.
 """
 import math
 
@@ -163,10 +164,11 @@ def test_autotuner_tiles_3d_fp32(native, scheme, tile):
     assert max_abs(gu, ou) < 5e-6
 
 
-def test_dendrite_256_cube_bench_tile_fp32(native):
+@pytest.mark.parametrize("tile", [(34, 18, 32), (34, 10, 52)])
+def test_dendrite_256_cube_bench_tile_fp32(native, tile):
     w = synth.free_dendrite_3d(256, scheme="SBAR120")
     s = native.Sim.from_workload(w, "f32")
-    s.set_tile(34, 18, 32)
+    s.set_tile(*tile)
     s.step(40)
     p0, u0 = s.get_fields()
     s.step(1)
