@@ -199,8 +199,13 @@ template <typename T, int S, int TX, int TY> struct Tile3 {
         sizeof(T) * (8 * PX * PY + 8 * NT + 4 * NT + 4 * NT + 2 * 4 * NT + 2 * NFI * NT + 2 * 2 * NFZ * NT);
 };
 
+// Resident blocks per SM asked of the FP32 kernels on the 30 x 6 tile: two
+// for S-bar_{1,2,0} (128 registers), three for S_{1,0,0} (80 registers, 20 B
+// spilled).  Independent blocks keep their barrier phases apart, which pays
+// for the tile's larger ring recompute; three S_{1,0,0} blocks run 7 % faster
+// than two, while S-bar_{1,2,0} spills too much at 80 registers.
 template <typename T, int S, int TX, int TY>
-__global__ void __launch_bounds__((TX + 2) * (TY + 2)) k_step3d(const WorkItem* __restrict__ work, int n_work,
+__global__ void __launch_bounds__((TX + 2) * (TY + 2), (sizeof(T) == 4 && TY == 6) ? (S == S100 ? 3 : 2) : 1) k_step3d(const WorkItem* __restrict__ work, int n_work,
                                                               const InstRec* __restrict__ recs, int launch_parity,
                                                               StepClock clk) {
     using TL = Tile3<T, S, TX, TY>;
