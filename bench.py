@@ -189,7 +189,10 @@ class Clocks:
             util = [float(r[9]) for r in (x.split(",") for x in sampled)
                     if len(r) > 9 and r[9].strip().replace(".", "", 1).isdigit()]
             return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
-                    "gpu_util_pct_median": statistics.median(util) if util else None,
+                    # NVML's utilisation is an average over its own sampling period: a
+                    # median of a handful of samples around a sub-second timed region
+                    # says nothing, so it is reported from five samples up
+                    "gpu_util_pct_median": statistics.median(util) if len(util) >= 5 else None,
                     "samples": len(sampled), "edge_samples": len(self.edges),
                     "edge_sm_mhz": [float(r.split(",")[1]) for r in self.edges],
                     "window": f"200 ms sampler over {self.window}, plus one sample right before and one right "
