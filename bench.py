@@ -264,36 +264,31 @@ def cpu_baseline_1thread(n, scheme, steps=2):
     return {"value": v, "unit": "GLUPS", "cores": 1, "sample": f"{steps} steps of the same instance, one thread"}
 
 
-def at_stated_error(stream, ws, steps):
+def at_stated_error(stream, ws, steps, n_streams=2):
     """The same batch on the compensated FP32 state (PF_F32C), the precision
     that meets the accuracy contract: max |d phi|, |d U| <= 1e-4 against the
     FP64 oracle after 10^4 steps of the 200^2 free dendrite, tip speed within
     0.5 % (checked by tests/test_gpu_contract.py, not here).  Autotuned tile,
-    persistent launch replayed from CUDA graphs, device time of `steps` steps
-    after a warm-up; no observe inside the timed region."""
+    persistent launches replayed from CUDA graphs, the batch as `n_streams`
+    groups on their own streams like the main measurement, device time of
+    `steps` steps after a warm-up; no observe inside the timed region."""
     import torch
 
     from paper_2110_12448_gb300 import autotune
     from paper_2110_12448_gb300 import native as N
+    from paper_2110_12448_gb300.batch import Batch
     tile, _ = autotune.tune(ws, "f32c")
-    sims = [N.Sim.from_workload(w, "f32c", stream=stream) for w in ws]
-    for s in sims:
-        s.set_tile(*tile)
-    g = N.Group(len(sims), sum(N.Group.work_items(s) for s in sims), stream=stream)
-    for s in sims:
-        g.add(s)
-    g.step(32)
+    batch = Batch(ws, "f32c", n_streams=n_streams, tile=tile)
+    batch.step(32, stream=stream)
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    g.step(steps)
+    batch.step(steps, stream=stream)
     b.record(stream)
     b.synchronize()
     ms = a.elapsed_time(b)
-    cells = sum(w.n_cells for w in ws)
-    g.close()
-    for s in sims:
-        s.close()
+    cells = batch.n_cells
+    batch.close()
     return {"value": cells * steps / (ms / 1e3) / 1e9, "unit": "GLUPS", "precision": "f32c",
             "ms_per_step": ms / steps, "steps": steps, "tile": list(tile),
             "contract": "max |d phi|, |d U| <= 1e-4 vs the FP64 oracle after 10^4 steps of the 200^2 free dendrite, "
@@ -769,35 +764,32 @@ def run_native(args):
     if not args.no_tune:
         from paper_2110_12448_gb300 import autotune
         tile, _ = autotune.tune(ws, args.precision)
-    sims = []
-    with torch.cuda.stream(stream):
-        for w in ws:
-            sims.append(N.Sim.from_workload(w, args.precision, stream=stream))
-            if tile:
-                sims[-1].set_tile(*tile)
-    max_work = sum(N.Group.work_items(s) for s in sims)
-    group = N.Group(len(sims), max_work, stream=stream)
-    for s in sims:
-        group.add(s)
-    cells = sum(s.n_cells for s in sims)
+    # the batch as `args.streams` groups on their own streams (forked from and
+    # joined to `stream` around every run of steps): one group's launches fill
+    # the tail of the other's persistent launch
+    from paper_2110_12448_gb300.batch import Batch
+    batch = Batch(ws, args.precision, n_streams=args.streams, tile=tile)
+    sims = batch.members
+    cells = batch.n_cells
     observes = [0]
 
     def steps(k):
         """k steps with the FP64 observe of every instance every OBS_EVERY
-        steps and after the last one; returns kernel-only event pairs."""
+        steps and after the last one; returns event pairs around the step
+        launches alone (fork to join), without the observes."""
         done = 0
         pairs = []
         while done < k:
-            chunk = min(OBS_EVERY - (sims[0].steps_done % OBS_EVERY), k - done)
+            chunk = min(OBS_EVERY - (batch.steps_done % OBS_EVERY), k - done)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            group.step(chunk, use_graph=True)
+            batch.step(chunk, use_graph=True, stream=stream)
             b.record(stream)
             pairs.append((a, b, chunk))
             done += chunk
-            if sims[0].steps_done % OBS_EVERY == 0 or done == k:
-                group.observe(0)  # every instance, one synchronisation
+            if batch.steps_done % OBS_EVERY == 0 or done == k:
+                batch.observe(0)  # every instance, one synchronisation per group
                 observes[0] += 1
         return pairs
 
@@ -831,7 +823,7 @@ def run_native(args):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        group.step(1, use_graph=False)
+        batch.step(1, use_graph=False, stream=stream)
         b.record(stream)
         lat.append((a, b))
     torch.cuda.synchronize()
@@ -877,7 +869,8 @@ def run_native(args):
         if default_path and args.scheme in ("SBAR21", "SBAR120") else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic_for(args.workload, tile) if default_path else None, "peak_source": peak_kind,
-            "bytes_per_cell": bpc, "kernel": kname}
+            "bytes_per_cell": bpc, "kernel": kname,
+            "timing": "step launches of the whole batch, fork to join of its group streams, observes excluded"}
     roof_alu = None
     if fpc:
         tf = cells * fpc / (kern_ms / n_launch / 1e3) / 1e12
@@ -965,7 +958,8 @@ def run_native(args):
                                        (", T0 time level" if args.time_level == "t0" or args.kernels == "two" else "") +
                                        (", two-kernel form (psi kernel stores d psi/dt, then the U kernel)"
                                         if args.kernels == "two" else "") +
-                                       f", {args.precision.upper()} fields, batched persistent launch + CUDA graph, "
+                                       f", {args.precision.upper()} fields, batched persistent launches + CUDA graphs as "
+                                       f"{len(batch.groups)} group(s) on their own streams, "
                                        f"FP64 observe of every instance every {OBS_EVERY} steps and after the last "
                                        f"timed step ({n_observe} inside the timed region)",
                            "cells_per_gpu": cells,
@@ -977,19 +971,19 @@ def run_native(args):
                                         "over": f"{len(per_step)} single steps of the whole batch after the timed "
                                                 f"region, each launched directly with its own events"},
                 "tile": list(tile) if tile else None,
-                "gpu_launches": n_launch + 2 * len(sims) * n_observe}
+                "gpu_launches": (n_launch + 2 * n_observe) * len(batch.groups)}
         if sweep:
             line["directional" if args.workload == "directional2d" else "tip_radius_call"] = sweep
         if world == 1 and not args.no_fp64:
             line["fp64_plain"] = fp64_plain(stream)
         if world == 1 and args.workload == "sweep2d" and args.precision == "f32" and not args.no_fp64:
-            line["at_stated_error"] = at_stated_error(stream, ws, max(200, args.steps))
+            line["at_stated_error"] = at_stated_error(stream, ws, max(200, args.steps), args.streams)
         if world == 1 and not args.no_physics and args.workload == "sweep2d":
             line["orientation_physics"] = orientation_physics(stream, args.n, PHYS_STEPS)
         if world == 1 and not args.no_cpu and args.workload == "sweep2d":
             line["cpu_baseline"] = cpu_baseline(args.n, args.scheme)
         print(json.dumps(line), flush=True)
-    group.close()
+    batch.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -1004,6 +998,8 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f32c"],
                     help="f32c: FP32 arithmetic on the compensated (hi + lo) state, 2D")
     ap.add_argument("--time-level", default="t1", choices=["t1", "t0"])
+    ap.add_argument("--streams", type=int, default=2,
+                    help="groups the batch is split into, each on its own CUDA stream (fewer for fewer instances)")
     ap.add_argument("--kernels", default="fused", choices=["fused", "two"],
                     help="two: the psi kernel stores d psi/dt, then the U kernel (2D, T0)")
     ap.add_argument("--scheme", default="SBAR21", choices=["SBAR21", "S21", "S10", "SBAR120", "S100"])
