@@ -277,7 +277,7 @@ def at_stated_error(stream, ws, steps, n_streams=2):
     from paper_2110_12448_gb300 import autotune
     from paper_2110_12448_gb300 import native as N
     from paper_2110_12448_gb300.batch import Batch
-    tile, _ = autotune.tune(ws, "f32c")
+    tile, _ = autotune.tune(ws, "f32c", n_streams=n_streams)
     batch = Batch(ws, "f32c", n_streams=n_streams, tile=tile)
     batch.step(32, stream=stream)
     a = torch.cuda.Event(enable_timing=True)
@@ -763,7 +763,7 @@ def run_native(args):
     tile = None
     if not args.no_tune:
         from paper_2110_12448_gb300 import autotune
-        tile, _ = autotune.tune(ws, args.precision)
+        tile, _ = autotune.tune(ws, args.precision, n_streams=args.streams)
     # the batch as `args.streams` groups on their own streams (forked from and
     # joined to `stream` around every run of steps): one group's launches fill
     # the tail of the other's persistent launch

@@ -50,10 +50,11 @@ def wave_aligned(workloads, bx, by, resident, max_waves=8, min_sweep=8):
     return out
 
 
-def _key(device_name, w, precision, count):
+def _key(device_name, w, precision, count, n_streams=1):
     ds = "|ds" if getattr(w, "thermal", 0) or getattr(w, "bc_x", 0) else ""  # the directional kernel variant
     ds += "|t0" if getattr(w, "time_level", 0) else ""
     ds += "|two" if getattr(w, "kernels", 0) else ""
+    ds += f"|s{n_streams}" if n_streams > 1 else ""
     return f"{device_name}|{w.dim}|{w.scheme}|{precision}|{w.nx}x{w.ny}x{w.nz}|n{count}{ds}"
 
 
@@ -73,21 +74,26 @@ def _store(d):
     os.replace(tmp, _CACHE)
 
 
-def tune(workloads, precision="f32", steps=24, repeats=2, use_cache=True, verbose=False):
+def tune(workloads, precision="f32", steps=24, repeats=2, use_cache=True, verbose=False, n_streams=1):
     """Best (block_x, block_y, sweep) for a batch shaped like `workloads`
-    (all of one class).  Returns (tile, {tile: seconds per step})."""
+    (all of one class), timed under the schedule it will run with: the batch
+    as `n_streams` groups on their own streams (batch.Batch), one group when
+    1.  Returns (tile, {tile: seconds per step})."""
     import torch
 
     from . import native as N
     w0 = workloads[0]
+    n_streams = max(1, min(int(n_streams), len(workloads)))
     dev = torch.cuda.get_device_name()
-    key = _key(dev, w0, precision, len(workloads))
+    key = _key(dev, w0, precision, len(workloads), n_streams)
     with _lock:
         cache = _load() if use_cache else {}
     if key in cache:
         return tuple(cache[key]["tile"]), cache[key]["times"]
-    stream = torch.cuda.Stream()
-    sims = [N.Sim.from_workload(w, precision, stream=stream) for w in workloads]
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
+    # members of part k run on stream k (round-robin, as batch.Batch splits)
+    part_of = [i % n_streams for i in range(len(workloads))]
+    sims = [N.Sim.from_workload(w, precision, stream=streams[k]) for w, k in zip(workloads, part_of)]
     cands = list(CANDIDATES_2D if w0.dim == 2 else CANDIDATES_3D)
     for bx, by in sorted({(t[0], t[1]) for t in cands}):
         try:
@@ -104,20 +110,33 @@ def tune(workloads, precision="f32", steps=24, repeats=2, use_cache=True, verbos
                 s.set_tile(*tile)
         except N.PfError:
             continue
-        g = N.Group(len(sims), sum(N.Group.work_items(s) for s in sims), stream=stream)
-        for s in sims:
-            g.add(s)
-        g.step(4, use_graph=False)
+        groups = []
+        for k, st in enumerate(streams):
+            mine = [s for s, p in zip(sims, part_of) if p == k]
+            g = N.Group(len(mine), sum(N.Group.work_items(s) for s in mine), stream=st)
+            for s in mine:
+                g.add(s)
+            g.step(4, use_graph=False)
+            groups.append(g)
+        main = torch.cuda.current_stream()
         best = float("inf")
         for _ in range(repeats):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            g.step(steps, use_graph=True)
-            b.record(stream)
+            a.record(main)
+            for st in streams:
+                st.wait_event(a)
+            for g in groups:
+                g.step(steps, use_graph=True)
+            for st in streams:
+                j = torch.cuda.Event()
+                j.record(st)
+                main.wait_event(j)
+            b.record(main)
             b.synchronize()
             best = min(best, a.elapsed_time(b) / 1e3 / steps)
-        g.close()
+        for g in groups:
+            g.close()
         times[str(tile)] = best
         if verbose:
             print(f"autotune {key} {tile}: {best * 1e3:.3f} ms/step", flush=True)

@@ -55,3 +55,15 @@ def test_batch_equals_one_group(native, n_streams):
     b.close()
     for s in sims:
         s.close()
+
+
+def test_autotune_under_two_streams(native):
+    from paper_2110_12448_gb300 import autotune
+    from paper_2110_12448_gb300.batch import Batch
+    ws = [synth.free_dendrite_2d(160, theta_deg=t) for t in (0.0, 15.0, 30.0)]
+    tile, times = autotune.tune(ws, "f32", steps=4, repeats=1, use_cache=False, n_streams=2)
+    assert str(tuple(tile)) in times and all(t > 0 for t in times.values())
+    b = Batch(ws, "f32", n_streams=2, tile=tile)
+    b.step(5)
+    assert b.steps_done == 5 and all(o["nonfinite"] == 0 for o in b.observe(0))
+    b.close()
