@@ -113,10 +113,14 @@ def percentile(xs, q):
 
 
 class Server:
-    """Drives the batched C-ABI path for a stream of requests."""
+    """Drives the batched C-ABI path for a stream of requests.  The running
+    requests are spread over `n_streams` groups, each on its own CUDA stream
+    (a request joins the group with the fewest cells), so that one group's
+    launches overlap another's: the 2D and 3D classes, and the tails of each
+    group's persistent launches."""
 
     def __init__(self, budget_frac: float = 0.8, max_running: int = 256, chunk: int = 100, use_graph: bool = True,
-                 device: int = 0, budget_bytes: Optional[int] = None):
+                 device: int = 0, budget_bytes: Optional[int] = None, n_streams: int = 2):
         import torch
 
         from . import native as N
@@ -125,13 +129,16 @@ class Server:
         torch.cuda.set_device(device)
         total = torch.cuda.mem_get_info()[1]
         self.budget = int(budget_bytes if budget_bytes is not None else budget_frac * total)
-        self.stream = torch.cuda.Stream()
+        self.streams = [torch.cuda.Stream() for _ in range(max(1, int(n_streams)))]
+        self.stream = self.streams[0]
         self.chunk = int(chunk)
         self.use_graph = use_graph
         self.max_running = max_running
         self.sched = Scheduler(self.budget, max_running, self._bytes_of)
         self._work_cap = 1 << 20  # 32 MB of work items
-        self.group = N.Group(max_running, self._work_cap, stream=self.stream)
+        self.groups = [N.Group(max_running, self._work_cap, stream=st) for st in self.streams]
+        self.load = [0] * len(self.groups)  # cells running in each group
+        self.where: Dict[int, int] = {}
         self.sims: Dict[int, object] = {}
         self.target: Dict[int, int] = {}
         self.admit_t: Dict[int, float] = {}
@@ -153,9 +160,12 @@ class Server:
         return n
 
     def _admit(self, r: Request, now: float):
-        with self.torch.cuda.stream(self.stream):
-            s = self.N.Sim.from_workload(r.workload, r.precision, stream=self.stream)
-        self.group.add(s)
+        k = min(range(len(self.groups)), key=lambda i: self.load[i])
+        with self.torch.cuda.stream(self.streams[k]):
+            s = self.N.Sim.from_workload(r.workload, r.precision, stream=self.streams[k])
+        self.groups[k].add(s)
+        self.where[r.rid] = k
+        self.load[k] += s.n_cells
         self.sims[r.rid] = s
         self.target[r.rid] = r.steps
         self.admit_t[r.rid] = now
@@ -163,7 +173,9 @@ class Server:
     def _retire(self, rid: int, now_fn):
         s = self.sims.pop(rid)
         r = self.sched.running[rid]
-        self.group.remove(s)
+        k = self.where.pop(rid)
+        self.groups[k].remove(s)
+        self.load[k] -= s.n_cells
         obs = s.observe(-1, allow_nonfinite=True)
         fields = s.get_fields() if r.keep_fields else None
         self.results.append(Result(rid, r.arrival_s * self._scale, self.admit_t.pop(rid), now_fn(), r.steps, s.n_cells,
@@ -194,13 +206,16 @@ class Server:
             # a chunk never passes any running run's own step count
             n = min([self.chunk] + [self.target[rid] - self.sims[rid].steps_done for rid in self.sims])
             if n > 0:
-                self.group.step(n, use_graph=self.use_graph)
+                for g in self.groups:  # each on its own stream, queued back to back
+                    if len(g.members):
+                        g.step(n, use_graph=self.use_graph)
                 self.cell_steps += n * sum(s.n_cells for s in self.sims.values())
                 for s in self.sims.values():
                     self.cell_steps_by_dim[s.p.dim] += n * s.n_cells
                 self.max_running_seen = max(self.max_running_seen, len(self.sims))
                 self.peak_bytes = max(self.peak_bytes, self.sched.used)
-            self.stream.synchronize()  # bound the queue depth: times below are device-complete
+            for st in self.streams:  # bound the queue depth: times below are device-complete
+                st.synchronize()
             for rid in [rid for rid in self.sims if self.sims[rid].steps_done >= self.target[rid]]:
                 self._retire(rid, now)
         self.wall_s = now()
@@ -216,6 +231,7 @@ class Server:
     def close(self):
         for rid in list(self.sims):
             s = self.sims.pop(rid)
-            self.group.remove(s)
+            self.groups[self.where.pop(rid)].remove(s)
             s.close()
-        self.group.close()
+        for g in self.groups:
+            g.close()

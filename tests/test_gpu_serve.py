@@ -19,7 +19,8 @@ def native():
     return N
 
 
-def test_served_results_equal_alone(native):
+@pytest.mark.parametrize("n_streams", [1, 2, 3])
+def test_served_results_equal_alone(native, n_streams):
     from paper_2110_12448_gb300.serve import Request, Server
     rng = np.random.default_rng(31)
     reqs = []
@@ -32,7 +33,7 @@ def test_served_results_equal_alone(native):
         prec = "f64" if i == 4 else "f32"
         reqs.append(Request(i, w, steps=int(rng.integers(20, 120)), precision=prec, arrival_s=0.02 * i,
                             keep_fields=True))
-    srv = Server(chunk=16, budget_bytes=1 << 30)
+    srv = Server(chunk=16, budget_bytes=1 << 30, n_streams=n_streams)
     res = {r.rid: r for r in srv.run(reqs)}
     summ = srv.summary()
     srv.close()
