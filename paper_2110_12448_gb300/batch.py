@@ -27,6 +27,8 @@ class Batch:
 
     def __init__(self, workloads, precision="f32", n_streams=2, tile=None, device="cuda"):
         import torch
+        if not workloads:
+            raise ValueError("Batch: no workloads")
         n = max(1, min(int(n_streams), len(workloads)))
         self.streams = [torch.cuda.Stream(device=device) for _ in range(n)]
         self.order = []   # (group index, member index) of each workload, in workload order

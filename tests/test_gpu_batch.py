@@ -67,3 +67,9 @@ def test_autotune_under_two_streams(native):
     b.step(5)
     assert b.steps_done == 5 and all(o["nonfinite"] == 0 for o in b.observe(0))
     b.close()
+
+
+def test_empty_batch_rejected(native):
+    from paper_2110_12448_gb300.batch import Batch
+    with pytest.raises(ValueError):
+        Batch([], "f32")
