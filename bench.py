@@ -880,12 +880,13 @@ def run_native(args):
                     "flop_source": "ncu thread-instruction counts of one launch (FADD, FMUL, FFMA and packed pairs)"}
 
     # end to end through the public API, as a client pipelines a batch: the
-    # instances split into two halves, each half a group on its own stream;
-    # per half, its state queued in from pinned host buffers
+    # instances split into `args.e2e_parts` parts, each a group on its own
+    # stream; per part, its state queued in from pinned host buffers
     # (pf_set_fields_async), the K steps with their observes
-    # (pf_group_observe), the state queued back out (pf_get_fields_async).
-    # One half's copies overlap the other half's steps; all inside the timed
-    # region, from the first upload to the last download.
+    # (pf_group_observe), the state queued back out (pf_get_fields_async)
+    # right after the part's last observe.  One part's copies overlap the
+    # other parts' steps; all inside the timed region, from the first upload
+    # to the last download.
     e2e = None
     if not args.no_e2e:
         dt_np = np.float32 if args.precision == "f32" else np.float64
@@ -895,8 +896,8 @@ def run_native(args):
             hu = torch.empty_like(hp).pin_memory()
             s.get_fields(out=(hp.numpy(), hu.numpy()))
             host.append((hp, hu))
-        half = (len(ws) + 1) // 2
-        parts = [list(range(half)), list(range(half, len(ws)))]
+        n_parts = max(1, min(args.e2e_parts, len(ws)))
+        parts = [list(range(len(ws)))[k::n_parts] for k in range(n_parts)]
         pipes = []
         for idx in parts:
             if not idx:
@@ -928,13 +929,16 @@ def run_native(args):
             for st_, ss, g_, hh in pipes:
                 g_.step(chunk, use_graph=True)
             done += chunk
-            if (at + chunk) % OBS_EVERY == 0 or done == args.steps:
+            last = done == args.steps
+            if (at + chunk) % OBS_EVERY == 0 or last:
                 for st_, ss, g_, hh in pipes:
                     g_.observe(0)
+                    if last:  # this part's state back out while the other parts still step
+                        for x, (hp, hu) in zip(ss, hh):
+                            x.get_fields_async(hp.numpy(), hu.numpy())  # straight into the pinned buffers
         h2d = d2h = 0
         for st_, ss, g_, hh in pipes:
             for x, (hp, hu) in zip(ss, hh):
-                x.get_fields_async(hp.numpy(), hu.numpy())  # straight into the pinned buffers
                 h2d += hp.numel() * hp.element_size() * 2
                 d2h += hp.numel() * hp.element_size() * 2
         for st_, ss, g_, hh in pipes:
@@ -946,9 +950,9 @@ def run_native(args):
                 x.close()
         e2e = {"value": cells * args.steps * world / e2e_s / 1e9, "unit": "GLUPS",
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
-               "copies": "two half-batches on two streams, each: pf_set_fields_async from pinned host buffers, "
-                         "the steps and observes, pf_get_fields_async into them; one half's copies overlap the "
-                         "other's steps"}
+               "copies": f"{len(pipes)} parts of the batch on their own streams, each: pf_set_fields_async from "
+                         "pinned host buffers, the steps and observes, pf_get_fields_async into them after its last "
+                         "observe; one part's copies overlap the other parts' steps"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
@@ -998,6 +1002,8 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f32c"],
                     help="f32c: FP32 arithmetic on the compensated (hi + lo) state, 2D")
     ap.add_argument("--time-level", default="t1", choices=["t1", "t0"])
+    ap.add_argument("--e2e-parts", type=int, default=2,
+                    help="parts of the batch in the end-to-end measurement, each on its own stream")
     ap.add_argument("--streams", type=int, default=2,
                     help="groups the batch is split into, each on its own CUDA stream (fewer for fewer instances)")
     ap.add_argument("--kernels", default="fused", choices=["fused", "two"],
