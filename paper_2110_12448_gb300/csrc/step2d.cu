@@ -79,7 +79,13 @@ template <> struct M<float> {
         return fmaf(-2.0f, rcp_approx(1.0f + e), 1.0f);
     }
     static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
-    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    // single-instruction approximate square root (0 at 0): the App. B and
+    // <10> anti-trapping magnitudes, guarded where |grad psi| vanishes
+    static __device__ __forceinline__ float sqrt_(float x) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
 };
 #else
 // correctly rounded division and the library tanh (slower; for accuracy studies)

@@ -34,7 +34,13 @@ template <> struct M3<float> {
         return 1.0f - __fdividef(2.0f, 1.0f + __expf(2.0f * x));
     }
     static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    // single-instruction approximate square root (0 at 0) for the <100>
+    // anti-trapping magnitude; the flux is guarded where |grad psi| vanishes
+    static __device__ __forceinline__ float sqrt_(float x) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
 };
 template <> struct M3<double> {
     // tanh is exactly +-1 beyond |x| = 22.6 (|psi| = 32); the FP64 library
