@@ -73,3 +73,31 @@ def test_empty_batch_rejected(native):
     from paper_2110_12448_gb300.batch import Batch
     with pytest.raises(ValueError):
         Batch([], "f32")
+
+
+@pytest.mark.parametrize("n_streams", [2, 3])
+def test_batch_equals_one_group_frozen_gradient(native, n_streams):
+    """Frozen-temperature instances read their time from each group's step
+    clock: split over several groups they still reach the same state."""
+    import torch
+    from paper_2110_12448_gb300.batch import Batch
+    ws = [synth.directional_2d(96, 70, t, "SBAR21", Vp=0.3, lT=60.0) for t in (0.0, 20.0, 35.0)]
+    st = torch.cuda.Stream()
+    sims = [native.Sim.from_workload(w, "f32", stream=st) for w in ws]
+    for s in sims:
+        s.set_tile(64, 1, 16)
+    g = native.Group(len(sims), sum(native.Group.work_items(s) for s in sims), stream=st)
+    for s in sims:
+        g.add(s)
+    g.step(40, use_graph=True)
+    ref = [s.get_fields() for s in sims]
+    g.close()
+    b = Batch(ws, "f32", n_streams=n_streams, tile=(64, 1, 16))
+    b.step(24, use_graph=True, stream=st)
+    b.step(16, use_graph=False, stream=st)
+    for s, (p0, u0) in zip(b.members, ref):
+        p1, u1 = s.get_fields()
+        assert np.array_equal(p0, p1) and np.array_equal(u0, u1)
+    b.close()
+    for s in sims:
+        s.close()
