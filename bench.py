@@ -677,7 +677,7 @@ def run_serve(args):
     reqs = synth.request_stream(rate_per_s=args.rate, window_s=args.window, size_scale=args.serve_scale,
                                 steps_scale=args.serve_scale)
     rq = [serve.Request(i, r.workload, r.workload.steps, "f32", r.arrival_s) for i, r in enumerate(reqs)]
-    srv = serve.Server(budget_frac=0.8, chunk=100)
+    srv = serve.Server(budget_frac=0.8, chunk=100, n_streams=args.streams)
     with Clocks(local) as clocks:
         srv.run(rq)
     summ = srv.summary()
