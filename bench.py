@@ -61,7 +61,7 @@ TRAFFIC = {
     # k_step2d<float, S-bar_21> launches of the two five-instance groups, summed (ncu runs them one
     # after the other, so each group's half of the state partly stays in L2)
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu", "tile": [64, 1, 38],
-                "sha256": "3b1c66eb91e052c71c4ba8c84395ea905f6c9df95ae5ac738da90e29ad7f57c4", "bytes": 119783424},
+                "sha256": "14be623eb6a89ef5e15fc15b790f6f3aba135cbc80291d90a6a528ccd3ee2178", "bytes": 120115200},
     # ncu capture of one k_step3d<float, S-bar_120, 30, 6> launch of the 256^3 free dendrite (tile 34 x 10 x 52)
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu", "tile": [34, 10, 52],
                    "sha256": "1f5d22af251dade05882fb4be57c4fe582caa7ec964125d0cab5048c80b10939", "bytes": 263584512},
@@ -78,7 +78,7 @@ TRAFFIC = {
 FLOPS = {
     # k_step2d<float, S-bar_21> launch of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38)
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu", "tile": [64, 1, 38],
-                "sha256": "3b1c66eb91e052c71c4ba8c84395ea905f6c9df95ae5ac738da90e29ad7f57c4", "flop_per_cell": 261.2},
+                "sha256": "14be623eb6a89ef5e15fc15b790f6f3aba135cbc80291d90a6a528ccd3ee2178", "flop_per_cell": 261.2},
     # k_step3d<float, S-bar_120, 30, 6> launch of the 256^3 free dendrite (tile 34 x 10 x 52)
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu", "tile": [34, 10, 52],
                    "sha256": "1f5d22af251dade05882fb4be57c4fe582caa7ec964125d0cab5048c80b10939", "flop_per_cell": 1100.6},

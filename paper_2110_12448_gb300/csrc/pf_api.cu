@@ -210,9 +210,11 @@ void build_work(const pf_sim* s, int inst, std::vector<WorkItem>& out) {
     }
 }
 
-// the 2D kernel variant with frozen temperature / periodic x / T0 time level
-bool ds_of(const pf_params& p) {
-    return p.thermal == PF_FROZEN_GRADIENT || p.bc_x == PF_BC_PERIODIC || p.time_level == PF_T0;
+// the 2D kernel variant: 1 frozen temperature and/or periodic x (either time
+// level), 2 isothermal with mirror walls at the T0 level, 0 otherwise
+int ds_of(const pf_params& p) {
+    if (p.thermal == PF_FROZEN_GRADIENT || p.bc_x == PF_BC_PERIODIC) return 1;
+    return p.time_level == PF_T0 ? 2 : 0;
 }
 
 // resident units of the step's kernel; for the two-kernel form those of the
@@ -315,8 +317,10 @@ bool launch_sim_step(const pf_sim* s, int64_t step) {
     const int lp = (int)(step & 1);
     const StepClock clk{nullptr, nullptr, (long long)step};
     if (s->p.dim == 2 && s->p.kernels == PF_TWO_KERNELS)
-        return launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp, clk, true, 1) &&
-               launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp, clk, true, 2);
+        return launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp, clk,
+                             ds_of(s->p), 1) &&
+               launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp, clk,
+                             ds_of(s->p), 2);
     if (s->p.dim == 2)
         return launch_step2d(prec, s->p.scheme, s->bx, s->grid, s->st, s->work, s->n_work, s->rec, lp, clk,
                              ds_of(s->p));
@@ -960,7 +964,7 @@ struct pf_group {
     bool dirty;
     struct Cls {
         int dim, scheme, prec, bx, by, w0, n, grid;
-        bool ds;   // 2D kernel variant with frozen temperature / periodic x
+        int ds;    // 2D kernel variant (ds_of: 0 isothermal T1, 1 frozen temperature / periodic x, 2 isothermal T0)
         bool two;  // two-kernel form: the psi pass, then the U pass
     };
     std::vector<Cls> classes;
@@ -1047,9 +1051,9 @@ bool group_launch_once(pf_group* g, int launch_parity) {
                                clk);
         else if (c.two)
             ok = launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs, launch_parity, clk,
-                               true, 1) &&
+                               c.ds, 1) &&
                  launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs, launch_parity, clk,
-                               true, 2);
+                               c.ds, 2);
         else
             ok = launch_step2d(c.prec, c.scheme, c.bx, c.grid, g->st, g->work + c.w0, c.n, g->recs, launch_parity, clk,
                                c.ds);

@@ -122,17 +122,19 @@ struct StepClock {
     const long long* base;
     long long step;
 };
-// mode: 0 the fused step; 1, 2 the psi and U passes of the two-kernel form
-// (T0 time level, the ds variant, prec 0 or 1)
+// var: the 2D kernel variant: 0 isothermal, mirror walls, T1; 1 frozen
+// temperature and/or periodic x (T1 or T0 read from the record); 2 isothermal,
+// mirror walls, T0.  mode: 0 the fused step; 1, 2 the psi and U passes of the
+// two-kernel form (T0 time level: variant 1 or 2, prec 0 or 1)
 bool launch_step2d(int prec, int scheme, int bx, int grid, cudaStream_t st, const WorkItem* work, int n_work,
-                   const InstRec* recs, int launch_parity, StepClock clk, bool ds, int mode = 0);
+                   const InstRec* recs, int launch_parity, StepClock clk, int var, int mode = 0);
 bool launch_step3d(int prec, int scheme, int bx, int by, int grid, cudaStream_t st, const WorkItem* work,
                    int n_work, const InstRec* recs, int launch_parity, StepClock clk);
 // clock += 1 (one thread)
 cudaError_t launch_tick(long long* clock, cudaStream_t st);
-// Blocks of the fused kernel that fit on one SM (0 if not compiled).
-// ds: the kernel variant for frozen-temperature / periodic-x instances
-int occupancy_step2d(int prec, int scheme, int bx, bool ds, int mode = 0);
+// Blocks of the fused kernel that fit on one SM (0 if not compiled); var as
+// for launch_step2d
+int occupancy_step2d(int prec, int scheme, int bx, int var, int mode = 0);
 int occupancy_step3d(int prec, int scheme, int bx, int by);
 
 // Observation / initialisation kernels (observe.cu).

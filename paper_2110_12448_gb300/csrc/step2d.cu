@@ -256,6 +256,15 @@ template <typename T> __device__ __forceinline__ V<T> aniso_w2(V<T> gx, V<T> gy,
     const V<T> w = bc<T>(T(4) * eps) * fma(sx, sx, sy * sy);
     return mk(r2.x() * hh < Guard<T>::v ? T(3) * eps : w.x(), r2.y() * hh < Guard<T>::v ? T(3) * eps : w.y());
 }
+// explicitly rounded scalar operations: the compiler contracts none of them,
+// so every kernel that inlines the scalar face below computes the same bits
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // scalar version for the rare faces between two grains
 template <typename T>
 __device__ __forceinline__ T aniso_qn1(T gx, T gy, T Ra, T Rb, T Rc, T Rd, T eps, T hh, bool xface) {
@@ -271,6 +280,26 @@ __device__ __forceinline__ T aniso_qn1(T gx, T gy, T Ra, T Rb, T Rc, T Rd, T eps
     const T c0 = a * a - T(1) - c1 * q;
     const T jx = cx * (c0 + c1 * sx), jy = cy * (c0 + c1 * sy);
     return xface ? (Ra * jx + Rb * jy) : (Rc * jx + Rd * jy);
+}
+// The same face with every operation explicitly rounded, for the T0 kernels:
+// the fused T0 step and the two passes of the two-kernel form then compute
+// the same bits (the contractible version above may be contracted
+// differently in different kernels).
+template <typename T>
+__device__ __forceinline__ T aniso_qn1_rn(T gx, T gy, T Ra, T Rb, T Rc, T Rd, T eps, T hh, bool xface) {
+    const T cx = rn_fma(Ra, gx, rn_mul(Rc, gy));
+    const T cy = rn_fma(Rb, gx, rn_mul(Rd, gy));
+    const T r2 = rn_fma(cx, cx, rn_mul(cy, cy));
+    if (rn_mul(r2, hh) < Guard<T>::v) return T(0);
+    const T inv = M<T>::rcp(r2);
+    const T sx = rn_mul(rn_mul(cx, cx), inv), sy = rn_mul(rn_mul(cy, cy), inv);
+    const T q = rn_fma(sx, sx, rn_mul(sy, sy));
+    const T e4 = rn_mul(T(4), eps);
+    const T a = rn_fma(e4, q, rn_fma(T(-3), eps, T(1)));
+    const T c1 = rn_mul(rn_mul(T(16), eps), a);
+    const T c0 = rn_add(rn_fma(a, a, T(-1)), -rn_mul(c1, q));
+    const T jx = rn_mul(cx, rn_fma(c1, sx, c0)), jy = rn_mul(cy, rn_fma(c1, sy, c0));
+    return xface ? rn_fma(Ra, jx, rn_mul(Rb, jy)) : rn_fma(Rc, jx, rn_mul(Rd, jy));
 }
 
 // App. B: |grad b| at a <10> face (pairs); B(p, q) = b at origin + p normal + q tangent.
@@ -516,21 +545,25 @@ __device__ __forceinline__ void store_pair(T* __restrict__ row, int c, int nx, b
 #define PF_STEP2D_MIN_BLOCKS_F32C 11
 #endif
 
-// DS = false: isothermal instances with mirror walls (the flags below are
-// compile-time false and their code disappears); DS = true: instances with a
-// frozen temperature and/or periodic x.  CMP = true (T = float, DS = false):
-// the compensated state of precision PF_F32C, the lo halves of psi and U
-// stored right after the hi halves of each time level.  MODE (T0 time level
-// only, DS = true): 0 the fused step; 1 the psi pass of the two-kernel form of
+// VAR 0: isothermal instances with mirror walls at the T1 time level (the
+// flags below are compile-time false and their code disappears); VAR 1 (DS):
+// instances with a frozen temperature and/or periodic x, T1 or T0 read from
+// the record; VAR 2: isothermal instances with mirror walls at the T0 time
+// level, T0 fixed at compile time.  CMP = true (T = float, VAR 0): the
+// compensated state of precision PF_F32C, the lo halves of psi and U stored
+// right after the hi halves of each time level.  MODE (T0 time level only,
+// VAR 1 or 2): 0 the fused step; 1 the psi pass of the two-kernel form of
 // Sec. 3.3.1, which stores psi' and d psi/dt (InstRec::rate); 2 its U pass,
 // which reads d psi/dt back instead of recomputing phase 1 (U' needs only
 // psi^n, U^n and d psi/dt^n at the T0 level).
-template <typename T, int S, bool DS, bool CMP, int MODE = 0>
+template <typename T, int S, int VAR, bool CMP, int MODE = 0>
 __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                                   sizeof(T) == 4 ? (CMP ? PF_STEP2D_MIN_BLOCKS_F32C : PF_STEP2D_MIN_BLOCKS_F32) : 1)
     k_step2d(const WorkItem* __restrict__ work, int n_work, const InstRec* __restrict__ recs, int launch_parity,
              StepClock clk) {
     constexpr bool ISO = (S == S21 || S == SBAR21);
+    constexpr bool DS = VAR == 1;   // frozen temperature / periodic x, T0 from the record
+    constexpr bool T0I = VAR == 2;  // isothermal, mirror walls, T0
     const int lane = threadIdx.x & 31;
     const int warps_per_block = blockDim.x >> 5;
     const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
@@ -563,7 +596,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
         const T isq2dt = cst[C_ISQ2DT];
         const bool vec = (nx & 1) == 0;
         const bool per = DS && rec.bcx != 0;
-        const bool t0 = DS && rec.tlevel != 0;  // T0 time level
+        const bool t0 = T0I || (DS && rec.tlevel != 0);  // T0 time level
         // frozen temperature: zeta at row p = zeta_y0 + (p - y0) zA (Eqs. Thermal_F1/_F2);
         // the DS variant applies it branch-free (zA = zB = zC = 0 gives zeta = 0, F1 = 1)
         T zeta_y0 = T(0), zA = T(0);
@@ -726,6 +759,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             };
             auto aq1 = [&](T gx, T gy, T Ra, T Rb, T Rc, T Rd) -> T {
                 if constexpr (CMP) return aniso_qn1c<T>(gx, gy, Ra, Rb, Rc, Rd, eps, hh, true);
+                if constexpr (VAR != 0) return aniso_qn1_rn<T>(gx, gy, Ra, Rb, Rc, Rd, eps, hh, true);
                 return aniso_qn1<T>(gx, gy, Ra, Rb, Rc, Rd, eps, hh, true);
             };
             const V<T> gxX = (E0 - C0) * bc<T>(ih), gyX = ((Ep + Cp) - (Em + Cm)) * bc<T>(i4h);
@@ -831,6 +865,13 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             phc = ph;
             psin = fma(bc<T>(dt), rate, C0);
             psin_lo = L0.C();
+            if constexpr (T0I) {
+                // T0: chain-rule increment dt (1 - phi^2)/sqrt2 dpsi/dt and phi^n on the
+                // left-hand side; phi' is not needed
+                dph = bc<T>(dt * T(0.70710678118654752440)) * (bc<T>(T(1)) - ph * ph) * rate;
+                phin = ph;
+                return;
+            }
             if constexpr (sizeof(T) == 8) {
                 const T B = Bulk<T>::psi;
                 if (__all_sync(FULL, fabs(psin.x()) > B && fabs(psin.y()) > B))
@@ -1164,48 +1205,60 @@ constexpr int WARPS_PER_BLOCK = PF_STEP2D_WPB;
 
 template <typename T, int S>
 bool launch_one(int grid_warps, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp,
-                StepClock clk, bool ds, int mode) {
+                StepClock clk, int var, int mode) {
     const int blocks = (grid_warps + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-    if (mode != 0 && !ds) return false;  // the two-kernel form runs on the T0 (ds) variant
-    if (mode == 1)
-        k_step2d<T, S, true, false, 1><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
-    else if (mode == 2)
-        k_step2d<T, S, true, false, 2><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
-    else if (ds)
-        k_step2d<T, S, true, false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
-    else
-        k_step2d<T, S, false, false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
+    const int th = 32 * WARPS_PER_BLOCK;
+    if (var < 0 || var > 2) return false;
+    if (mode != 0 && var == 0) return false;  // the two-kernel form runs at the T0 level (variant 1 or 2)
+    if (mode == 1) {
+        if (var == 2) k_step2d<T, S, 2, false, 1><<<blocks, th, 0, st>>>(work, n_work, recs, lp, clk);
+        else k_step2d<T, S, 1, false, 1><<<blocks, th, 0, st>>>(work, n_work, recs, lp, clk);
+    } else if (mode == 2) {
+        if (var == 2) k_step2d<T, S, 2, false, 2><<<blocks, th, 0, st>>>(work, n_work, recs, lp, clk);
+        else k_step2d<T, S, 1, false, 2><<<blocks, th, 0, st>>>(work, n_work, recs, lp, clk);
+    } else if (var == 2) {
+        k_step2d<T, S, 2, false><<<blocks, th, 0, st>>>(work, n_work, recs, lp, clk);
+    } else if (var == 1) {
+        k_step2d<T, S, 1, false><<<blocks, th, 0, st>>>(work, n_work, recs, lp, clk);
+    } else {
+        k_step2d<T, S, 0, false><<<blocks, th, 0, st>>>(work, n_work, recs, lp, clk);
+    }
     return true;
 }
 // compensated state (isothermal, mirror walls, T1 only)
 template <int S>
 bool launch_cmp(int grid_warps, cudaStream_t st, const WorkItem* work, int n_work, const InstRec* recs, int lp,
-                StepClock clk, bool ds) {
-    if (ds) return false;
+                StepClock clk, int var) {
+    if (var != 0) return false;
     const int blocks = (grid_warps + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-    k_step2d<float, S, false, true><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
+    k_step2d<float, S, 0, true><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(work, n_work, recs, lp, clk);
     return true;
 }
 
-template <typename T, int S> int occ_one(bool ds, int mode) {
+template <typename T, int S> int occ_one(int var, int mode) {
     int n = 0;
-    if (mode != 0 && !ds) return 0;
+    if (var < 0 || var > 2 || (mode != 0 && var == 0)) return 0;
+    const int th = 32 * WARPS_PER_BLOCK;
     cudaError_t e;
     if (mode == 1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, true, false, 1>, 32 * WARPS_PER_BLOCK, 0);
+        e = var == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, 2, false, 1>, th, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, 1, false, 1>, th, 0);
     else if (mode == 2)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, true, false, 2>, 32 * WARPS_PER_BLOCK, 0);
-    else if (ds)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, true, false>, 32 * WARPS_PER_BLOCK, 0);
+        e = var == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, 2, false, 2>, th, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, 1, false, 2>, th, 0);
+    else if (var == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, 2, false>, th, 0);
+    else if (var == 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, 1, false>, th, 0);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, false, false>, 32 * WARPS_PER_BLOCK, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<T, S, 0, false>, th, 0);
     return e == cudaSuccess ? n * WARPS_PER_BLOCK : 0;
 }
-template <int S> int occ_cmp(bool ds) {
-    if (ds) return 0;
+template <int S> int occ_cmp(int var) {
+    if (var != 0) return 0;
     int n = 0;
     const cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<float, S, false, true>, 32 * WARPS_PER_BLOCK, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2d<float, S, 0, true>, 32 * WARPS_PER_BLOCK, 0);
     return e == cudaSuccess ? n * WARPS_PER_BLOCK : 0;
 }
 
@@ -1216,26 +1269,26 @@ PF_BOUNDS_READER(bounds_step2d)
 // The 2D kernel is warp-granular: `bx` must be 64 (columns a warp holds) and
 // `grid` counts warps.
 bool launch_step2d(int prec, int scheme, int bx, int grid, cudaStream_t st, const WorkItem* work, int n_work,
-                   const InstRec* recs, int lp, StepClock clk, bool ds, int mode) {
+                   const InstRec* recs, int lp, StepClock clk, int var, int mode) {
     if (bx != WARP_COLS) return false;
     if (prec == 0) {
         switch (scheme) {
-            case S10: return launch_one<float, S10>(grid, st, work, n_work, recs, lp, clk, ds, mode);
-            case S21: return launch_one<float, S21>(grid, st, work, n_work, recs, lp, clk, ds, mode);
-            case SBAR21: return launch_one<float, SBAR21>(grid, st, work, n_work, recs, lp, clk, ds, mode);
+            case S10: return launch_one<float, S10>(grid, st, work, n_work, recs, lp, clk, var, mode);
+            case S21: return launch_one<float, S21>(grid, st, work, n_work, recs, lp, clk, var, mode);
+            case SBAR21: return launch_one<float, SBAR21>(grid, st, work, n_work, recs, lp, clk, var, mode);
         }
     } else if (prec == 2) {
         if (mode != 0) return false;
         switch (scheme) {
-            case S10: return launch_cmp<S10>(grid, st, work, n_work, recs, lp, clk, ds);
-            case S21: return launch_cmp<S21>(grid, st, work, n_work, recs, lp, clk, ds);
-            case SBAR21: return launch_cmp<SBAR21>(grid, st, work, n_work, recs, lp, clk, ds);
+            case S10: return launch_cmp<S10>(grid, st, work, n_work, recs, lp, clk, var);
+            case S21: return launch_cmp<S21>(grid, st, work, n_work, recs, lp, clk, var);
+            case SBAR21: return launch_cmp<SBAR21>(grid, st, work, n_work, recs, lp, clk, var);
         }
     } else {
         switch (scheme) {
-            case S10: return launch_one<double, S10>(grid, st, work, n_work, recs, lp, clk, ds, mode);
-            case S21: return launch_one<double, S21>(grid, st, work, n_work, recs, lp, clk, ds, mode);
-            case SBAR21: return launch_one<double, SBAR21>(grid, st, work, n_work, recs, lp, clk, ds, mode);
+            case S10: return launch_one<double, S10>(grid, st, work, n_work, recs, lp, clk, var, mode);
+            case S21: return launch_one<double, S21>(grid, st, work, n_work, recs, lp, clk, var, mode);
+            case SBAR21: return launch_one<double, SBAR21>(grid, st, work, n_work, recs, lp, clk, var, mode);
         }
     }
     return false;
@@ -1243,26 +1296,26 @@ bool launch_step2d(int prec, int scheme, int bx, int grid, cudaStream_t st, cons
 
 // Warps of the fused kernel (mode 0) or of a pass of the two-kernel form
 // resident on one SM (0 if not compiled).
-int occupancy_step2d(int prec, int scheme, int bx, bool ds, int mode) {
+int occupancy_step2d(int prec, int scheme, int bx, int var, int mode) {
     if (bx != WARP_COLS) return 0;
     if (prec == 0) {
         switch (scheme) {
-            case S10: return occ_one<float, S10>(ds, mode);
-            case S21: return occ_one<float, S21>(ds, mode);
-            case SBAR21: return occ_one<float, SBAR21>(ds, mode);
+            case S10: return occ_one<float, S10>(var, mode);
+            case S21: return occ_one<float, S21>(var, mode);
+            case SBAR21: return occ_one<float, SBAR21>(var, mode);
         }
     } else if (prec == 2) {
         if (mode != 0) return 0;
         switch (scheme) {
-            case S10: return occ_cmp<S10>(ds);
-            case S21: return occ_cmp<S21>(ds);
-            case SBAR21: return occ_cmp<SBAR21>(ds);
+            case S10: return occ_cmp<S10>(var);
+            case S21: return occ_cmp<S21>(var);
+            case SBAR21: return occ_cmp<SBAR21>(var);
         }
     } else {
         switch (scheme) {
-            case S10: return occ_one<double, S10>(ds, mode);
-            case S21: return occ_one<double, S21>(ds, mode);
-            case SBAR21: return occ_one<double, SBAR21>(ds, mode);
+            case S10: return occ_one<double, S10>(var, mode);
+            case S21: return occ_one<double, S21>(var, mode);
+            case SBAR21: return occ_one<double, SBAR21>(var, mode);
         }
     }
     return 0;
