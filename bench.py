@@ -52,19 +52,21 @@ def dist_env():
     return rank, world, local
 
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
-# source is byte-identical to the one captured (sha256 of the .cu file) and
-# the launch uses the captured tile (block x, block y, sweep).
+# DRAM traffic per step of the dominant kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) without cache flushes between
+# launches (--cache-control none: the lines a launch leaves dirty in L2 are
+# written back during the next one, as in a live run), valid only while the
+# kernel source is byte-identical to the one captured (sha256 of the .cu file)
+# and the launch uses the captured tile (block x, block y, sweep).
 TRAFFIC = {
-    # ncu capture of one step of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38): the two
+    # one step of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38): the two
     # k_step2d<float, S-bar_21> launches of the two five-instance groups, summed (ncu runs them one
     # after the other, so each group's half of the state partly stays in L2)
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu", "tile": [64, 1, 38],
-                "sha256": "14be623eb6a89ef5e15fc15b790f6f3aba135cbc80291d90a6a528ccd3ee2178", "bytes": 120115200},
-    # ncu capture of one k_step3d<float, S-bar_120, 30, 6> launch of the 256^3 free dendrite (tile 34 x 10 x 52)
+                "sha256": "14be623eb6a89ef5e15fc15b790f6f3aba135cbc80291d90a6a528ccd3ee2178", "bytes": 120690176},
+    # one k_step3d<float, S-bar_120, 30, 6> launch of the 256^3 free dendrite (tile 34 x 10 x 52)
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu", "tile": [34, 10, 52],
-                   "sha256": "1f5d22af251dade05882fb4be57c4fe582caa7ec964125d0cab5048c80b10939", "bytes": 263584512},
+                   "sha256": "1f5d22af251dade05882fb4be57c4fe582caa7ec964125d0cab5048c80b10939", "bytes": 265664000},
 }
 
 
@@ -90,12 +92,17 @@ def _captured(table, workload, key, tile=None):
     """table[workload][key] if the kernel source still matches the capture and
     the launch uses the captured block shape, else None.  (The sweep length
     moves the per-cell figures only through the halo rows or planes of each
-    work item's prologue: well under 1 % between neighbouring sweeps.)"""
+    work item's prologue: well under 1 % between neighbouring sweeps.)  The
+    DRAM bytes were captured at depth 1 (one launch per step); a depth-2 tile
+    (two steps per wavefront of band launches) runs the same work items, so
+    its FLOP per cell carry over, its DRAM bytes do not."""
     import hashlib
     t = table.get(workload)
     if not t or not t["sha256"]:
         return None
     if tile is None or list(tile)[:2] != list(t["tile"])[:2]:
+        return None
+    if key == "bytes" and len(tile) > 3 and int(tile[3]) != 1:
         return None
     with open(os.path.join(ROOT, t["source"]), "rb") as f:
         if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
@@ -377,10 +384,11 @@ def run_batch(stream, ws, precision, obs_back=1000, keep=()):
     with torch.cuda.stream(stream):
         for w in ws:
             sims.append(N.Sim.from_workload(w, precision, stream=stream))
-            sims[-1].set_tile(*tile)
+            sims[-1].set_tile(*autotune.split(tile)[0])
     group = N.Group(len(sims), sum(N.Group.work_items(s) for s in sims), stream=stream)
     for s in sims:
         group.add(s)
+    group.set_depth(*autotune.split(tile)[1])
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     ms = 0.0
@@ -439,10 +447,11 @@ def batch_rate(stream, ws, precision, steps, warm=5):
     with torch.cuda.stream(stream):
         for w in ws:
             sims.append(N.Sim.from_workload(w, precision, stream=stream))
-            sims[-1].set_tile(*tile)
+            sims[-1].set_tile(*autotune.split(tile)[0])
     group = N.Group(len(sims), sum(N.Group.work_items(s) for s in sims), stream=stream)
     for s in sims:
         group.add(s)
+    group.set_depth(*autotune.split(tile)[1])
     group.step(warm)
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
@@ -762,10 +771,13 @@ def run_native(args):
     # fresh box) to the end of the timed region
     clocks = Clocks(local, window="the autotuner, the warm-up and the timed region")
     clocks.__enter__()
-    tile = None
-    if not args.no_tune:
+    tile, tune_times = None, {}
+    if args.tile:
         from paper_2110_12448_gb300 import autotune
-        tile, _ = autotune.tune(ws, args.precision, n_streams=args.streams)
+        tile = tuple(int(x) for x in args.tile.split(","))
+    elif not args.no_tune:
+        from paper_2110_12448_gb300 import autotune
+        tile, tune_times = autotune.tune(ws, args.precision, n_streams=args.streams)
     # the batch as `args.streams` groups on their own streams (forked from and
     # joined to `stream` around every run of steps): one group's launches fill
     # the tail of the other's persistent launch
@@ -910,10 +922,12 @@ def run_native(args):
                 for i in idx:
                     ss.append(N.Sim.from_workload(ws[i], args.precision, stream=st_, init=False))
                     if tile:
-                        ss[-1].set_tile(*tile)
+                        ss[-1].set_tile(*autotune.split(tile)[0])
             g_ = N.Group(len(ss), sum(N.Group.work_items(x) for x in ss), stream=st_)
             for x in ss:
                 g_.add(x)
+            if tile:
+                g_.set_depth(*autotune.split(tile)[1])
             pipes.append((st_, ss, g_, [host[i] for i in idx]))
         for st_, ss, g_, hh in pipes:  # untimed warm-up of the new groups (graph capture)
             for x, (hp, hu) in zip(ss, hh):
@@ -977,7 +991,12 @@ def run_native(args):
                                         "over": f"{len(per_step)} single steps of the whole batch after the timed "
                                                 f"region, each launched directly with its own events"},
                 "tile": list(tile) if tile else None,
-                "gpu_launches": (n_launch + 2 * n_observe) * len(batch.groups)}
+                # a depth-2 step is one launch per band (one class per group here)
+                "gpu_launches": (n_launch * (autotune.bands(ws, tile) if tile else 1) + 2 * n_observe)
+                                * len(batch.groups)}
+        if tune_times:
+            # temporal-blocking depth as the autotuner raced it (ms per step of the batch)
+            line["depth_race"] = autotune.depth_race(tune_times)
         if sweep:
             line["directional" if args.workload == "directional2d" else "tip_radius_call"] = sweep
         if world == 1 and not args.no_fp64:
@@ -1021,6 +1040,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
     ap.add_argument("--no-tune", action="store_true", help="use the default tile instead of the autotuner's")
+    ap.add_argument("--tile", default=None,
+                    help="force a tile instead of the autotuner's: block_x,block_y,sweep[,depth,band_sweeps]")
     ap.add_argument("--no-physics", action="store_true",
                     help="skip the orientation sweep's tip-state runs (three schemes to 2e4 steps, FP64 check)")
     args = ap.parse_args()

@@ -364,6 +364,36 @@ int pf_group_remove(pf_group* g, pf_sim* s);
  * n < 0 is PF_ERR_INVALID. */
 int pf_group_step(pf_group* g, int64_t n, int use_graph);
 int pf_group_size(const pf_group* g);
+
+/* Temporal blocking of a group (explicit Euler, Sec. 3.3.1: step n+1 reads
+ * only level n).  depth 1 (the default) launches every step over whole grids.
+ * depth 2 advances two steps per wavefront over bands along the sweep axis
+ * (2D: y, 3D: z), band_sweeps work-item sweeps high (per member:
+ * band_sweeps x its sweep rows):
+ *   step n+1 on band 0, step n+1 on band 1, step n+2 on band 0,
+ *   step n+1 on band 2, step n+2 on band 1, ..., step n+2 on the last band
+ * (pf_wavefront_order), all on the group's stream.  Step n+2 on band b reads
+ * level n+1 on band b and two rows (planes) into its neighbours, which the
+ * step n+1 launches before it have written and no later launch overwrites; it
+ * writes level n+2 only into band b, which no later step n+1 launch reads,
+ * since a band (at least one sweep of at least 8 rows) is higher than the
+ * two-row psi halo.  The intermediate level is then read back while it is
+ * still in L2.  Every cell gets the same arithmetic as at depth 1, so results
+ * are bit-identical.  A group whose members include a frozen temperature (one
+ * step clock per launch) or a two-kernel member (its U pass needs the psi
+ * pass of the neighbouring bands) steps at depth 1; pf_group_get_depth
+ * reports the depth in effect.  An odd step
+ * count ends with one depth-1 step.  depth outside {1, 2} or band_sweeps < 1
+ * is PF_ERR_INVALID; the setting holds across membership changes. */
+int pf_group_set_depth(pf_group* g, int depth, int band_sweeps);
+/* The setting, and the depth the current members step at (1 or 2). */
+int pf_group_get_depth(pf_group* g, int* depth, int* band_sweeps, int* effective);
+/* The launch order of one depth-2 wavefront over n_bands bands (host only,
+ * no device work): entry i is (level[i], band[i]), level 0 = step n+1,
+ * level 1 = step n+2.  Writes min(cap, 2 n_bands) entries and returns
+ * 2 n_bands; n_bands < 1, cap < 0, or cap > 0 with a NULL array is
+ * PF_ERR_INVALID. */
+int pf_wavefront_order(int n_bands, int* level, int* band, int cap);
 /* pf_observe of every member (in the order they were added, out[i] for the
  * i-th) with one synchronisation: the reductions of all members are queued on
  * the group's stream and their records read back together.  grain as in

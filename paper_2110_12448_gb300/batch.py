@@ -23,7 +23,9 @@ from . import native as N
 
 class Batch:
     """`workloads` split round-robin over `n_streams` groups (fewer when there
-    are fewer workloads), each group and its members on their own stream."""
+    are fewer workloads), each group and its members on their own stream.
+    `tile` as autotune.tune returns it: (block_x, block_y, sweep) for the
+    members, and at depth 2 the group's temporal-blocking depth and band."""
 
     def __init__(self, workloads, precision="f32", n_streams=2, tile=None, device="cuda"):
         import torch
@@ -39,14 +41,17 @@ class Batch:
             self.parts[k].append(w)
         self.sims = []    # per group, its members
         self.groups = []
+        from .autotune import split
         for st, part in zip(self.streams, self.parts):
             ss = [N.Sim.from_workload(w, precision, stream=st) for w in part]
             if tile:
                 for s in ss:
-                    s.set_tile(*tile)
+                    s.set_tile(*split(tile)[0])
             g = N.Group(len(ss), sum(N.Group.work_items(s) for s in ss), stream=st, device=device)
             for s in ss:
                 g.add(s)
+            if tile:
+                g.set_depth(*split(tile)[1])
             self.sims.append(ss)
             self.groups.append(g)
 

@@ -966,8 +966,15 @@ struct pf_group {
         int dim, scheme, prec, bx, by, w0, n, grid;
         int ds;    // 2D kernel variant (ds_of: 0 isothermal T1, 1 frozen temperature / periodic x, 2 isothermal T0)
         bool two;  // two-kernel form: the psi pass, then the U pass
+        int occ;   // resident units per SM
+        std::vector<int> boff;  // depth 2: work items of band b are [w0 + boff[b], w0 + boff[b + 1])
     };
     std::vector<Cls> classes;
+    // temporal blocking (pf_group_set_depth): the setting, and whether the
+    // current members step as depth-2 wavefronts over n_bands bands
+    int depth, band_sweeps;
+    bool wave;
+    int n_bands;
     // step counter of frozen-temperature members: member m is at step
     // step_base[m] + *clock; the clock is advanced on the device after every
     // launch (also inside captured graphs) when any member is thermal
@@ -1002,25 +1009,56 @@ int group_rebuild(pf_group* g) {
         recs.push_back(make_rec(s, (int)((s->step ^ g->launches) & 1)));
     }
     long long prev = -1;
+    // depth 2 applies when no member has a frozen temperature or the
+    // two-kernel form; a band must be at least two rows high (the psi halo),
+    // which sweeps of at least 8 rows already guarantee
+    g->wave = g->depth == 2;
+    for (const pf_sim* s : g->members)
+        if (s->p.thermal == PF_FROZEN_GRADIENT || s->p.kernels == PF_TWO_KERNELS || (long long)g->band_sweeps * s->sweep < 2)
+            g->wave = false;
+    g->n_bands = 0;
+    std::vector<int> band_of;  // depth 2: band of every work item, in work order
     for (int i : order) {
         const pf_sim* s = g->members[i];
         const long long k = key(i);
         if (k != prev) {
             pf_group::Cls c{s->p.dim, s->p.scheme, kprec(s->p), s->bx, s->by, (int)work.size(), 0, 0,
-                            ds_of(s->p), s->p.kernels == PF_TWO_KERNELS};
+                            ds_of(s->p), s->p.kernels == PF_TWO_KERNELS, 0, {}};
             g->classes.push_back(c);
             prev = k;
         }
+        const size_t first = work.size();
         build_work(s, i, work);
         g->classes.back().n = (int)work.size() - g->classes.back().w0;
+        if (g->wave)
+            for (size_t w = first; w < work.size(); ++w) {
+                const int c0 = s->p.dim == 2 ? work[w].y0 : work[w].z0;
+                band_of.push_back(c0 / s->sweep / g->band_sweeps);
+                g->n_bands = std::max(g->n_bands, band_of.back() + 1);
+            }
     }
     if ((int)work.size() > g->max_work) return PF_ERR_BUDGET;
+    if (g->wave) {
+        // each class's items ordered by band (stable: members, then rows, then columns within a band)
+        for (auto& c : g->classes) {
+            std::vector<int> idx(c.n);
+            for (int j = 0; j < c.n; ++j) idx[j] = j;
+            std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return band_of[c.w0 + a] < band_of[c.w0 + b]; });
+            std::vector<WorkItem> sorted(c.n);
+            for (int j = 0; j < c.n; ++j) sorted[j] = work[c.w0 + idx[j]];
+            std::copy(sorted.begin(), sorted.end(), work.begin() + c.w0);
+            c.boff.assign(g->n_bands + 1, 0);
+            for (int j = 0; j < c.n; ++j) ++c.boff[band_of[c.w0 + j] + 1];
+            for (int b = 0; b < g->n_bands; ++b) c.boff[b + 1] += c.boff[b];
+        }
+    }
     for (auto& c : g->classes) {
         int occ = c.dim == 3 ? occupancy_step3d(c.prec, c.scheme, c.bx, c.by)
                   : c.two    ? std::min(occupancy_step2d(c.prec, c.scheme, c.bx, c.ds, 1),
                                         occupancy_step2d(c.prec, c.scheme, c.bx, c.ds, 2))
                              : occupancy_step2d(c.prec, c.scheme, c.bx, c.ds);
         if (occ <= 0) return PF_ERR_INVALID;
+        c.occ = occ;
         c.grid = std::min(c.n, occ * num_sms());
     }
     if (!recs.empty()) CK(cudaMemcpyAsync(g->recs, recs.data(), recs.size() * sizeof(InstRec), cudaMemcpyHostToDevice, g->st));
@@ -1063,6 +1101,33 @@ bool group_launch_once(pf_group* g, int launch_parity) {
     return true;
 }
 
+// the work items of band b of every class at one launch parity (depth 2;
+// fused kernels only, no frozen temperature: the step clock is not read)
+bool group_launch_band(pf_group* g, int launch_parity, int b) {
+    const StepClock clk{g->clock, g->step_base, 0};
+    for (const auto& c : g->classes) {
+        const int lo = c.boff[b], cnt = c.boff[b + 1] - lo;
+        if (cnt <= 0) continue;
+        const int grid = std::min(cnt, c.occ * num_sms());
+        const bool ok = c.dim == 3 ? launch_step3d(c.prec, c.scheme, c.bx, c.by, grid, g->st, g->work + c.w0 + lo, cnt,
+                                                   g->recs, launch_parity, clk)
+                                   : launch_step2d(c.prec, c.scheme, c.bx, grid, g->st, g->work + c.w0 + lo, cnt,
+                                                   g->recs, launch_parity, clk, c.ds);
+        if (!ok) return false;
+    }
+    return true;
+}
+
+// two steps as one wavefront over the bands, starting at launch parity lp
+bool group_launch_pair(pf_group* g, int lp) {
+    const int m = 2 * g->n_bands;
+    std::vector<int> level(m), band(m);
+    pf_wavefront_order(g->n_bands, level.data(), band.data(), m);
+    for (int i = 0; i < m; ++i)
+        if (!group_launch_band(g, lp ^ level[i], band[i])) return false;
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1072,6 +1137,46 @@ size_t pf_group_required_bytes(int max_instances, int max_work) {
     return align256((size_t)max_instances * sizeof(InstRec)) + align256((size_t)max_work * sizeof(WorkItem)) +
            align256((size_t)(max_instances + 1) * sizeof(long long)) +
            align256((size_t)max_instances * sizeof(ObsPartial)) + align256((size_t)max_instances * sizeof(ObsJob));
+}
+
+int pf_wavefront_order(int n_bands, int* level, int* band, int cap) {
+    if (n_bands < 1 || cap < 0 || (cap > 0 && (!level || !band))) return PF_ERR_INVALID;
+    int n = 0;
+    auto put = [&](int l, int b) {
+        if (n < cap) {
+            level[n] = l;
+            band[n] = b;
+        }
+        ++n;
+    };
+    // step n+1 runs one band ahead of step n+2
+    for (int b = 0; b <= n_bands; ++b) {
+        if (b < n_bands) put(0, b);
+        if (b >= 1) put(1, b - 1);
+    }
+    return n;
+}
+
+int pf_group_set_depth(pf_group* g, int depth, int band_sweeps) {
+    if (!g || depth < 1 || depth > 2 || band_sweeps < 1) return PF_ERR_INVALID;
+    if (depth != g->depth || band_sweeps != g->band_sweeps) {
+        g->depth = depth;
+        g->band_sweeps = band_sweeps;
+        g->dirty = true;
+    }
+    return PF_OK;
+}
+
+int pf_group_get_depth(pf_group* g, int* depth, int* band_sweeps, int* effective) {
+    if (!g) return PF_ERR_INVALID;
+    if (g->dirty && !g->members.empty()) {
+        const int rc = group_rebuild(g);
+        if (rc != PF_OK) return rc;
+    }
+    if (depth) *depth = g->depth;
+    if (band_sweeps) *band_sweeps = g->band_sweeps;
+    if (effective) *effective = (g->wave && !g->members.empty()) ? 2 : 1;
+    return PF_OK;
 }
 
 int pf_group_work_items(const pf_sim* s) {
@@ -1102,6 +1207,10 @@ int pf_group_create(int max_instances, int max_work, void* dev_mem, size_t bytes
     g->jobs = reinterpret_cast<ObsJob*>(reinterpret_cast<char*>(g->obs) +
                                         align256((size_t)max_instances * sizeof(ObsPartial)));
     g->thermal_any = false;
+    g->depth = 1;
+    g->band_sweeps = 1;
+    g->wave = false;
+    g->n_bands = 0;
     g->launches = 0;
     g->dirty = true;
     g->graph = nullptr;
@@ -1143,7 +1252,7 @@ int pf_group_step(pf_group* g, int64_t n, int use_graph) {
         if (rc != PF_OK) return rc;
     }
     int64_t done = 0;
-    const int GL = 16;  // launches per graph replay (even)
+    const int GL = 16;  // steps per graph replay (even)
     // on a failure the group and its members advance by the `done` steps launched
     auto stop = [&](int rc) {
         g->launches += done;
@@ -1161,7 +1270,10 @@ int pf_group_step(pf_group* g, int64_t n, int use_graph) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal));
             bool ok = true;
-            for (int i = 0; i < GL && ok; ++i) ok = group_launch_once(g, i & 1);
+            if (g->wave)
+                for (int i = 0; i < GL && ok; i += 2) ok = group_launch_pair(g, 0);
+            else
+                for (int i = 0; i < GL && ok; ++i) ok = group_launch_once(g, i & 1);
             cudaError_t e = cudaStreamEndCapture(g->st, &graph);
             if (!ok) return PF_ERR_INVALID;
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -1177,6 +1289,11 @@ int pf_group_step(pf_group* g, int64_t n, int use_graph) {
             done += GL;
         }
     }
+    if (g->wave)
+        for (; n - done >= 2; done += 2) {
+            if (inject_hits(2)) return stop(PF_ERR_CUDA);
+            if (!group_launch_pair(g, (int)((g->launches + done) & 1))) return stop(PF_ERR_INVALID);
+        }
     for (; done < n; ++done) {
         if (inject_hits(1)) return stop(PF_ERR_CUDA);
         if (!group_launch_once(g, (int)((g->launches + done) & 1))) return stop(PF_ERR_INVALID);

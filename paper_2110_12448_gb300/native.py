@@ -118,6 +118,9 @@ def lib():
                 "pf_group_size": (C.c_int, [vp]),
                 "pf_group_observe": (C.c_int, [vp, C.c_int, vp]),
                 "pf_group_destroy": (C.c_int, [vp]),
+                "pf_group_set_depth": (C.c_int, [vp, C.c_int, C.c_int]),
+                "pf_group_get_depth": (C.c_int, [vp, P(C.c_int), P(C.c_int), P(C.c_int)]),
+                "pf_wavefront_order": (C.c_int, [C.c_int, P(C.c_int), P(C.c_int), C.c_int]),
                 "pf_observe_fields_noalloc": (C.c_int, [P(Params), vp, vp, vp, P(C.c_double), P(C.c_double), C.c_int,
                                                         vp, P(Obs)]),
             }
@@ -373,6 +376,17 @@ def observe_fields_noalloc(p: Params, psi_dev: int, U_dev: int, grain_dev: Optio
     return d
 
 
+def wavefront_order(n_bands: int) -> list:
+    """pf_wavefront_order: the (level, band) launches of one depth-2
+    wavefront, level 0 = step n+1, level 1 = step n+2."""
+    m = 2 * int(n_bands)
+    lv, bd = (C.c_int * max(1, m))(), (C.c_int * max(1, m))()
+    n = lib().pf_wavefront_order(int(n_bands), lv, bd, m)
+    if n < 0:
+        raise PfError(n, "pf_wavefront_order")
+    return [(lv[i], bd[i]) for i in range(n)]
+
+
 class Group:
     """Instances stepped together by one persistent launch per class."""
 
@@ -406,6 +420,17 @@ class Group:
 
     def step(self, n: int = 1, use_graph: bool = True):
         _check(lib().pf_group_step(self.h, int(n), 1 if use_graph else 0), "pf_group_step")
+
+    def set_depth(self, depth: int, band_sweeps: int = 1):
+        """pf_group_set_depth: temporal-blocking depth 1 or 2 (two steps per
+        wavefront over bands of band_sweeps sweeps)."""
+        _check(lib().pf_group_set_depth(self.h, int(depth), int(band_sweeps)), "pf_group_set_depth")
+
+    def depth(self) -> tuple:
+        """(depth, band_sweeps, depth in effect for the current members)"""
+        d, b, e = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().pf_group_get_depth(self.h, C.byref(d), C.byref(b), C.byref(e)), "pf_group_get_depth")
+        return d.value, b.value, e.value
 
     def observe(self, grain: int = -1, allow_nonfinite=False) -> list:
         """pf_group_observe: observe() of every member, one synchronisation;

@@ -1,5 +1,5 @@
-"""Host logic of the autotuner (no GPU): the work-list size model and the
-wave-aligned sweep candidates."""
+"""Host logic of the autotuner (no GPU): the work-list size model, the
+wave-aligned sweep candidates and the temporal-blocking candidates."""
 from paper_2110_12448_gb300 import autotune as A
 from paper_2110_12448_gb300 import synth
 
@@ -34,3 +34,41 @@ def test_wave_aligned_handles_batches_larger_than_one_wave_per_band():
     cands = A.wave_aligned(w3, 34, 10, 304)
     assert cands[0][2] == 256  # whole-depth sweeps already need two waves
     assert all(8 <= t[2] <= 256 for t in cands)
+
+
+def test_band_candidates_fill_their_waves():
+    ws = [synth.free_dendrite_2d(1024, 5.0 * t) for t in range(10)]
+    resident = 2432
+    for base in ((64, 1, 38), (64, 1, 8)):
+        cands = A.band_candidates(ws, base, resident)
+        assert [c[:4] for c in cands] == [base + (2,)] * len(cands)
+        per_row = 10 * 18  # 60-column strips of ten 1024-column instances
+        for k, c in zip((1, 2), cands):
+            bs = c[4]
+            # the fewest sweeps per band whose items fill k waves (or the whole depth)
+            assert bs * per_row >= k * resident or bs == -(-1024 // base[2])
+            assert bs == 1 or (bs - 1) * per_row < k * resident
+    assert A.band_candidates(ws, (64, 1, 38), resident)[-1] == (64, 1, 38, 2, 27)  # one band: two plain steps
+
+
+def test_split_bands_and_depth_race():
+    assert A.split((64, 1, 38)) == ((64, 1, 38), (1, 1))
+    assert A.split([34, 10, 8, 2, 3]) == ((34, 10, 8), (2, 3))
+    ws = [synth.free_dendrite_2d(1024), synth.free_dendrite_2d(200)]
+    assert A.bands(ws, (64, 1, 38)) == 1
+    assert A.bands(ws, (64, 1, 8, 2, 14)) == 10  # 128 sweeps of the deeper instance in bands of 14
+    w3 = [synth.free_dendrite_3d(64)]
+    assert A.bands(w3, (34, 10, 16, 2, 3)) == 2
+    r = A.depth_race({"(64, 1, 38)": 1.2e-4, "(64, 1, 8, 2, 14)": 1.6e-4, "(64, 1, 12)": 1.3e-4,
+                      "(64, 1, 38, 2, 27)": 1.25e-4})
+    assert r["depth1_tile"] == [64, 1, 38] and abs(r["depth1_ms"] - 0.12) < 1e-12
+    assert r["depth2_tile"] == [64, 1, 38, 2, 27] and abs(r["depth2_ms"] - 0.125) < 1e-12
+
+
+def test_wavefront_eligibility():
+    w = synth.free_dendrite_2d(64)
+    assert A.wavefront_ok(w)
+    w.thermal = 1
+    assert not A.wavefront_ok(w)
+    w.thermal, w.kernels = 0, 1
+    assert not A.wavefront_ok(w)

@@ -2,7 +2,8 @@
 gives every instance exactly the state it reaches in one group on one stream:
 the instances are independent and each group launch computes the same
 arithmetic.  Checked bit for bit in FP32 after graph-replayed runs with
-observes in between, with the observe records in workload order."""
+observes in between, with the observe records in workload order, also with
+the groups at temporal-blocking depth 2 (two steps per band wavefront)."""
 import numpy as np
 import pytest
 
@@ -22,7 +23,8 @@ def native():
 
 
 @pytest.mark.parametrize("n_streams", [1, 2, 3])
-def test_batch_equals_one_group(native, n_streams):
+@pytest.mark.parametrize("tile", [(64, 1, 16), (64, 1, 16, 2, 2)])
+def test_batch_equals_one_group(native, n_streams, tile):
     import torch
     from paper_2110_12448_gb300.batch import Batch
     ws = [synth.free_dendrite_2d(n, theta_deg=t) for n, t in ((96, 0.0), (130, 10.0), (70, 25.0), (111, 40.0))]
@@ -39,8 +41,9 @@ def test_batch_equals_one_group(native, n_streams):
     ref_obs = g.observe(0)
     g.close()
 
-    b = Batch(ws, "f32", n_streams=n_streams, tile=(64, 1, 16))
+    b = Batch(ws, "f32", n_streams=n_streams, tile=tile)
     assert len(b.groups) == min(n_streams, len(ws))
+    assert all(g.depth()[2] == (tile[3] if len(tile) > 3 else 1) for g in b.groups)
     b.step(20, use_graph=True, stream=st)
     mid = b.observe(0)
     assert len(mid) == len(ws)
