@@ -145,3 +145,81 @@ def test_set_depth_validates(native):
     grp.set_depth(2, 4)
     assert grp.depth() == (2, 4, 1)  # no members: nothing steps as a wavefront
     grp.close()
+
+
+def _sims(N, cases, prec, tiles, st):
+    sims = []
+    for (w, psi, U, g, rots), tile in zip(cases, tiles):
+        p = N.make_params(w.dim, w.nx, w.ny, w.nz, w.h, w.dt, w.k, w.eps4, w.lam, w.D, w.U0, w.scheme, prec,
+                          max_grains=rots.shape[0])
+        s = N.Sim(p, stream=st)
+        s.set_grains(rots)
+        s.set_grain_index(g)
+        dt = np.float32 if prec == "f32" else np.float64
+        s.set_fields(psi.astype(dt), U.astype(dt))
+        s.set_tile(*tile)
+        sims.append(s)
+    return sims
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_2d_and_3d_classes_with_different_band_counts(native, prec):
+    """A 2D and a 3D member in one depth-2 group: the classes have different
+    band counts (the 2D member 11 one-sweep bands, the 3D member 5), and each
+    band launch skips the classes that have no items in it."""
+    import torch
+    cases = states(2, ["SBAR21"], seed=9) + states(3, ["SBAR120"], seed=10)
+    tiles = [(64, 1, 8), (34, 10, 8)]
+    out = []
+    for depth in (1, 2):
+        st = torch.cuda.Stream()
+        sims = _sims(native, cases, prec, tiles, st)
+        grp = native.Group(2, sum(native.Group.work_items(s) for s in sims), stream=st)
+        for s in sims:
+            grp.add(s)
+        grp.set_depth(depth, 1)
+        assert grp.depth()[2] == depth
+        grp.step(20, use_graph=True)
+        grp.step(3, use_graph=False)
+        grp.close()
+        out.append([s.get_fields() for s in sims])
+        for s in sims:
+            s.close()
+    for (pa, ua), (pb, ub) in zip(*out):
+        assert np.array_equal(pa, pb) and np.array_equal(ua, ub)
+
+
+def test_depth_survives_membership_changes(native):
+    """The depth setting holds when members leave and join; a thermal member
+    joining turns the wavefronts off, and its leaving turns them back on."""
+    import torch
+    cases = states(2, ["SBAR21", "SBAR21"], seed=12)
+    st = torch.cuda.Stream()
+    a, b = _sims(native, cases, "f32", [(64, 1, 8)] * 2, st)
+    grp = native.Group(3, native.Group.work_items(a) + 2 * native.Group.work_items(b), stream=st)
+    grp.set_depth(2, 3)
+    grp.add(a)
+    grp.add(b)
+    assert grp.depth() == (2, 3, 2)
+    grp.step(4, use_graph=False)
+    grp.remove(b)
+    assert grp.depth() == (2, 3, 2)
+    w = cases[0][0]
+    pt = native.make_params(w.dim, w.nx, w.ny, w.nz, w.h, w.dt, w.k, w.eps4, w.lam, w.D, w.U0, w.scheme, "f32",
+                            thermal=1, Vp=0.01, lT=1000.0, yT=0.3 * w.ny * w.h)
+    t = native.Sim(pt, stream=st)
+    t.set_fields(cases[0][1].astype(np.float32), cases[0][2].astype(np.float32))
+    t.set_tile(64, 1, 8)
+    grp.add(t)
+    assert grp.depth() == (2, 3, 1)
+    grp.step(2, use_graph=False)
+    grp.remove(t)
+    assert grp.depth() == (2, 3, 2)
+    grp.step(2, use_graph=False)
+    grp.close()
+    # a alone at depth 1 for the same 8 steps
+    (ref,), _ = run(native, cases[:1], "f32", (64, 1, 8), 1, 1, 8, False)
+    got = a.get_fields()
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+    for s in (a, b, t):
+        s.close()
