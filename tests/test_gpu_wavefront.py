@@ -1,9 +1,9 @@
 """GPU checks of depth-2 temporal blocking (pf_group_set_depth): a group that
 advances two steps per wavefront over bands gives, cell for cell, the same
 arithmetic as one launch per step, so its fields equal the depth-1 group's
-bit for bit, in FP32 and FP64, 2D and 3D, for ragged bands, odd step counts,
-odd starting parity, graph replay and mixed classes; FP64 also against the
-oracle directly.  Groups that cannot step as wavefronts (frozen temperature,
+bit for bit, in FP32, FP64 and on the compensated FP32 state, 2D and 3D, for
+ragged bands, odd step counts, odd starting parity, graph replay and mixed
+classes; FP64 also against the oracle directly.  Groups that cannot step as wavefronts (frozen temperature,
 two-kernel form) report depth 1 in effect and step as before."""
 import numpy as np
 import pytest
@@ -70,7 +70,7 @@ def run(N, cases, prec, tile, depth, band_sweeps, steps, use_graph, pre=0, extra
     return out, eff
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("prec", ["f32", "f64", "f32c"])
 @pytest.mark.parametrize("band_sweeps", [1, 2, 5])
 @pytest.mark.parametrize("steps,use_graph,pre", [(5, False, 0), (7, False, 1), (36, True, 0), (21, True, 1)])
 def test_2d_depth2_equals_depth1(native, prec, band_sweeps, steps, use_graph, pre):
