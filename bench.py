@@ -38,11 +38,23 @@ PHYS_STEPS = 20000
 DS_THETAS = (0, 10, 20, 30, 40)
 DS_VP, DS_LT = 0.1, 2000.0
 OBS_EVERY = 100
-# algorithmic bytes per cell update: read psi, U, grain; write psi', U'
-# (f32c: hi and lo halves of psi and U).  The two-kernel form adds the
-# d psi/dt write and read and the U pass's second read of psi and U.
-B_PER_CELL = {"f32": 18, "f64": 34, "f32c": 34}
-B_PER_CELL_TWO = {"f32": 34, "f64": 66}
+# algorithmic bytes per cell update: read psi, U; write psi', U' (f32c: hi
+# and lo halves of psi and U); the two-kernel form adds the d psi/dt write
+# and read and the U pass's second read of psi and U.  Plus the int16 grain
+# index where it is read: in 3D always, in 2D only for instances with cells
+# outside grain 0 (the 2D step reads no grain rows when every cell is in
+# grain 0).
+B_STATE = {"f32": 16, "f64": 32, "f32c": 32}
+B_STATE_TWO = {"f32": 32, "f64": 64}
+B_GRAIN = 2
+
+
+def bytes_per_cell(ws, precision, two=False) -> float:
+    """Algorithmic bytes per cell update of a batch, averaged over its cells."""
+    cells = sum(w.n_cells for w in ws)
+    graincells = sum(w.n_cells for w in ws
+                     if w.dim == 3 or (len(w.seed_grain) and int(max(w.seed_grain)) > 0))
+    return (B_STATE_TWO if two else B_STATE)[precision] + B_GRAIN * graincells / cells
 
 
 def dist_env():
@@ -63,7 +75,7 @@ TRAFFIC = {
     # k_step2d<float, S-bar_21> launches of the two five-instance groups, summed (ncu runs them one
     # after the other, so each group's half of the state partly stays in L2)
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu", "tile": [64, 1, 38],
-                "sha256": "14be623eb6a89ef5e15fc15b790f6f3aba135cbc80291d90a6a528ccd3ee2178", "bytes": 120690176},
+                "sha256": "51b2245cc8536307702969be51cd8ebcc4eef9819cb65035bf04650382af4634", "bytes": 103638016},
     # one k_step3d<float, S-bar_120, 30, 6> launch of the 256^3 free dendrite (tile 34 x 10 x 52)
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu", "tile": [34, 10, 52],
                    "sha256": "1f5d22af251dade05882fb4be57c4fe582caa7ec964125d0cab5048c80b10939", "bytes": 265664000},
@@ -80,7 +92,7 @@ TRAFFIC = {
 FLOPS = {
     # k_step2d<float, S-bar_21> launch of the orientation sweep (10 x 1024^2, tile 64 x 1 x 38)
     "sweep2d": {"source": "paper_2110_12448_gb300/csrc/step2d.cu", "tile": [64, 1, 38],
-                "sha256": "14be623eb6a89ef5e15fc15b790f6f3aba135cbc80291d90a6a528ccd3ee2178", "flop_per_cell": 261.2},
+                "sha256": "51b2245cc8536307702969be51cd8ebcc4eef9819cb65035bf04650382af4634", "flop_per_cell": 261.2},
     # k_step3d<float, S-bar_120, 30, 6> launch of the 256^3 free dendrite (tile 34 x 10 x 52)
     "dendrite3d": {"source": "paper_2110_12448_gb300/csrc/step3d.cu", "tile": [34, 10, 52],
                    "sha256": "1f5d22af251dade05882fb4be57c4fe582caa7ec964125d0cab5048c80b10939", "flop_per_cell": 1100.6},
@@ -302,8 +314,8 @@ def at_stated_error(stream, ws, steps, n_streams=2):
             "ms_per_step": ms / steps, "steps": steps, "tile": list(tile),
             "contract": "max |d phi|, |d U| <= 1e-4 vs the FP64 oracle after 10^4 steps of the 200^2 free dendrite, "
                         "tip speed within 0.5 % (tests/test_gpu_contract.py)",
-            "bytes_per_cell": B_PER_CELL["f32c"],
-            "hbm_frac": cells * B_PER_CELL["f32c"] / (ms / steps / 1e3) / 1e9 / peaks()[0]}
+            "bytes_per_cell": bytes_per_cell(ws, "f32c"),
+            "hbm_frac": cells * bytes_per_cell(ws, "f32c") / (ms / steps / 1e3) / 1e9 / peaks()[0]}
 
 
 def fp64_plain(stream, n=200, steps=2000):
@@ -870,7 +882,7 @@ def run_native(args):
 
     # roofline of the fused step kernel: algorithmic bytes per launch / mean launch time
     peak, peak_kind = peaks()
-    bpc = (B_PER_CELL_TWO if args.kernels == "two" else B_PER_CELL)[args.precision]
+    bpc = bytes_per_cell(ws, args.precision, two=args.kernels == "two")
     achieved = cells * bpc / (kern_ms / n_launch / 1e3) / 1e9
     tname = {"f32": "float", "f64": "double", "f32c": "float, compensated state"}[args.precision]
     kname = ("k_step2d" if ws[0].dim == 2 else "k_step3d") + f"<{tname},{args.scheme}>"

@@ -93,15 +93,18 @@ def wavefront_ok(w) -> bool:
 
 def band_candidates(workloads, tile, resident, waves=(1, 2)):
     """Depth-2 candidates for a depth-1 tile: for each wave count k, the
-    fewest sweeps per band whose work items fill k waves of `resident` units
-    (capped at the deepest instance's sweeps, where one band is two plain
-    steps)."""
+    fewest sweeps per band whose work items fill k waves of `resident` units,
+    at most half the deepest instance's sweeps: a single band would be two
+    whole-grid launches, the schedule of depth 1 (a batch too small to fill
+    the GPU with one band gets two bands)."""
     bx, by, sw = tile
     per_band_row = sum(work_items(w, (bx, by, 1 << 30)) for w in workloads)  # items of one sweep row
     sweeps = max(-(-(w.ny if w.dim == 2 else w.nz) // sw) for w in workloads)
     out = []
+    if sweeps < 2:
+        return out
     for k in waves:
-        bs = min(sweeps, max(1, -(-k * resident // per_band_row)))
+        bs = min(max(1, -(-k * resident // per_band_row)), -(-sweeps // 2))
         if (bx, by, sw, 2, bs) not in out:
             out.append((bx, by, sw, 2, bs))
     return out

@@ -171,6 +171,8 @@ struct pf_sim {
     InstRec* rec;
     void* rate;  // d psi/dt of the two-kernel form (nullptr when fused)
     int n_grains;
+    int gmax;         // largest grain index in the map (0: every cell in grain 0)
+    int64_t rec_gen;  // advanced by every change the instance record carries
     std::vector<double> rot_h, centres_h;
     int64_t step;
     int bx, by, sweep, n_work, grid;
@@ -246,6 +248,7 @@ InstRec make_rec(const pf_sim* s, int parity_offset) {
     r.bcx = s->p.bc_x == PF_BC_PERIODIC ? 1 : 0;
     r.tlevel = s->p.time_level == PF_T0 ? 1 : 0;
     r.n_grains = s->n_grains;
+    r.one_grain = s->gmax == 0 ? 1 : 0;
     if (r.thermal) {
         r.zA = s->p.h / s->p.lT;
         r.zB = s->p.yT / s->p.lT;
@@ -394,6 +397,8 @@ int pf_create(const pf_params* p, void* dev_mem, size_t bytes, void* stream, pf_
     s->rec = reinterpret_cast<InstRec*>(s->base + L.rec);
     s->rate = p->kernels == PF_TWO_KERNELS ? s->base + L.rate : nullptr;
     s->n_grains = 1;
+    s->gmax = 0;  // the grain map starts zero-filled
+    s->rec_gen = 0;
     s->rot_h.assign(9, 0.0);
     s->rot_h[0] = s->rot_h[4] = s->rot_h[8] = 1.0;
     s->centres_h.assign(3, 0.0);
@@ -449,6 +454,7 @@ int pf_set_grains(pf_sim* s, int n_grains, const double* rot9, const double* cen
     s->have_prev.assign(n_grains + 2, 0);
     s->prev.assign(4 * (n_grains + 2), 0.0);
     s->work_dirty = true;  // the instance record carries the grain count
+    ++s->rec_gen;
     return upload_rot(s);
 }
 
@@ -462,6 +468,9 @@ int pf_init_seeds(pf_sim* s, int n_seeds, const pf_seed* seeds) {
             return PF_ERR_INVALID;
         h[i] = SeedDev{seeds[i].x, seeds[i].y, s->p.dim == 3 ? seeds[i].z : 0.0, seeds[i].r, seeds[i].grain, 0};
     }
+    // every cell takes the grain of its nearest seed
+    int gmax = 0;
+    for (int i = 0; i < n_seeds; ++i) gmax = std::max(gmax, (int)seeds[i].grain);
     CK(cudaMemcpyAsync(s->seeds, h.data(), n_seeds * sizeof(SeedDev), cudaMemcpyHostToDevice, s->st));
     const int cur = (int)(s->step & 1);
     if (s->p.precision == PF_F32C) {
@@ -474,15 +483,24 @@ int pf_init_seeds(pf_sim* s, int n_seeds, const pf_seed* seeds) {
                              s->seeds, n_seeds, s->psi[cur], s->U[cur], s->grain, s->st));
     }
     CK(cudaStreamSynchronize(s->st));
+    s->gmax = gmax;
+    s->work_dirty = true;
+    ++s->rec_gen;
     return PF_OK;
 }
 
 int pf_set_grain_index(pf_sim* s, const int16_t* g) {
     if (!s || !g) return PF_ERR_INVALID;
-    for (size_t c = 0; c < s->L.N; ++c)
+    int gmax = 0;
+    for (size_t c = 0; c < s->L.N; ++c) {
         if (g[c] < 0 || g[c] >= s->n_grains) return PF_ERR_INVALID;
+        gmax = std::max(gmax, (int)g[c]);
+    }
     CK(cudaMemcpyAsync(s->grain, g, s->L.N * sizeof(int16_t), cudaMemcpyHostToDevice, s->st));
     CK(cudaStreamSynchronize(s->st));
+    s->gmax = gmax;  // the instance record says whether every cell is in grain 0
+    s->work_dirty = true;
+    ++s->rec_gen;
     return PF_OK;
 }
 
@@ -970,6 +988,7 @@ struct pf_group {
         std::vector<int> boff;  // depth 2: work items of band b are [w0 + boff[b], w0 + boff[b + 1])
     };
     std::vector<Cls> classes;
+    std::vector<int64_t> gens;  // members' record generations at the last rebuild
     // temporal blocking (pf_group_set_depth): the setting, and whether the
     // current members step as depth-2 wavefronts over n_bands bands
     int depth, band_sweeps;
@@ -1004,9 +1023,11 @@ int group_rebuild(pf_group* g) {
                ((long long)s->p.precision << 24) | ((long long)s->bx << 12) | (long long)s->by;
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
+    g->gens.clear();
     for (size_t m = 0; m < g->members.size(); ++m) {
         const pf_sim* s = g->members[m];
         recs.push_back(make_rec(s, (int)((s->step ^ g->launches) & 1)));
+        g->gens.push_back(s->rec_gen);
     }
     long long prev = -1;
     // depth 2 applies when no member has a frozen temperature or the
@@ -1247,6 +1268,9 @@ int pf_group_remove(pf_group* g, pf_sim* s) {
 int pf_group_step(pf_group* g, int64_t n, int use_graph) {
     if (!g || n < 0) return PF_ERR_INVALID;
     if (g->members.empty() || n == 0) return PF_OK;
+    // a member whose grains changed since the last rebuild needs a new record
+    for (size_t m = 0; m < g->members.size() && !g->dirty; ++m)
+        if (m >= g->gens.size() || g->members[m]->rec_gen != g->gens[m]) g->dirty = true;
     if (g->dirty) {
         int rc = group_rebuild(g);
         if (rc != PF_OK) return rc;

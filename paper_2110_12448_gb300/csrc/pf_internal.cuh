@@ -45,6 +45,8 @@ struct InstRec {
     int32_t bcx;      // 1: periodic x (2D)
     int32_t tlevel;   // 1: T0 time level (pure forward Euler of Eq. PF_b)
     int32_t n_grains; // rows of the rotation table
+    int32_t one_grain; // 1: every cell is in grain 0 (the grain map need not be read)
+    int32_t pad_;
     double h, dt, k, eps4, lambda, D;
     // frozen temperature: zeta(row j, step n) = j zA - zB - n zC
     // (zA = h / lT, zB = yT / lT, zC = Vp dt / lT)

@@ -596,6 +596,9 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
         const T isq2dt = cst[C_ISQ2DT];
         const bool vec = (nx & 1) == 0;
         const bool per = DS && rec.bcx != 0;
+        // every cell in grain 0 (warp-uniform): one crystal frame, no grain
+        // rows to read and no grain-boundary faces to recompute
+        const bool one = rec.one_grain != 0;
         const bool t0 = T0I || (DS && rec.tlevel != 0);  // T0 time level
         // frozen temperature: zeta at row p = zeta_y0 + (p - y0) zA (Eqs. Thermal_F1/_F2);
         // the DS variant applies it branch-free (zA = zB = zC = 0 gives zeta = 0, F1 = 1)
@@ -710,6 +713,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
         V<T> qy_c = bc<T>(T(0));
         int gyL_c = -1, gyR_c = -1;
         int prow_c = -100;
+        if (one) set_rot(0, 0);
 
         // phase 1 at real row p (psi rows Pm = p-1, P0 = p, Pp = p+1), grains
         // gL, gR: returns psi' and phi' of the own columns and delta phi.
@@ -746,8 +750,8 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                 psin = psin_lo = bc<T>(T(0));
                 return;
             }
-            set_rot(gL, gR);
-            const int gM = shup(gR);  // grain of column L-1
+            if (!one) set_rot(gL, gR);
+            const int gM = one ? 0 : shup(gR);  // grain of column L-1
             const V<T> W0 = P0.W(), C0 = P0.C(), E0 = P0.E();
             const V<T> Wm = Pm.W(), Cm = Pm.C(), Em = Pm.E();
             const V<T> Wp = Pp.W(), Cp = Pp.C(), Ep = Pp.E();
@@ -767,14 +771,16 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             // x- faces: from the left column; recomputed across grain boundaries.
             // Lane 0 receives its own value: its column L (x0-2) feeds no output.
             T xmL = shup(Xp.y()), xmR = Xp.x();
-            if (gM != gL)
-                xmL = aq1((P0.l - P0.m1) * ih, ((Pp.l + Pp.m1) - (Pm.l + Pm.m1)) * i4h, RR.a.x(), RR.b.x(), RR.c.x(),
-                          RR.d.x());
-            if (gR != gL) xmR = aq1(gxX.x(), gyX.x(), RR.a.y(), RR.b.y(), RR.c.y(), RR.d.y());
+            if (!one) {
+                if (gM != gL)
+                    xmL = aq1((P0.l - P0.m1) * ih, ((Pp.l + Pp.m1) - (Pm.l + Pm.m1)) * i4h, RR.a.x(), RR.b.x(),
+                              RR.c.x(), RR.d.x());
+                if (gR != gL) xmR = aq1(gxX.x(), gyX.x(), RR.a.y(), RR.b.y(), RR.c.y(), RR.d.y());
+            }
             // y+ faces; y- faces carried from row p-1 when valid
             const V<T> Yp = aq2(((Ep + E0) - (Wp + W0)) * bc<T>(i4h), (Cp - C0) * bc<T>(ih), false);
             V<T> Ym = qy_c;
-            const bool okL = prow_c == p && gyL_c == gL, okR = prow_c == p && gyR_c == gR;
+            const bool okL = prow_c == p && (one || gyL_c == gL), okR = prow_c == p && (one || gyR_c == gR);
             if (!(okL && okR)) {
                 const V<T> Yc = aq2(((E0 + Em) - (W0 + Wm)) * bc<T>(i4h), (C0 - Cm) * bc<T>(ih), false);
                 Ym = mk(okL ? Ym.x() : Yc.x(), okR ? Ym.y() : Yc.y());
@@ -1063,12 +1069,13 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             int gL, gR;
             V<T> psn, psnl, fn, dm = bc<T>(T(0)), d0, rt, phc_unused;
             const bool ghost = (y0 - 1) < 0;
+            gL = gR = 0;
             if (!ghost && MODE != 1) {
-                load_grain_pair(grain + (size_t)PF_CHK((y0 - 1), ny) * nx, cL, nx, vec, per, gL, gR);
+                if (!one) load_grain_pair(grain + (size_t)PF_CHK((y0 - 1), ny) * nx, cL, nx, vec, per, gL, gR);
                 phase1(y0 - 1, P[1], P[2], P[3], phm, um, gL, gR, lq[0], lq[1], lq[2], ulm.C(), psn, psnl, fn, dm, rt,
                        phc_unused);
             }
-            load_grain_pair(grain + (size_t)PF_CHK(y0, ny) * nx, cL, nx, vec, per, gL, gR);
+            if (!one) load_grain_pair(grain + (size_t)PF_CHK(y0, ny) * nx, cL, nx, vec, per, gL, gR);
             phase1(y0, P[2], P[3], P[4], ph0, u0, gL, gR, lq[1], lq[2], lq[3], ul0.C(), psn, psnl, fn, d0, rt,
                    phc_unused);
             if (ghost) dm = d0;
@@ -1104,7 +1111,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
             fetch_row(psiL, y0 + 2, nPLa, nPLb);
             fetch_row(UfL, y0 + 1, nULa, nULb);
         }
-        if (y0 + 1 < ny) load_grain_pair(grain + (size_t)PF_CHK((y0 + 1), ny) * nx, cL, nx, vec, per, nGa, nGb);
+        if (!one && y0 + 1 < ny) load_grain_pair(grain + (size_t)PF_CHK((y0 + 1), ny) * nx, cL, nx, vec, per, nGa, nGb);
 
         // ---------------- sweep ----------------
         for (int r = y0; r < y1; ++r) {
@@ -1124,7 +1131,7 @@ __global__ void __launch_bounds__(32 * PF_STEP2D_WPB,
                 fetch_row(psiL, r + 3, nPLa, nPLb);
                 fetch_row(UfL, r + 2, nULa, nULb);
             }
-            if (r + 2 < ny) load_grain_pair(grain + (size_t)PF_CHK((r + 2), ny) * nx, cL, nx, vec, per, nGa, nGb);
+            if (!one && r + 2 < ny) load_grain_pair(grain + (size_t)PF_CHK((r + 2), ny) * nx, cL, nx, vec, per, nGa, nGb);
 
             // phase 1 at row r+1 (the psi pass of the two-kernel form: only
             // rows it stores)

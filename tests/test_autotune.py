@@ -45,10 +45,17 @@ def test_band_candidates_fill_their_waves():
         per_row = 10 * 18  # 60-column strips of ten 1024-column instances
         for k, c in zip((1, 2), cands):
             bs = c[4]
-            # the fewest sweeps per band whose items fill k waves (or the whole depth)
-            assert bs * per_row >= k * resident or bs == -(-1024 // base[2])
-            assert bs == 1 or (bs - 1) * per_row < k * resident
-    assert A.band_candidates(ws, (64, 1, 38), resident)[-1] == (64, 1, 38, 2, 27)  # one band: two plain steps
+            # the fewest sweeps per band whose items fill k waves, at most half the depth
+            half = -(-(-(-1024 // base[2])) // 2)
+            assert bs == half or (bs * per_row >= k * resident and (bs == 1 or (bs - 1) * per_row < k * resident))
+            assert bs <= half
+    # 27 sweeps of 38 rows cover the 1024 rows: one band, the depth-1 schedule, is not raced
+    assert A.band_candidates(ws, (64, 1, 38), resident) == [(64, 1, 38, 2, 14)]
+    assert A.band_candidates(ws, (64, 1, 8), resident) == [(64, 1, 8, 2, 14), (64, 1, 8, 2, 28)]
+    # two 256^2 instances cannot fill the GPU with one band: two bands of 16 sweeps
+    small = [synth.free_dendrite_2d(256), synth.free_dendrite_2d(256)]
+    assert A.band_candidates(small, (64, 1, 8), resident) == [(64, 1, 8, 2, 16)]
+    assert A.band_candidates(small, (64, 1, 256), resident) == []  # one sweep: no band to split
 
 
 def test_split_bands_and_depth_race():
