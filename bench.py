@@ -933,6 +933,9 @@ def run_native(args):
             with torch.cuda.stream(st_):
                 for i in idx:
                     ss.append(N.Sim.from_workload(ws[i], args.precision, stream=st_, init=False))
+                    # the grain map is part of the problem, not of the per-step state: the
+                    # same map as the measured instance, set before the timed region
+                    ss[-1].set_grain_index(sims[i].get_grain_index())
                     if tile:
                         ss[-1].set_tile(*autotune.split(tile)[0])
             g_ = N.Group(len(ss), sum(N.Group.work_items(x) for x in ss), stream=st_)
