@@ -194,7 +194,14 @@ int pf_set_grains(pf_sim* s, int n_grains, const double* rot9, const double* cen
  * handle that was never seeded holds the all-liquid state pf_create leaves). */
 int pf_init_seeds(pf_sim* s, int n_seeds, const pf_seed* seeds);
 
-/* Copy an explicit per-cell grain map (nx*ny*nz int16, values < n_grains). */
+/* Copy an explicit per-cell grain map (nx*ny*nz int16, values < n_grains).
+ * The library remembers the largest index it has written into the map
+ * (here and in pf_init_seeds); while that is 0, every cell is in grain 0 and
+ * the 2D step reads no grain rows, with the same arithmetic.  A change of
+ * grains (this call, pf_init_seeds, pf_set_grains) on a member of a group
+ * takes effect at the group's next pf_group_step, which rebuilds that
+ * member's instance record; the caller orders the change after the group's
+ * queued work, as for any call on a member. */
 int pf_set_grain_index(pf_sim* s, const int16_t* host_grain);
 int pf_get_grain_index(pf_sim* s, int16_t* host_grain);
 
